@@ -1,0 +1,148 @@
+"""Seeded synthetic inputs shaped like the paper's MDS workloads.
+
+This module only *generates data*: latent positions, the dissimilarity matrix
+Y and start points.  It holds none of the likelihood, gradient or HMC
+arithmetic, and both the CUDA path's tests/benchmarks and the CPU oracle take
+their inputs from it.
+
+The paper's data (5,392 influenza sequences and air-traffic effective
+distances, section 3) are not available, so every input here is synthetic:
+latent positions from a seeded Gaussian mixture (or a standard normal for the
+small case), dissimilarities drawn from the model of Eq. (1) -- the true
+distance plus N(0, noise^2) noise, folded at zero so that y_ij >= 0 -- and an
+evaluation point X_eval = X_true + N(0, 0.1^2).
+
+Y is returned as the packed strict upper triangle, row-major
+(0,1),(0,2),...,(N-2,N-1), in FP32.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy.spatial.distance import cdist
+
+
+@dataclass
+class Workload:
+    name: str
+    n: int
+    d: int
+    sigma: float
+    seed: int
+    x_true: np.ndarray  # N x D float64
+    x_eval: np.ndarray  # N x D float32 (the point the likelihood is evaluated at)
+    y_packed: np.ndarray  # N(N-1)/2 float32
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def m(self) -> int:
+        return self.n * (self.n - 1) // 2
+
+
+def _positions_normal(rng, n, d):
+    return rng.standard_normal((n, d))
+
+
+def _positions_mixture(rng, n, d, n_comp, spread, box=5.0):
+    centres = rng.uniform(-box, box, size=(n_comp, d))
+    labels = rng.integers(0, n_comp, size=n)
+    return centres[labels] + spread * rng.standard_normal((n, d))
+
+
+def _packed_dissimilarities(rng, x, noise, block=256):
+    """|dist(x_i, x_j) + noise * eps_ij| for i < j, packed row-major, FP32.
+    Rows are produced in blocks; the noise stream is drawn in packed order."""
+    n = x.shape[0]
+    out = np.empty(n * (n - 1) // 2, dtype=np.float32)
+    pos = 0
+    for i0 in range(0, n, block):
+        i1 = min(n, i0 + block)
+        dist = cdist(x[i0:i1], x[i0:])  # rows i0..i1-1 against columns i0..N-1
+        for r in range(i1 - i0):
+            i = i0 + r
+            row = dist[r, r + 1:]
+            cnt = row.shape[0]
+            if cnt == 0:
+                continue
+            eps = rng.standard_normal(cnt)
+            out[pos:pos + cnt] = np.abs(row + noise * eps).astype(np.float32)
+            pos += cnt
+    assert pos == out.shape[0]
+    return out
+
+
+def make(name, n, d, sigma, seed, noise, mixture=None, eval_jitter=0.1):
+    """Build one workload.  mixture=(n_comp, spread) draws positions from a
+    Gaussian mixture with centres uniform in [-5, 5]^D; None draws N(0, I)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if mixture is None:
+        x_true = _positions_normal(rng, n, d)
+    else:
+        x_true = _positions_mixture(rng, n, d, mixture[0], mixture[1])
+    y = _packed_dissimilarities(rng, x_true, noise)
+    x_eval = (x_true + eval_jitter * rng.standard_normal((n, d))).astype(np.float32)
+    meta = {"noise_sd": noise, "mixture": mixture, "eval_jitter": eval_jitter}
+    return Workload(name, n, d, float(sigma), seed, x_true, x_eval, y, meta)
+
+
+# --- the five workload recipes ------------------------------------------
+
+def small(seed=0):
+    """Oracle-sized case: N=200, D=2, x ~ N(0, I), noise sd 0.5, sigma 0.5."""
+    return make("small N=200 D=2", 200, 2, 0.5, seed, 0.5)
+
+
+def paper_scale(seed=1, d=2):
+    """Paper-scale case: N=5392 (the paper's number of items), D=2, 6-component
+    mixture (spread 0.3), noise sd 0.3 folded at 0, sigma 0.3."""
+    return make(f"paper-scale N=5392 D={d}", 5392, d, 0.3, seed, 0.3, mixture=(6, 0.3))
+
+
+BATCH_NS = (1600, 1500, 1300, 992)
+BATCH_SIGMAS = (0.2, 0.3, 0.4, 0.5)
+
+
+def batch_datasets():
+    """Four independent datasets of uneven N (1600, 1500, 1300, 992), D=2,
+    seeds 3..6, 6-component mixtures, noise sd = sigma in {0.2,0.3,0.4,0.5}."""
+    return [make(f"batch N={n} D=2", n, 2, s, 3 + k, s, mixture=(6, 0.3))
+            for k, (n, s) in enumerate(zip(BATCH_NS, BATCH_SIGMAS))]
+
+
+def scale_sweep(n, d, seed=7):
+    """Scale sweep: N in {20000, 50000}, D in {2, 6}, 12-component mixture,
+    noise sd 0.3, sigma 0.3 (Y stored as the packed upper triangle)."""
+    return make(f"scale N={n} D={d}", n, d, 0.3, seed, 0.3, mixture=(12, 0.3))
+
+
+def custom(n, d, sigma=0.5, seed=11, noise=None, mixture=None):
+    """Any other size, for tile-edge and ragged-tail tests."""
+    return make(f"custom N={n} D={d}", n, d, sigma, seed, sigma if noise is None else noise,
+                mixture=mixture)
+
+
+# --- layout helpers (pure data movement) ---------------------------------
+
+def packed_to_full(y_packed, n, diag=0.0, dtype=np.float32):
+    """Symmetric N x N matrix from the packed strict upper triangle."""
+    full = np.zeros((n, n), dtype=dtype)
+    iu = np.triu_indices(n, 1)
+    full[iu] = y_packed
+    full.T[iu] = y_packed
+    np.fill_diagonal(full, diag)
+    return full
+
+
+def full_to_packed(full):
+    n = full.shape[0]
+    return np.ascontiguousarray(full[np.triu_indices(n, 1)])
+
+
+def momenta(seed, n_iter, n, d):
+    """Standard-normal momenta (n_iter x N x D) and Metropolis uniforms
+    (n_iter), for runs where both sides are given the same random draws."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = rng.standard_normal((n_iter, n, d))
+    u = rng.uniform(size=n_iter)
+    return p, u
