@@ -1,0 +1,144 @@
+"""Plant plausible mistakes in copies of the oracle (on the CPU) and check that
+the pins catch every one: a dropped term, a wrong sign, a wrong index, a
+transposed operand, a wrong constant, the half-step drift of the printed
+Hamiltonian dynamics, and a wrong Philox multiplier."""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.spatial.distance import pdist
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mds_oracle.c")
+
+MUTANTS = {
+    "drop_log_phi": ("return e * e / (2.0 * sigma * sigma) + log_std_normal_cdf(delta / sigma);",
+                     "return e * e / (2.0 * sigma * sigma);"),
+    "sign_log_phi": ("return e * e / (2.0 * sigma * sigma) + log_std_normal_cdf(delta / sigma);",
+                     "return e * e / (2.0 * sigma * sigma) - log_std_normal_cdf(delta / sigma);"),
+    "sigma_sq_not_doubled": ("return e * e / (2.0 * sigma * sigma) + log_std_normal_cdf",
+                             "return e * e / (sigma * sigma) + log_std_normal_cdf"),
+    "row_order_reversed": ("nsum_add(&s, r_term((double)yp[packed_index(n, i, j)]",
+                           "nsum_add(&s, r_term((double)yp[i * n - i * (i + 1) / 2 + (n - 1 - j)]"),
+    "drop_m_log_sigma": ("*loglik = -m * log(sigma) - sr;", "*loglik = -sr;"),
+    "grad_sign": ("nsum_add(&g[k], -term);", "nsum_add(&g[k], term);"),
+    "grad_wrong_operand": ("double term = w * (x[i * d + k] - x[j * d + k]) / delta;",
+                           "double term = w * (x[i * d + k] - x[j * d + 0]) / delta;"),
+    "grad_drop_mills": ("return (delta - y) / (sigma * sigma) + std_normal_pdf(z) / (sigma * std_normal_cdf(z));",
+                        "return (delta - y) / (sigma * sigma);"),
+    "grad_wrong_y": ("double w = grad_factor(y_at(yp, n, i, j), delta, sigma);",
+                     "double w = grad_factor(y_at(yp, n, i, (j + 1) % n == i ? j : (j + 1) % n), delta, sigma);"),
+    "dsigma_drop_m": ("*dsigma = -m / sigma + nsum_get(&tot);", "*dsigma = nsum_get(&tot);"),
+    "dsigma_sign_mills": ("std_normal_pdf(z) * delta / (sigma * sigma * std_normal_cdf(z));",
+                          "-std_normal_pdf(z) * delta / (sigma * sigma * std_normal_cdf(z));"),
+    "half_step_drift": ("for (int64_t k = 0; k < nd; ++k) x[k] += eps * p[k];",
+                        "for (int64_t k = 0; k < nd; ++k) x[k] += 0.5 * eps * p[k];"),
+    "philox_multiplier": ("uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];",
+                          "uint64_t p1 = (uint64_t)0xCD9E8D57u * c[1];"),
+}
+
+_i64, _int, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+def _build(tmp_path, name, src_text):
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"{name}.so"
+    c.write_text(src_text)
+    subprocess.run(["gcc", "-O1", "-std=c99", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC",
+                    "-shared", str(c), "-o", str(so), "-lm"], check=True)
+    lib = ctypes.CDLL(str(so))
+    lib.mdso_loglik.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp, _vp]
+    lib.mdso_gradient_rows.argtypes = [_i64, _int, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp]
+    lib.mdso_dsigma.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp]
+    lib.mdso_leapfrog.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _int, _vp, _vp]
+    lib.mdso_philox4x32_10.argtypes = [_vp, _vp, _vp]
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_vp)
+
+
+def _pins_hold(lib):
+    """The pins of test_oracle_pins.py, condensed; True iff all hold."""
+    rng = np.random.default_rng(99)
+    n, d, s = 9, 2, 0.7
+    x = rng.standard_normal((n, d))
+    y = np.abs(pdist(x) + 0.5 * rng.standard_normal(n * (n - 1) // 2)).astype(np.float32)
+
+    def ll(xx, ss=s):
+        out = np.zeros(1)
+        lib.mdso_loglik(n, d, _p(y), _p(np.ascontiguousarray(xx)), ss, 1, None, _p(out))
+        return out[0]
+
+    dl = pdist(x)
+    ref = stats.truncnorm.logpdf(y.astype(np.float64), -dl / s, np.inf, loc=dl, scale=s).sum() \
+        + 0.5 * len(dl) * math.log(2 * math.pi)
+    if not math.isclose(ll(x), ref, rel_tol=1e-12):
+        return False
+    g = np.zeros((n, d))
+    lib.mdso_gradient_rows(n, d, _p(y), _p(x), s, None, 0, 1, _p(g), None)
+    h = 1e-6
+    for i in range(n):
+        for k in range(d):
+            xp = x.copy(); xp[i, k] += h
+            xm = x.copy(); xm[i, k] -= h
+            if not math.isclose(g[i, k], (ll(xp) - ll(xm)) / (2 * h), rel_tol=1e-5, abs_tol=1e-6):
+                return False
+    ds = np.zeros(1)
+    lib.mdso_dsigma(n, d, _p(y), _p(x), s, 1, _p(ds))
+    if not math.isclose(ds[0], (ll(x, s + h) - ll(x, s - h)) / (2 * h), rel_tol=1e-6):
+        return False
+    # harmonic oscillator closed form
+    lam, eps, steps = 1.0, 0.1, 5
+    xx = rng.standard_normal((4, 2)); pp = rng.standard_normal((4, 2))
+    a = np.array([[1 - eps * eps * lam / 2, eps], [-eps * lam * (1 - eps * eps * lam / 4), 1 - eps * eps * lam / 2]])
+    an = np.linalg.matrix_power(a, steps)
+    x1, p1 = xx.copy(), pp.copy()
+    hh = np.zeros(2)
+    lib.mdso_leapfrog(4, 2, None, _p(x1), _p(p1), 1.0, 0.0, lam, eps, steps, 1, _p(hh), _p(hh[1:]))
+    if not np.allclose(x1, an[0, 0] * xx + an[0, 1] * pp, rtol=1e-12, atol=1e-13):
+        return False
+    # Philox blocks against a fresh cuRAND host Philox generator (counter (0,0,k,0))
+    ref = _curand_blocks(0x0123456789ABCDEF, 4)
+    if ref is not None:
+        for k in range(4):
+            o = np.zeros(4, dtype=np.uint32)
+            lib.mdso_philox4x32_10(_p(np.array([0, 0, k, 0], dtype=np.uint32)),
+                                   _p(np.array([0x89ABCDEF, 0x01234567], dtype=np.uint32)), _p(o))
+            if not np.array_equal(o, ref[4 * k:4 * k + 4]):
+                return False
+    return True
+
+
+def _curand_blocks(seed, nblocks):
+    try:
+        cr = ctypes.CDLL("/usr/local/cuda/lib64/libcurand.so")
+    except OSError:
+        return None
+    gen = ctypes.c_void_p()
+    if cr.curandCreateGeneratorHost(ctypes.byref(gen), 161) != 0:
+        return None
+    try:
+        cr.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed))
+        out = np.zeros(4 * nblocks, dtype=np.uint32)
+        cr.curandGenerate(gen, _p(out), ctypes.c_size_t(out.size))
+        return out
+    finally:
+        cr.curandDestroyGenerator(gen)
+
+
+def test_unmutated_oracle_passes(tmp_path):
+    assert _pins_hold(_build(tmp_path, "orig", open(SRC).read()))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site for {name} not unique"
+    assert not _pins_hold(_build(tmp_path, name, text.replace(old, new)))
