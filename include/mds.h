@@ -1,0 +1,206 @@
+/*
+ * mds.h -- C ABI of the GB300 (sm_103a) library for the hot path of Bayesian
+ * multidimensional scaling fitted by Hamiltonian Monte Carlo
+ * (Holbrook et al., "Massive parallelization boosts big Bayesian
+ * multidimensional scaling", arXiv:1905.04582).
+ *
+ * Model (section 2.1, Eq. (1)-(2)).  N items with latent locations
+ * x_i in R^D, observed dissimilarities y_ij >= 0 (i != j, symmetric),
+ * y_ij ~ N(delta_ij, sigma^2) truncated to y_ij > 0, delta_ij = ||x_i - x_j||.
+ * The library evaluates, over the M = N(N-1)/2 pairs i < j,
+ *
+ *   L(X, sigma) = -M log sigma - sum_{i<j} r_ij,
+ *   r_ij        = (y_ij - delta_ij)^2 / (2 sigma^2) + log Phi(delta_ij / sigma),
+ *   dL/dx_i     = -sum_{j != i} [ (delta_ij - y_ij)/sigma^2
+ *                                 + phi(delta_ij/sigma) / (sigma Phi(delta_ij/sigma)) ]
+ *                              (x_i - x_j) / delta_ij                  (Eq. (9)),
+ *   dL/dsigma   = -M/sigma + sum_{i<j} [ (y_ij - delta_ij)^2 / sigma^3
+ *                                 + phi(z_ij) delta_ij / (sigma^2 Phi(z_ij)) ]
+ *                 (Eq. (2) differentiated in sigma; not printed in the paper),
+ *
+ * in ONE fused pass over the pairs (section 2.5: the per-pair terms are a
+ * transformation, their sums a reduction, and nothing per pair is stored).
+ * L keeps the sigma^(-M) factor of Eq. (2) and drops the (2 pi)^(-M/2)
+ * constant.  Coincident points (delta_ij = 0) contribute r_ij at delta = 0
+ * and nothing to the gradient.
+ *
+ * HMC (section 2.3, Eq. (6)-(8)) uses the identity mass matrix: the target is
+ * log pi(X) = L(X, sigma) - (lambda/2) ||X||_F^2 (lambda >= 0, default 0),
+ * H = -log pi(X) + p^T p / 2, leapfrog steps
+ *   p += eps/2 grad;  x += eps p;  p += eps/2 grad,
+ * and a proposal is accepted when log u < H(start) - H(end).
+ *
+ * Conventions for every call:
+ *   - Return value: MDS_OK (0) or an MDS_ERR_* code; mds_last_error() then
+ *     gives a one-line message.  No call aborts the process or throws across
+ *     the ABI.  After MDS_ERR_CUDA the context must be destroyed.
+ *   - Sizes and offsets are 64-bit.  All matrices are row-major, contiguous.
+ *   - `where` says whether a caller pointer is host (MDS_HOST) or device
+ *     (MDS_DEVICE) memory.  Caller buffers are never retained: inputs are
+ *     copied in, outputs copied out; the caller keeps ownership.
+ *   - Work is enqueued on the context's stream (mds_set_stream; default: the
+ *     legacy default stream).  Calls that return host values synchronise that
+ *     stream before returning; calls whose outputs are device buffers are
+ *     asynchronous.
+ *   - One context per host thread; contexts are independent.
+ *   - Results are bitwise reproducible for a fixed context configuration
+ *     (precision, tile strip length): every reduction has a fixed order and
+ *     no floating-point atomics are used.
+ */
+#ifndef MDS_H_
+#define MDS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define MDS_OK 0
+#define MDS_ERR_INVALID_ARG 1 /* bad pointer, size, enum, or non-finite / negative input */
+#define MDS_ERR_STATE 2       /* call order: e.g. evaluation before mds_set_data */
+#define MDS_ERR_CUDA 3        /* a CUDA runtime call failed; destroy the context */
+#define MDS_ERR_OOM 4         /* device or host allocation failed */
+#define MDS_ERR_TIMEOUT 5     /* a bounded device-side wait gave up */
+#define MDS_ERR_NONFINITE 6   /* a result was NaN/Inf (reported, not hidden) */
+#define MDS_ERR_UNSUPPORTED 7 /* no sm_100-family GPU, or a size beyond the limits */
+
+/* mds_create flags: arithmetic of the pair pass. */
+#define MDS_PREC_FP32C 0u /* FP32 per-pair math, compensated FP32 partials reduced in FP64 */
+#define MDS_PREC_FP64 1u  /* FP64 per-pair math and sums (the plain FP64 GPU path) */
+
+/* Element types of caller buffers. */
+#define MDS_F32 0
+#define MDS_F64 1
+
+/* Where a caller buffer lives. */
+#define MDS_HOST 0
+#define MDS_DEVICE 1
+
+/* Layouts of Y for mds_set_data. */
+#define MDS_Y_FULL 0         /* N x N row-major, leading dimension ld >= N */
+#define MDS_Y_PACKED_UPPER 1 /* M entries (0,1),(0,2),...,(0,N-1),(1,2),...,(N-2,N-1) */
+
+/* Limits. */
+#define MDS_MAX_D 8
+
+typedef struct mds_ctx mds_ctx;
+
+/* Create a context for N items in D latent dimensions (2 <= N <= 2^31 - 1,
+ * 1 <= D <= MDS_MAX_D) on the current CUDA device.  flags: MDS_PREC_FP32C
+ * (default) or MDS_PREC_FP64.  Allocates the device state (tile-packed Y:
+ * about 4 M bytes; locations, momenta, gradients and partial sums: O(N D)
+ * plus about D/16 of the Y bytes).  *out receives the context, owned by the
+ * library until mds_destroy.  Errors: INVALID_ARG, UNSUPPORTED (device is not
+ * compute capability 10.x), OOM, CUDA. */
+int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out);
+
+/* Free the context and all its device memory.  NULL is allowed. */
+int mds_destroy(mds_ctx *ctx);
+
+/* Enqueue all later work of `ctx` on `stream` (a cudaStream_t, e.g. torch's
+ * current stream); NULL selects the legacy default stream. */
+int mds_set_stream(mds_ctx *ctx, void *stream);
+
+/* Set the observed dissimilarities Y (section 2.1; symmetric, section 2.2).
+ * dtype MDS_F32 or MDS_F64; layout MDS_Y_FULL (ld = row stride in elements,
+ * ld >= N; only the strict upper triangle i < j is read, the diagonal and the
+ * lower triangle are ignored) or MDS_Y_PACKED_UPPER (ld ignored).  Values are
+ * rounded once to FP32 and re-packed into the library's tile layout.
+ * Errors: INVALID_ARG if any read entry is negative, NaN or Inf (the message
+ * names the first offending (i, j)); the previous Y stays in place then. */
+int mds_set_data(mds_ctx *ctx, const void *y, int dtype, int layout, int64_t ld, int where);
+
+/* Set the latent locations X (N x D row-major, dtype MDS_F32 or MDS_F64).
+ * The FP32C path keeps X in FP32, the FP64 path in FP64.  Errors:
+ * INVALID_ARG for a non-finite entry. */
+int mds_set_locations(mds_ctx *ctx, const void *x, int dtype, int where);
+
+/* Copy the current locations out (N x D row-major). */
+int mds_get_locations(mds_ctx *ctx, void *x, int dtype, int where);
+
+/* Set sigma (> 0, finite; the FP32C path accepts 1e-6 <= sigma <= 1e6). */
+int mds_set_sigma(mds_ctx *ctx, double sigma);
+
+/* Set the isotropic Gaussian prior precision lambda >= 0 of the HMC target
+ * (default 0: the target is the likelihood alone). */
+int mds_set_prior(mds_ctx *ctx, double lambda);
+
+/* Log-likelihood L(X, sigma) of Eq. (2) (incl. -M log sigma).  sum_r
+ * (optional) receives sum_{i<j} r_ij.  Synchronises.  Errors: STATE before
+ * set_data / set_locations / set_sigma; NONFINITE. */
+int mds_log_likelihood(mds_ctx *ctx, double *loglik, double *sum_r);
+
+/* One fused pass: L (optional), the gradient dL/dX of Eq. (9) into `grad`
+ * (N x D row-major, dtype MDS_F32/MDS_F64, host or device; optional) and
+ * dL/dsigma (optional).  Synchronises when any output is on the host. */
+int mds_gradient(mds_ctx *ctx, double *loglik, void *grad, int dtype, int where,
+                 double *dlogl_dsigma);
+
+/* Set / get the HMC momentum p (N x D). */
+int mds_set_momentum(mds_ctx *ctx, const void *p, int dtype, int where);
+int mds_get_momentum(mds_ctx *ctx, void *p, int dtype, int where);
+
+/* Advance (x, p) in place by n_steps >= 0 leapfrog steps of size eps
+ * (section 2.3, Eq. (7) with M = I), entirely on the device.  p0 (optional,
+ * N x D) replaces the momentum first.  dh (optional) receives
+ * H(end) - H(start) in FP64.  No Metropolis step.  Synchronises when dh is
+ * requested. */
+int mds_leapfrog(mds_ctx *ctx, int n_steps, double eps, const void *p0, int p0_dtype,
+                 int p0_where, double *dh);
+
+/* Statistics of an mds_hmc run. */
+typedef struct mds_hmc_stats {
+    int64_t iterations; /* iterations run */
+    int64_t accepted;   /* proposals accepted */
+    double last_dh;     /* H(end) - H(start) of the last iteration */
+    double last_loglik; /* L at the state after the last iteration */
+} mds_hmc_stats;
+
+/* n_iter HMC iterations of n_steps leapfrog steps each (step size eps), on
+ * the device, captured once into a CUDA graph and replayed.  Momenta and
+ * uniforms come from the Philox4x32-10 stream keyed by `seed` (counter
+ * layout: element e of iteration t uses counter (e/4, t0+t, chain, 0), the
+ * uniform counter (0, t0+t, chain, 1), chain = 0, t0 = iterations run so far
+ * by this context), unless p_all (n_iter x N x D, FP64, host) and u_all
+ * (n_iter uniforms in (0,1), FP64, host) are given, which makes runs
+ * comparable with an external implementation.  accepted (optional, n_iter
+ * ints, host) and dh (optional, n_iter doubles, host) receive per-iteration
+ * results.  Synchronises.  Errors: NONFINITE if an energy was not finite (the
+ * proposal is then rejected and the run continues). */
+int mds_hmc(mds_ctx *ctx, int n_iter, int n_steps, double eps, uint64_t seed, const double *p_all,
+            const double *u_all, int *accepted, double *dh, mds_hmc_stats *stats);
+
+/* Number of pairs M = N(N-1)/2 and the bytes of tile-packed Y resident on
+ * the device. */
+int mds_problem_size(const mds_ctx *ctx, int64_t *pairs, int64_t *y_bytes);
+
+/* Tile strip length S (tiles of 64 x 64 pairs processed by one CTA).  0 picks
+ * the autotuned value for this (GPU, N, D, precision).  Changing it changes
+ * the summation order (results stay within tolerance but not bit-identical). */
+int mds_set_strip(mds_ctx *ctx, int32_t strip);
+int mds_get_strip(const mds_ctx *ctx, int32_t *strip);
+
+/* Time the fused pass: run `reps` evaluations back to back on the context's
+ * stream and return the mean milliseconds per pass (CUDA events). */
+int mds_time_pass(mds_ctx *ctx, int reps, double *ms_per_pass);
+
+/* Kernel timing of the pair pass inside real work (benchmarks): while
+ * profiling is on, every pair-pass launch -- also inside the CUDA graphs of
+ * mds_hmc -- is bracketed by two CUDA events on the context's stream, and
+ * mds_hmc synchronises after each iteration to read them.
+ * mds_get_pass_time returns the number of timed launches and their total
+ * milliseconds since profiling was switched on. */
+int mds_set_profiling(mds_ctx *ctx, int on);
+int mds_get_pass_time(const mds_ctx *ctx, int64_t *launches, double *total_ms);
+
+/* Message of the last failed call on ctx (or of the last failed mds_create
+ * in this thread when ctx is NULL).  Never NULL. */
+const char *mds_last_error(const mds_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDS_H_ */

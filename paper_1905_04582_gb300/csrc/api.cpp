@@ -1,0 +1,1015 @@
+// Host runtime of the C ABI declared in include/mds.h: argument checks,
+// device state, the tile/strip work list, the strip-length autotuner, kernel
+// launches, CUDA-graph capture of HMC iterations, and error reporting.
+#include "mds.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "mds_internal.h"
+#include "mills_ratio_coeffs.h"
+
+using namespace mds;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mds_ctx {
+    int64_t n = 0;
+    int32_t d = 0;
+    bool fp64 = false;
+    int device = 0;
+    int sm_count = 0;
+    std::string device_name;
+    int64_t nt = 0;
+    int64_t n_pad = 0;
+    int64_t tiles = 0;
+    int32_t strip = 0;        // in use
+    int32_t strip_req = 0;    // 0 = autotune
+    int32_t n_strips = 0;
+    int32_t n_row_slots = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double sigma = 0.0;
+    double lambda = 0.0;
+    bool have_data = false, have_x = false, have_sigma = false, grad_valid = false;
+    uint64_t gen = 1;         // bumps whenever captured kernel arguments would change
+    int start_grid = 0;
+
+    // device buffers
+    float *y = nullptr;
+    void *x = nullptr, *xneg = nullptr, *p = nullptr, *x0 = nullptr;
+    double *grad = nullptr, *grad0 = nullptr;
+    void *col_part = nullptr;
+    double *row_part = nullptr;
+    size_t row_part_bytes = 0;
+    double *scal_part = nullptr;
+    size_t scal_part_bytes = 0;
+    Strip *strips = nullptr;
+    size_t strips_bytes = 0;
+    int32_t *row_first = nullptr;
+    double *scal = nullptr;
+    int64_t *counters = nullptr;
+    unsigned *err = nullptr;
+    unsigned long long *bad = nullptr;
+    double *e_start = nullptr, *e_end = nullptr;
+    void *stage = nullptr;    // conversion staging (n_pad * D doubles)
+    double *p_inj = nullptr;
+    size_t p_inj_bytes = 0;
+    double *u_inj = nullptr;
+    size_t u_inj_bytes = 0;
+    int32_t *acc_out = nullptr;
+    double *dh_out = nullptr;
+    size_t out_cap = 0;
+
+    // pair-pass timing (mds_set_profiling)
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_a, prof_b;
+    int prof_used = 0;        // event pairs recorded since the last harvest
+    int64_t prof_launches = 0;
+    double prof_ms = 0.0;
+
+    // graph cache (one HMC iteration)
+    cudaGraphExec_t graph = nullptr;
+    std::tuple<uint64_t, int, double, int, int, uint64_t, int> graph_key{};
+    int graph_prof = 0;       // event pairs inside the captured graph
+
+    std::string last_error = "no error";
+};
+
+namespace {
+
+int fail(mds_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->last_error = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(c, MDS_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                      \
+    } while (0)
+
+#define CHECK(st)                        \
+    do {                                 \
+        int s_ = (st);                   \
+        if (s_ != MDS_OK) return s_;     \
+    } while (0)
+
+int dev_alloc(mds_ctx *c, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, MDS_ERR_OOM, "cudaMalloc of %zu bytes failed: out of device memory", bytes);
+    }
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    return MDS_OK;
+}
+
+template <typename P>
+int dev_alloc_t(mds_ctx *c, P **p, size_t bytes) {
+    void *v = nullptr;
+    int st = dev_alloc(c, &v, bytes);
+    *p = static_cast<P *>(v);
+    return st;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+size_t elem(const mds_ctx *c) { return c->fp64 ? sizeof(double) : sizeof(float); }
+
+int check_ctx(mds_ctx *c) {
+    if (!c) return MDS_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return MDS_OK;
+}
+
+// Read and clear the device error word; map it to a status.
+int check_device_err(mds_ctx *c, const char *what) {
+    unsigned h = 0;
+    CU(cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h == 0) return MDS_OK;
+    CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h & kErrTimeout) return fail(c, MDS_ERR_TIMEOUT, "%s: a device-side wait timed out", what);
+    if (h & kErrBadArgs) return fail(c, MDS_ERR_CUDA, "%s: kernel argument check failed", what);
+    if (h & kErrNonfinite) return fail(c, MDS_ERR_NONFINITE, "%s: non-finite result (NaN/Inf)", what);
+    return fail(c, MDS_ERR_INVALID_ARG, "%s: invalid input value", what);
+}
+
+// ---------------------------------------------------------------- strips
+
+int build_strips(mds_ctx *c, int strip) {
+    const int64_t nt = c->nt;
+    std::vector<Strip> v;
+    std::vector<int32_t> first(nt + 1, 0);
+    int32_t slot = 0;
+    for (int64_t I = 0; I < nt; ++I) {
+        first[I] = slot;
+        for (int64_t j0 = I; j0 < nt; j0 += strip) {
+            Strip s;
+            s.I = static_cast<int32_t>(I);
+            s.j0 = static_cast<int32_t>(j0);
+            s.j1 = static_cast<int32_t>(std::min<int64_t>(nt, j0 + strip));
+            s.row_slot = slot++;
+            v.push_back(s);
+        }
+    }
+    first[nt] = slot;
+    // largest strips first: blocks are dispatched roughly in index order, so
+    // this approximates longest-processing-time-first scheduling
+    std::stable_sort(v.begin(), v.end(), [](const Strip &a, const Strip &b) {
+        return (a.j1 - a.j0) > (b.j1 - b.j0);
+    });
+    const size_t sb = v.size() * sizeof(Strip);
+    if (sb > c->strips_bytes) {
+        dev_free(c->strips);
+        c->strips = nullptr;
+        CHECK(dev_alloc_t(c, &c->strips, sb));
+        c->strips_bytes = sb;
+    }
+    const size_t rb = static_cast<size_t>(slot) * kTile * c->d * sizeof(double);
+    if (rb > c->row_part_bytes) {
+        dev_free(c->row_part);
+        c->row_part = nullptr;
+        CHECK(dev_alloc_t(c, &c->row_part, rb));
+        c->row_part_bytes = rb;
+    }
+    const size_t spb = v.size() * kScalarParts * sizeof(double);
+    if (spb > c->scal_part_bytes) {
+        dev_free(c->scal_part);
+        c->scal_part = nullptr;
+        CHECK(dev_alloc_t(c, &c->scal_part, spb));
+        c->scal_part_bytes = spb;
+    }
+    CU(cudaMemcpyAsync(c->strips, v.data(), sb, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->row_first, first.data(), (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->n_strips = static_cast<int32_t>(v.size());
+    c->n_row_slots = slot;
+    c->strip = strip;
+    c->gen++;
+    return MDS_OK;
+}
+
+int max_strip_for_smem(const mds_ctx *c) {
+    int s = 1;
+    while (s < 64 && pair_smem_bytes(c->d, s + 1, c->fp64) <= 40 * 1024) ++s;
+    return s;
+}
+
+// --------------------------------------------------------------- passes
+
+PairArgs pair_args(const mds_ctx *c) {
+    PairArgs a{};
+    a.y = c->y;
+    a.xrow = c->x;
+    a.xneg = c->xneg;
+    a.strips = c->strips;
+    a.n_strips = c->n_strips;
+    a.nt = static_cast<int32_t>(c->nt);
+    a.n = c->n;
+    a.row_part = c->row_part;
+    a.col_part = c->col_part;
+    a.scal_part = c->scal_part;
+    a.err = c->err;
+    const double s = c->sigma;
+    const double inv_sqrt_2pi = 0.39894228040143267794;
+    double sk = 1.0;
+    for (int k = 0; k < 4; ++k) {
+        const float pv = static_cast<float>(-kMillsP[k] * inv_sqrt_2pi / sk);
+        const float dv = static_cast<float>(kMillsD[k] / sk);
+        a.mp[k] = make_float2(pv, pv);
+        a.md[k] = make_float2(dv, dv);
+        sk *= s;
+    }
+    const float cphi = static_cast<float>(-1.4426950408889634074 / (2.0 * s * s));
+    const float nis2 = static_cast<float>(-1.0 / (s * s));
+    const float mc = static_cast<float>(inv_sqrt_2pi / s);
+    a.c_phi = make_float2(cphi, cphi);
+    a.neg_inv_s2 = make_float2(nis2, nis2);
+    a.m_coef = make_float2(mc, mc);
+    a.sigma = s;
+    a.inv_sigma = 1.0 / s;
+    a.inv_s2 = 1.0 / (s * s);
+    return a;
+}
+
+ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
+    ReduceArgs r{};
+    r.row_part = c->row_part;
+    r.col_part = c->col_part;
+    r.scal_part = c->scal_part;
+    r.row_first_slot = c->row_first;
+    r.n_strips = c->n_strips;
+    r.nt = static_cast<int32_t>(c->nt);
+    r.n = c->n;
+    r.d = c->d;
+    r.mode = mode;
+    r.fp64 = c->fp64;
+    r.sigma = c->sigma;
+    r.lambda = c->lambda;
+    r.eps = eps;
+    r.grad = c->grad;
+    r.scal = c->scal;
+    r.x = c->x;
+    r.xneg = c->xneg;
+    r.p = c->p;
+    r.energy_part = c->e_end;
+    r.err = c->err;
+    return r;
+}
+
+int record_prof(mds_ctx *c, cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusActive)
+        CU(cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal));
+    else
+        CU(cudaEventRecord(ev, s));
+    return MDS_OK;
+}
+
+// Add the elapsed times of the event pairs recorded since the last harvest
+// (their work must have completed).
+int harvest_prof(mds_ctx *c) {
+    for (int k = 0; k < c->prof_used; ++k) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, c->prof_a[k], c->prof_b[k]));
+        c->prof_ms += ms;
+        c->prof_launches++;
+    }
+    c->prof_used = 0;
+    return MDS_OK;
+}
+
+int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s) {
+    PairArgs a = pair_args(c);
+    const int pk = c->prof_used;
+    if (c->profiling) {
+        while (static_cast<int>(c->prof_a.size()) <= pk) {
+            cudaEvent_t ea, eb;
+            CU(cudaEventCreate(&ea));
+            CU(cudaEventCreate(&eb));
+            c->prof_a.push_back(ea);
+            c->prof_b.push_back(eb);
+        }
+        CHECK(record_prof(c, c->prof_a[pk], s));
+    }
+    cudaError_t e = c->fp64 ? launch_pair_pass_f64(a, c->d, c->strip, s) : launch_pair_pass_f32(a, c->d, c->strip, s);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
+    if (c->profiling) {
+        CHECK(record_prof(c, c->prof_b[pk], s));
+        c->prof_used = pk + 1;
+    }
+    ReduceArgs r = reduce_args(c, mode, eps);
+    e = launch_reduce(r, s);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(e));
+    return MDS_OK;
+}
+
+int ready(mds_ctx *c) {
+    if (!c->have_data) return fail(c, MDS_ERR_STATE, "no data: call mds_set_data first");
+    if (!c->have_x) return fail(c, MDS_ERR_STATE, "no locations: call mds_set_locations first");
+    if (!c->have_sigma) return fail(c, MDS_ERR_STATE, "no sigma: call mds_set_sigma first");
+    return MDS_OK;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<std::string, int64_t, int, bool>, int> g_tune_cache;
+
+// Pick the strip length by timing the pass for a few candidates (once per
+// process and (GPU, N, D, precision)); MDS_STRIP in the environment forces it.
+int autotune(mds_ctx *c) {
+    if (c->strip_req > 0) {
+        if (c->strip != c->strip_req) CHECK(build_strips(c, c->strip_req));
+        return MDS_OK;
+    }
+    if (const char *env = getenv("MDS_STRIP")) {
+        const int s = atoi(env);
+        if (s > 0) {
+            if (c->strip != s) CHECK(build_strips(c, std::min(s, max_strip_for_smem(c))));
+            return MDS_OK;
+        }
+    }
+    const auto key = std::make_tuple(c->device_name, c->n, static_cast<int>(c->d), c->fp64);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            if (c->strip != it->second) CHECK(build_strips(c, it->second));
+            return MDS_OK;
+        }
+    }
+    const int smax = max_strip_for_smem(c);
+    std::vector<int> cands;
+    for (int s : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+        if (s > smax || s > c->nt) continue;
+        const int64_t strips_est = (c->tiles + s - 1) / s;
+        // keep enough CTAs for every SM, unless the problem is tiny anyway
+        if (!cands.empty() && strips_est < 2 * c->sm_count) continue;
+        cands.push_back(s);
+    }
+    if (cands.empty()) cands.push_back(1);
+    int best = cands[0];
+    float best_ms = 1e30f;
+    const bool prof = c->profiling;
+    c->profiling = false;
+    if (cands.size() > 1) {
+        for (int s : cands) {
+            CHECK(build_strips(c, s));
+            for (int w = 0; w < 2; ++w) CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+            CU(cudaEventRecord(c->ev0, c->stream));
+            const int reps = 5;
+            for (int w = 0; w < reps; ++w) CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+            CU(cudaEventRecord(c->ev1, c->stream));
+            CU(cudaEventSynchronize(c->ev1));
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = s;
+            }
+        }
+        CHECK(check_device_err(c, "autotune"));
+    }
+    c->profiling = prof;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if (c->strip != best) CHECK(build_strips(c, best));
+    return MDS_OK;
+}
+
+// Evaluate at the current x (gradient + scalars) and wait.
+int evaluate(mds_ctx *c) {
+    CHECK(ready(c));
+    CHECK(autotune(c));
+    CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+    CU(cudaGetLastError());
+    CHECK(check_device_err(c, "evaluation"));
+    if (c->profiling) CHECK(harvest_prof(c));
+    c->grad_valid = true;
+    return MDS_OK;
+}
+
+int copy_out(mds_ctx *c, const void *dev_src, bool src_f64, void *dst, int dtype, int where, int64_t count) {
+    const bool dst_f64 = dtype == MDS_F64;
+    const size_t eb = dst_f64 ? 8 : 4;
+    if (where == MDS_DEVICE) {
+        cudaError_t e = launch_convert(dev_src, src_f64, dst, dst_f64, count, c->stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "convert: %s", cudaGetErrorString(e));
+        return MDS_OK;
+    }
+    cudaError_t e = launch_convert(dev_src, src_f64, c->stage, dst_f64, count, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "convert: %s", cudaGetErrorString(e));
+    CU(cudaMemcpyAsync(dst, c->stage, count * eb, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return MDS_OK;
+}
+
+// Bring a caller N x D array (host or device, f32/f64) onto the device;
+// returns a device pointer (the caller's or the staging buffer).
+int stage_in(mds_ctx *c, const void *src, int dtype, int where, int64_t count, const void **dev) {
+    const size_t eb = dtype == MDS_F64 ? 8 : 4;
+    if (where == MDS_DEVICE) {
+        *dev = src;
+        return MDS_OK;
+    }
+    CU(cudaMemcpyAsync(c->stage, src, count * eb, cudaMemcpyHostToDevice, c->stream));
+    *dev = c->stage;
+    return MDS_OK;
+}
+
+int valid_enums(mds_ctx *c, int dtype, int where) {
+    if (dtype != MDS_F32 && dtype != MDS_F64) return fail(c, MDS_ERR_INVALID_ARG, "dtype must be MDS_F32 or MDS_F64");
+    if (where != MDS_HOST && where != MDS_DEVICE)
+        return fail(c, MDS_ERR_INVALID_ARG, "where must be MDS_HOST or MDS_DEVICE");
+    return MDS_OK;
+}
+
+// Enqueue one trajectory: start kernel, n_steps fused pair passes with their
+// leapfrog updates, end kernel (Metropolis when metropolis != 0).
+int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, int u_src, int metropolis,
+                       uint64_t seed, cudaStream_t s) {
+    TrajArgs t{};
+    t.n = c->n;
+    t.d = c->d;
+    t.fp64 = c->fp64;
+    t.eps = eps;
+    t.lambda = c->lambda;
+    t.momentum_src = momentum_src;
+    t.p_inj = c->p_inj;
+    t.seed = seed;
+    t.chain = 0;
+    t.x = c->x;
+    t.xneg = c->xneg;
+    t.p = c->p;
+    t.x0 = c->x0;
+    t.grad = c->grad;
+    t.grad0 = c->grad0;
+    t.scal = c->scal;
+    t.counters = c->counters;
+    t.energy_part = c->e_start;
+    t.drift = n_steps > 0 ? 1 : 0;
+    int grid = 0;
+    cudaError_t e = launch_traj_start(t, &grid, s);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "trajectory start: %s", cudaGetErrorString(e));
+    c->start_grid = grid;
+    for (int k = 0; k < n_steps; ++k)
+        CHECK(enqueue_pass(c, k + 1 < n_steps ? kModeKickDrift : kModeHalfKick, eps, s));
+    AcceptArgs a{};
+    a.n = c->n;
+    a.d = c->d;
+    a.fp64 = c->fp64;
+    a.metropolis = metropolis;
+    a.n_start_parts = grid;
+    a.start_part = c->e_start;
+    if (n_steps > 0) {
+        a.n_end_parts = static_cast<int32_t>(c->nt);
+        a.end_part = c->e_end;
+    } else {
+        a.n_end_parts = grid;
+        a.end_part = c->e_start;
+    }
+    a.lambda = c->lambda;
+    a.u_src = u_src;
+    a.u_inj = c->u_inj;
+    a.seed = seed;
+    a.chain = 0;
+    a.x = c->x;
+    a.xneg = c->xneg;
+    a.x0 = c->x0;
+    a.grad = c->grad;
+    a.grad0 = c->grad0;
+    a.scal = c->scal;
+    a.counters = c->counters;
+    // per-iteration outputs only for Metropolis runs (their index is the
+    // iteration within the current mds_hmc call, below out_cap)
+    a.acc_out = metropolis ? c->acc_out : nullptr;
+    a.dh_out = metropolis ? c->dh_out : nullptr;
+    a.err = c->err;
+    e = launch_traj_end(a, s);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "trajectory end: %s", cudaGetErrorString(e));
+    return MDS_OK;
+}
+
+int ensure_out_cap(mds_ctx *c, size_t n_iter) {
+    if (n_iter <= c->out_cap) return MDS_OK;
+    dev_free(c->acc_out);
+    dev_free(c->dh_out);
+    c->acc_out = nullptr;
+    c->dh_out = nullptr;
+    CHECK(dev_alloc_t(c, &c->acc_out, n_iter * sizeof(int32_t)));
+    CHECK(dev_alloc_t(c, &c->dh_out, n_iter * sizeof(double)));
+    c->out_cap = n_iter;
+    c->gen++;
+    return MDS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out) {
+    mds_ctx *c = nullptr;
+    if (!out) return fail(c, MDS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 2 || n > 2147483647LL) return fail(c, MDS_ERR_INVALID_ARG, "N must be in [2, 2^31-1], got %lld", (long long)n);
+    if (d < 1 || d > MDS_MAX_D) return fail(c, MDS_ERR_INVALID_ARG, "D must be in [1, %d], got %d", MDS_MAX_D, d);
+    if (flags != MDS_PREC_FP32C && flags != MDS_PREC_FP64)
+        return fail(c, MDS_ERR_INVALID_ARG, "flags must be MDS_PREC_FP32C or MDS_PREC_FP64");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_UNSUPPORTED, "no CUDA device: %s", cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    if (prop.major != 10)
+        return fail(c, MDS_ERR_UNSUPPORTED, "device %s is compute capability %d.%d; this build needs sm_103a",
+                    prop.name, prop.major, prop.minor);
+    c = new (std::nothrow) mds_ctx();
+    if (!c) return fail(nullptr, MDS_ERR_OOM, "host allocation failed");
+    c->n = n;
+    c->d = d;
+    c->fp64 = flags == MDS_PREC_FP64;
+    c->device = dev;
+    c->sm_count = prop.multiProcessorCount;
+    c->device_name = prop.name;
+    c->nt = (n + kTile - 1) / kTile;
+    c->n_pad = c->nt * kTile;
+    c->tiles = tile_count(c->nt);
+    auto cleanup = [&](int st) {
+        g_create_error = c->last_error;
+        mds_destroy(c);
+        return st;
+    };
+    const size_t eb = elem(c);
+    const int64_t nd_pad = c->n_pad * d;
+    int st = MDS_OK;
+    if ((st = dev_alloc_t(c, &c->y, static_cast<size_t>(c->tiles) * kTileElems * sizeof(float)))) return cleanup(st);
+    if ((st = dev_alloc(c, &c->x, nd_pad * eb))) return cleanup(st);
+    if ((st = dev_alloc(c, &c->xneg, nd_pad * eb))) return cleanup(st);
+    if ((st = dev_alloc(c, &c->p, nd_pad * eb))) return cleanup(st);
+    if ((st = dev_alloc(c, &c->x0, nd_pad * eb))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->grad, nd_pad * sizeof(double)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->grad0, nd_pad * sizeof(double)))) return cleanup(st);
+    if ((st = dev_alloc(c, &c->col_part, static_cast<size_t>(c->tiles) * kTile * d * eb))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->row_first, (c->nt + 1) * sizeof(int32_t)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->scal, kScalars * sizeof(double)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->counters, kCounters * sizeof(int64_t)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->err, sizeof(unsigned)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->bad, sizeof(unsigned long long)))) return cleanup(st);
+    const int64_t start_grid_max = (nd_pad + 4 * 256 - 1) / (4 * 256) + 1;
+    if ((st = dev_alloc_t(c, &c->e_start, start_grid_max * 2 * sizeof(double)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->e_end, (c->nt + 1) * 2 * sizeof(double)))) return cleanup(st);
+    if ((st = dev_alloc(c, &c->stage, nd_pad * sizeof(double)))) return cleanup(st);
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        c->last_error = "stream/event creation failed";
+        return cleanup(MDS_ERR_CUDA);
+    }
+    if (cudaMemset(c->x, 0, nd_pad * eb) != cudaSuccess || cudaMemset(c->xneg, 0, nd_pad * eb) != cudaSuccess ||
+        cudaMemset(c->p, 0, nd_pad * eb) != cudaSuccess || cudaMemset(c->grad, 0, nd_pad * 8) != cudaSuccess ||
+        cudaMemset(c->scal, 0, kScalars * 8) != cudaSuccess || cudaMemset(c->counters, 0, kCounters * 8) != cudaSuccess ||
+        cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess) {
+        c->last_error = "initial memset failed";
+        return cleanup(MDS_ERR_CUDA);
+    }
+    if ((st = build_strips(c, 1))) return cleanup(st);
+    *out = c;
+    return MDS_OK;
+}
+
+int mds_destroy(mds_ctx *c) {
+    if (!c) return MDS_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    void *bufs[] = {c->y,     c->x,        c->xneg,   c->p,        c->x0,     c->grad,    c->grad0,
+                    c->col_part, c->row_part, c->scal_part, c->strips, c->row_first, c->scal, c->counters,
+                    c->err,   c->bad,      c->e_start, c->e_end,    c->stage,  c->p_inj,   c->u_inj,
+                    c->acc_out, c->dh_out};
+    for (void *b : bufs) dev_free(b);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    for (cudaEvent_t e : c->prof_a) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->prof_b) cudaEventDestroy(e);
+    delete c;
+    return MDS_OK;
+}
+
+int mds_set_stream(mds_ctx *c, void *stream) {
+    CHECK(check_ctx(c));
+    c->stream = static_cast<cudaStream_t>(stream);
+    return MDS_OK;
+}
+
+int mds_set_data(mds_ctx *c, const void *y, int dtype, int layout, int64_t ld, int where) {
+    CHECK(check_ctx(c));
+    if (!y) return fail(c, MDS_ERR_INVALID_ARG, "Y is NULL");
+    CHECK(valid_enums(c, dtype, where));
+    if (layout != MDS_Y_FULL && layout != MDS_Y_PACKED_UPPER)
+        return fail(c, MDS_ERR_INVALID_ARG, "layout must be MDS_Y_FULL or MDS_Y_PACKED_UPPER");
+    if (layout == MDS_Y_FULL && ld < c->n) return fail(c, MDS_ERR_INVALID_ARG, "ld (%lld) < N", (long long)ld);
+    c->have_data = false;
+    c->grad_valid = false;
+    const bool f64 = dtype == MDS_F64;
+    const size_t eb = f64 ? 8 : 4;
+    const unsigned long long none = ~0ull;
+    CU(cudaMemcpyAsync(c->bad, &none, sizeof(none), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    IngestArgs a{};
+    a.src_f64 = f64;
+    a.packed = layout == MDS_Y_PACKED_UPPER;
+    a.ld = ld;
+    a.n = c->n;
+    a.nt = static_cast<int32_t>(c->nt);
+    a.y = c->y;
+    a.bad = c->bad;
+    a.err = c->err;
+    const int64_t n = c->n;
+    if (where == MDS_DEVICE) {
+        a.src = y;
+        a.r0 = 0;
+        a.r1 = n;
+        cudaError_t e = launch_ingest(a, c->stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "ingest: %s", cudaGetErrorString(e));
+    } else {
+        // host source: stage groups of row blocks through a device buffer
+        const int64_t rows_per = kTile * std::max<int64_t>(1, (int64_t(64) << 20) / (kTile * n * eb));
+        const size_t stage_bytes = static_cast<size_t>(std::min<int64_t>(rows_per, n)) * n * eb;
+        void *stg = nullptr;
+        CHECK(dev_alloc(c, &stg, stage_bytes));
+        int st = MDS_OK;
+        for (int64_t r0 = 0; r0 < n && st == MDS_OK; r0 += rows_per) {
+            const int64_t r1 = std::min(n, r0 + rows_per);
+            const char *src;
+            size_t bytes;
+            if (a.packed) {
+                const int64_t o0 = packed_row_start(r0, n), o1 = packed_row_start(r1, n);
+                src = static_cast<const char *>(y) + o0 * eb;
+                bytes = (o1 - o0) * eb;
+            } else {
+                src = static_cast<const char *>(y) + r0 * ld * eb;
+                bytes = ((r1 - r0 - 1) * ld + n) * eb;
+            }
+            if (bytes > 0) {
+                cudaError_t e = cudaMemcpyAsync(stg, src, bytes, cudaMemcpyHostToDevice, c->stream);
+                if (e != cudaSuccess) st = fail(c, MDS_ERR_CUDA, "Y upload: %s", cudaGetErrorString(e));
+            }
+            a.src = stg;
+            a.r0 = r0;
+            a.r1 = r1;
+            if (st == MDS_OK) {
+                cudaError_t e = launch_ingest(a, c->stream);
+                if (e != cudaSuccess) st = fail(c, MDS_ERR_CUDA, "ingest: %s", cudaGetErrorString(e));
+            }
+            if (st == MDS_OK) {
+                cudaError_t e = cudaStreamSynchronize(c->stream);  // staging buffer reuse
+                if (e != cudaSuccess) st = fail(c, MDS_ERR_CUDA, "ingest: %s", cudaGetErrorString(e));
+            }
+        }
+        cudaFree(stg);
+        if (st != MDS_OK) return st;
+    }
+    unsigned h = 0;
+    unsigned long long bad = 0;
+    CU(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(&bad, c->bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h & kErrBadInput) {
+        CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        return fail(c, MDS_ERR_INVALID_ARG,
+                    "Y(%llu, %llu) is negative, NaN or Inf; dissimilarities must be finite and >= 0 (no data set)",
+                    bad / static_cast<unsigned long long>(n), bad % static_cast<unsigned long long>(n));
+    }
+    if (h) return check_device_err(c, "set_data");
+    c->have_data = true;
+    return MDS_OK;
+}
+
+int mds_set_locations(mds_ctx *c, const void *x, int dtype, int where) {
+    CHECK(check_ctx(c));
+    if (!x) return fail(c, MDS_ERR_INVALID_ARG, "X is NULL");
+    CHECK(valid_enums(c, dtype, where));
+    const void *dev = nullptr;
+    CHECK(stage_in(c, x, dtype, where, c->n * c->d, &dev));
+    CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    cudaError_t e = launch_set_x(dev, dtype == MDS_F64, c->n, c->n_pad, c->d, c->fp64, c->x, c->xneg, c->err, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_locations: %s", cudaGetErrorString(e));
+    unsigned h = 0;
+    CU(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h) {
+        CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        c->have_x = false;
+        return fail(c, MDS_ERR_INVALID_ARG, "X has a NaN or Inf entry");
+    }
+    c->have_x = true;
+    c->grad_valid = false;
+    return MDS_OK;
+}
+
+int mds_get_locations(mds_ctx *c, void *x, int dtype, int where) {
+    CHECK(check_ctx(c));
+    if (!x) return fail(c, MDS_ERR_INVALID_ARG, "X is NULL");
+    CHECK(valid_enums(c, dtype, where));
+    if (!c->have_x) return fail(c, MDS_ERR_STATE, "no locations set");
+    return copy_out(c, c->x, c->fp64, x, dtype, where, c->n * c->d);
+}
+
+int mds_set_sigma(mds_ctx *c, double sigma) {
+    CHECK(check_ctx(c));
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(c, MDS_ERR_INVALID_ARG, "sigma must be finite and > 0");
+    if (!c->fp64 && (sigma < 1e-6 || sigma > 1e6))
+        return fail(c, MDS_ERR_INVALID_ARG, "the FP32C path needs 1e-6 <= sigma <= 1e6, got %g", sigma);
+    if (sigma != c->sigma) {
+        c->sigma = sigma;
+        c->grad_valid = false;
+        c->gen++;
+    }
+    c->have_sigma = true;
+    return MDS_OK;
+}
+
+int mds_set_prior(mds_ctx *c, double lambda) {
+    CHECK(check_ctx(c));
+    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(c, MDS_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    if (lambda != c->lambda) {
+        c->lambda = lambda;
+        c->gen++;
+    }
+    return MDS_OK;
+}
+
+int mds_log_likelihood(mds_ctx *c, double *loglik, double *sum_r) {
+    CHECK(check_ctx(c));
+    if (!loglik && !sum_r) return fail(c, MDS_ERR_INVALID_ARG, "no output requested");
+    if (!c->grad_valid) CHECK(evaluate(c));
+    double s[kScalars];
+    CU(cudaMemcpyAsync(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (loglik) *loglik = s[kLogLik];
+    if (sum_r) *sum_r = s[kSumR];
+    if (!std::isfinite(s[kLogLik])) return fail(c, MDS_ERR_NONFINITE, "log-likelihood is not finite");
+    return MDS_OK;
+}
+
+int mds_gradient(mds_ctx *c, double *loglik, void *grad, int dtype, int where, double *dsigma) {
+    CHECK(check_ctx(c));
+    if (grad) CHECK(valid_enums(c, dtype, where));
+    CHECK(evaluate(c));
+    if (grad) CHECK(copy_out(c, c->grad, true, grad, dtype, where, c->n * c->d));
+    if (loglik || dsigma) {
+        double s[kScalars];
+        CU(cudaMemcpyAsync(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        if (loglik) *loglik = s[kLogLik];
+        if (dsigma) *dsigma = s[kDSigma];
+    }
+    return MDS_OK;
+}
+
+int mds_set_momentum(mds_ctx *c, const void *p, int dtype, int where) {
+    CHECK(check_ctx(c));
+    if (!p) return fail(c, MDS_ERR_INVALID_ARG, "p is NULL");
+    CHECK(valid_enums(c, dtype, where));
+    const void *dev = nullptr;
+    CHECK(stage_in(c, p, dtype, where, c->n * c->d, &dev));
+    cudaError_t e = launch_convert(dev, dtype == MDS_F64, c->p, c->fp64, c->n * c->d, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_momentum: %s", cudaGetErrorString(e));
+    CU(cudaStreamSynchronize(c->stream));
+    return MDS_OK;
+}
+
+int mds_get_momentum(mds_ctx *c, void *p, int dtype, int where) {
+    CHECK(check_ctx(c));
+    if (!p) return fail(c, MDS_ERR_INVALID_ARG, "p is NULL");
+    CHECK(valid_enums(c, dtype, where));
+    return copy_out(c, c->p, c->fp64, p, dtype, where, c->n * c->d);
+}
+
+int mds_leapfrog(mds_ctx *c, int n_steps, double eps, const void *p0, int p0_dtype, int p0_where, double *dh) {
+    CHECK(check_ctx(c));
+    if (n_steps < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if (!std::isfinite(eps)) return fail(c, MDS_ERR_INVALID_ARG, "eps must be finite");
+    CHECK(ready(c));
+    if (p0) CHECK(mds_set_momentum(c, p0, p0_dtype, p0_where));
+    if (!c->grad_valid) CHECK(evaluate(c));
+    CHECK(autotune(c));
+    CHECK(enqueue_trajectory(c, n_steps, eps, 0, 1, 0, 0, c->stream));
+    CHECK(check_device_err(c, "leapfrog"));
+    if (c->profiling) CHECK(harvest_prof(c));
+    if (dh) {
+        double s[kScalars];
+        CU(cudaMemcpyAsync(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        *dh = s[kLastDH];
+    }
+    return MDS_OK;
+}
+
+int mds_hmc(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, const double *p_all, const double *u_all,
+            int *accepted, double *dh, mds_hmc_stats *stats) {
+    CHECK(check_ctx(c));
+    if (n_iter < 0 || n_steps < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_iter and n_steps must be >= 0");
+    if (!std::isfinite(eps)) return fail(c, MDS_ERR_INVALID_ARG, "eps must be finite");
+    if ((p_all == nullptr) != (u_all == nullptr))
+        return fail(c, MDS_ERR_INVALID_ARG, "p_all and u_all must be given together");
+    CHECK(ready(c));
+    if (!c->grad_valid) CHECK(evaluate(c));
+    CHECK(autotune(c));
+    if (n_iter == 0) return MDS_OK;
+    const int inj = p_all != nullptr;
+    const int64_t nd = c->n * c->d;
+    if (inj) {
+        const size_t pb = static_cast<size_t>(n_iter) * nd * sizeof(double);
+        if (pb > c->p_inj_bytes) {
+            dev_free(c->p_inj);
+            c->p_inj = nullptr;
+            CHECK(dev_alloc_t(c, &c->p_inj, pb));
+            c->p_inj_bytes = pb;
+            c->gen++;
+        }
+        const size_t ub = static_cast<size_t>(n_iter) * sizeof(double);
+        if (ub > c->u_inj_bytes) {
+            dev_free(c->u_inj);
+            c->u_inj = nullptr;
+            CHECK(dev_alloc_t(c, &c->u_inj, ub));
+            c->u_inj_bytes = ub;
+            c->gen++;
+        }
+        for (int t = 0; t < n_iter; ++t)
+            if (!(u_all[t] > 0.0 && u_all[t] < 1.0)) return fail(c, MDS_ERR_INVALID_ARG, "u_all[%d] not in (0,1)", t);
+        CU(cudaMemcpyAsync(c->p_inj, p_all, pb, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemcpyAsync(c->u_inj, u_all, ub, cudaMemcpyHostToDevice, c->stream));
+    }
+    CHECK(ensure_out_cap(c, static_cast<size_t>(n_iter)));
+    CU(cudaMemsetAsync(c->counters + kIterLocal, 0, sizeof(int64_t), c->stream));
+    int64_t acc_before = 0;
+    CU(cudaMemcpyAsync(&acc_before, c->counters + kAccepted, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+
+    // one HMC iteration as a CUDA graph, captured once per configuration
+    const auto key = std::make_tuple(c->gen, n_steps, eps, inj ? 2 : 1, c->profiling ? 1 : 0, seed, c->strip);
+    if (!c->graph || key != c->graph_key) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        c->prof_used = 0;
+        int st = enqueue_trajectory(c, n_steps, eps, inj ? 2 : 1, inj ? 2 : 1, 1, seed, c->cap_stream);
+        c->graph_prof = c->prof_used;
+        c->prof_used = 0;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (st != MDS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        c->graph_key = key;
+    }
+    for (int t = 0; t < n_iter; ++t) {
+        CU(cudaGraphLaunch(c->graph, c->stream));
+        if (c->profiling) {
+            CU(cudaStreamSynchronize(c->stream));
+            c->prof_used = c->graph_prof;
+            CHECK(harvest_prof(c));
+        }
+    }
+    int st = check_device_err(c, "hmc");
+    if (accepted) {
+        std::vector<int32_t> a(n_iter);
+        CU(cudaMemcpyAsync(a.data(), c->acc_out, n_iter * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        for (int t = 0; t < n_iter; ++t) accepted[t] = a[t];
+    }
+    if (dh) {
+        CU(cudaMemcpyAsync(dh, c->dh_out, n_iter * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    if (stats) {
+        double s[kScalars];
+        int64_t cnt[kCounters];
+        CU(cudaMemcpyAsync(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        stats->iterations = n_iter;
+        stats->accepted = cnt[kAccepted] - acc_before;
+        stats->last_dh = s[kLastDH];
+        stats->last_loglik = s[kLogLik];
+    }
+    return st;
+}
+
+int mds_problem_size(const mds_ctx *c, int64_t *pairs, int64_t *y_bytes) {
+    if (!c) return MDS_ERR_INVALID_ARG;
+    if (pairs) *pairs = c->n * (c->n - 1) / 2;
+    if (y_bytes) *y_bytes = c->tiles * kTileElems * static_cast<int64_t>(sizeof(float));
+    return MDS_OK;
+}
+
+int mds_set_strip(mds_ctx *c, int32_t strip) {
+    CHECK(check_ctx(c));
+    if (strip < 0) return fail(c, MDS_ERR_INVALID_ARG, "strip must be >= 0");
+    const int smax = max_strip_for_smem(c);
+    if (strip > smax) return fail(c, MDS_ERR_INVALID_ARG, "strip %d exceeds the shared-memory limit %d", strip, smax);
+    c->strip_req = strip;
+    if (strip > 0 && strip != c->strip) CHECK(build_strips(c, strip));
+    return MDS_OK;
+}
+
+int mds_get_strip(const mds_ctx *c, int32_t *strip) {
+    if (!c || !strip) return MDS_ERR_INVALID_ARG;
+    *strip = c->strip;
+    return MDS_OK;
+}
+
+int mds_time_pass(mds_ctx *c, int reps, double *ms_per_pass) {
+    CHECK(check_ctx(c));
+    if (reps < 1 || !ms_per_pass) return fail(c, MDS_ERR_INVALID_ARG, "reps must be >= 1 and ms_per_pass non-NULL");
+    CHECK(ready(c));
+    CHECK(autotune(c));
+    const bool prof = c->profiling;
+    c->profiling = false;
+    CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+    CU(cudaEventRecord(c->ev0, c->stream));
+    for (int r = 0; r < reps; ++r) CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+    CU(cudaEventRecord(c->ev1, c->stream));
+    CU(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    *ms_per_pass = ms / reps;
+    c->profiling = prof;
+    c->grad_valid = true;
+    return check_device_err(c, "time_pass");
+}
+
+int mds_set_profiling(mds_ctx *c, int on) {
+    CHECK(check_ctx(c));
+    c->profiling = on != 0;
+    c->prof_used = 0;
+    c->prof_launches = 0;
+    c->prof_ms = 0.0;
+    return MDS_OK;
+}
+
+int mds_get_pass_time(const mds_ctx *c, int64_t *launches, double *total_ms) {
+    if (!c) return MDS_ERR_INVALID_ARG;
+    if (launches) *launches = c->prof_launches;
+    if (total_ms) *total_ms = c->prof_ms;
+    return MDS_OK;
+}
+
+const char *mds_last_error(const mds_ctx *c) {
+    if (!c) return g_create_error.c_str();
+    return c->last_error.c_str();
+}
+
+}  // extern "C"

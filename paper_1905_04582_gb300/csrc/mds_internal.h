@@ -1,0 +1,239 @@
+// Internal declarations shared by the host runtime (api.cpp) and the CUDA
+// kernels.  Not part of the public ABI (include/mds.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mds {
+
+// ---------------------------------------------------------------------------
+// Tile geometry of the pair pass.
+//
+// The M = N(N-1)/2 pairs i < j are covered by 64 x 64 tiles (I, J), I <= J,
+// over row blocks I and column blocks J of 64 items (nt = ceil(N/64) blocks).
+// Diagonal tiles (I == J) hold the full square; pairs with j <= i, and items
+// past N in the last block, are masked.  Tiles are stored back to back in
+// row-block order, t(I, J) = I*nt - I*(I-1)/2 + (J - I), so the tiles of one
+// row block are contiguous.  Inside a tile, Y is column-chunk major:
+//   element (row r, column c) at  (c / 4) * 256 + r * 4 + (c % 4),
+// i.e. 16 chunks of 4 columns, each chunk 64 rows x 4 floats (1 KB).  A lane
+// owning rows r and r + 32 reads each chunk with two coalesced 128-bit loads.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 64;
+constexpr int kTileElems = kTile * kTile;   // 4096 FP32 values = 16 KB
+constexpr int kChunkCols = 4;
+constexpr int kChunksPerTile = kTile / kChunkCols;  // 16
+constexpr int kPairWarps = 4;               // warps per CTA in the pair kernel
+constexpr int kPairThreads = 32 * kPairWarps;
+constexpr int kChunksPerWarp = kChunksPerTile / kPairWarps;  // 4 chunks = 16 columns per tile
+
+__host__ __device__ inline int64_t tile_index(int64_t I, int64_t J, int64_t nt) {
+    return I * nt - I * (I - 1) / 2 + (J - I);
+}
+
+__host__ __device__ inline int64_t tile_count(int64_t nt) { return nt * (nt + 1) / 2; }
+
+// Offset of row i in the packed strict upper triangle (row-major (0,1),(0,2),...).
+__host__ __device__ inline int64_t packed_row_start(int64_t i, int64_t n) { return i * n - i * (i + 1) / 2; }
+
+// One unit of work of the pair kernel: row block I against column blocks
+// [j0, j1) (j0 >= I).  row_slot indexes this strip's row partial sums; the
+// strips of a row block occupy consecutive row slots.
+struct Strip {
+    int32_t I, j0, j1, row_slot;
+};
+
+// Scalar partial sums per strip (FP64), in this order.
+enum ScalarPart : int {
+    kSumE2 = 0,     // sum (y - delta)^2
+    kSumMDelta,     // FP32C: sum m' delta, m' = sqrt(2 pi) phi(z)/Phi(z);  FP64: sum (phi/Phi) delta
+    kSumLogPhi,     // FP32C: sum log2(1/Phi(z));                           FP64: sum log Phi(z)
+    kSumSpare,
+    kScalarParts
+};
+
+// Arguments of the fused pair pass.
+struct PairArgs {
+    const float *y;          // tile-packed Y (FP32)
+    const void *xrow;        // plain locations [n_pad][D] (float or double)
+    const void *xneg;        // negated locations, column-pair interleaved (see xneg layout below)
+    const Strip *strips;     // work list, one strip per CTA, largest first
+    int32_t n_strips;
+    int32_t nt;              // blocks per side
+    int64_t n;               // N
+    double *row_part;        // [row slots][64][D] FP64: sum_j w (x_i - x_j) / delta over the strip
+    void *col_part;          // [tiles][64][D] (float or double): sum_i w (x_i - x_j) / delta over the tile
+    double *scal_part;       // [n_strips][kScalarParts]
+    unsigned *err;           // device error word (see ErrBits)
+    // FP32C constants (sigma folded in on the host), each duplicated {c, c}
+    // so that it is a ready operand of the packed f32x2 instructions
+    float2 mp[4];            // -P(delta/sigma)/sqrt(2 pi) coefficients in powers of delta
+    float2 md[4];            // D(delta/sigma) coefficients in powers of delta (md[0] = 1)
+    float2 c_phi;            // -log2(e) / (2 sigma^2): 2^(c_phi delta^2) = exp(-z^2/2)
+    float2 neg_inv_s2;       // -1/sigma^2
+    float2 m_coef;           // 1/(sigma sqrt(2 pi))
+    // FP64 constants
+    double sigma;
+    double inv_sigma;
+    double inv_s2;
+};
+
+// xneg layout: for column pair cp = j/2 and coordinate k, the float2 (or
+// double2) { -x[2cp][k], -x[2cp+1][k] } at element (cp * D + k).  A strip of
+// columns [64 j0, 64 j1) is one contiguous byte range, copied to shared
+// memory with one bulk TMA copy.
+
+enum ErrBits : unsigned {
+    kErrTimeout = 1u,     // a bounded mbarrier wait gave up
+    kErrNonfinite = 2u,   // a partial sum was NaN / Inf
+    kErrBadArgs = 4u,     // kernel launched with inconsistent arguments
+    kErrBadInput = 8u,    // an input value was negative / NaN / Inf
+};
+
+// Kernel launchers (pair_kernel.cu).
+cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, int strip_len, cudaStream_t s);
+cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, int strip_len, cudaStream_t s);
+size_t pair_smem_bytes(int d, int strip_len, bool fp64);
+
+// ---------------------------------------------------------------------------
+// Reduction, leapfrog updates and HMC bookkeeping (reduce_kernel.cu).
+// ---------------------------------------------------------------------------
+
+// Per-context scalars kept on the device (FP64).
+enum Scalar : int {
+    kLogLik = 0,    // L at the current x (what the API reports)
+    kSumR,          // sum r at the current x
+    kDSigma,        // dL/dsigma at the current x
+    kLogLik0,       // L at the trajectory start (saved by the start kernel)
+    kSumR0,
+    kDSigma0,
+    kLogLikEnd,     // L at the end of the pass just reduced (read by the end kernel)
+    kLastDH,        // H(end) - H(start) of the last trajectory
+    kScalars
+};
+
+// Per-context counters kept on the device.  The start kernel snapshots the
+// running counters into the *Cur slots, which the end kernel only reads, so
+// that no CTA of the end kernel can observe CTA 0's increment.
+enum Counter : int {
+    kIter = 0,      // HMC iterations run (drives the Philox counter)
+    kIterLocal,     // iterations run in the current mds_hmc call
+    kAccepted,      // accepted proposals (total)
+    kIterCur,       // snapshot of kIter for the trajectory in flight
+    kIterLocalCur,  // snapshot of kIterLocal
+    kCounters
+};
+
+// Reduction / update modes of the reduce kernel.
+enum ReduceMode : int {
+    kModeEval = 0,      // gradient + scalars only
+    kModeKickDrift,     // + p += eps g(x); x += eps p            (inner leapfrog steps)
+    kModeHalfKick,      // + p += eps/2 g(x); kinetic / ||x||^2 partials (last step)
+};
+
+struct ReduceArgs {
+    const double *row_part;
+    const void *col_part;     // float or double
+    const double *scal_part;
+    const int32_t *row_first_slot;  // [nt + 1]
+    int32_t n_strips;
+    int32_t nt;
+    int64_t n;
+    int32_t d;
+    int32_t mode;
+    bool fp64;                // context precision (x, p, col_part type)
+    double sigma;
+    double lambda;            // prior precision
+    double eps;               // leapfrog step
+    double *grad;             // [N][D] dL/dx (FP64)
+    double *scal;             // [kScalars]
+    void *x;                  // [n_pad][D] (T)
+    void *xneg;               // column-pair layout (T2)
+    void *p;                  // [N][D] (T)
+    double *energy_part;      // [gridDim][2]: kinetic, ||x||^2 per CTA (kModeHalfKick)
+    unsigned *err;
+};
+
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t s);
+
+// Trajectory start: (optionally) draw / load p, save x0 and the cached
+// gradient / scalars, kinetic-energy partials, then p += eps/2 g, x += eps p.
+struct TrajArgs {
+    int64_t n;
+    int32_t d;
+    bool fp64;
+    double eps;
+    double lambda;
+    int32_t momentum_src;     // 0: keep p, 1: Philox draw, 2: injected FP64 array
+    const double *p_inj;      // [n_iter][N][D] when momentum_src == 2 (indexed by kIterLocal)
+    uint64_t seed;
+    uint32_t chain;
+    void *x;
+    void *xneg;
+    void *p;
+    void *x0;
+    double *grad;
+    double *grad0;
+    double *scal;
+    int64_t *counters;
+    double *energy_part;      // [gridDim][2]: kinetic energy, ||x||^2 at the start
+    int32_t drift;            // 1: take the first half kick + drift (n_steps > 0)
+};
+cudaError_t launch_traj_start(const TrajArgs &a, int *grid_out, cudaStream_t s);
+
+// Trajectory end: sum the energy partials in a fixed order, H0 and H1, the
+// Metropolis decision (log u < H0 - H1; u from Philox or injected), restore on
+// reject, bookkeeping.  Every CTA takes the same decision.
+struct AcceptArgs {
+    int64_t n;
+    int32_t d;
+    bool fp64;
+    int32_t metropolis;       // 0: always keep the end point (plain leapfrog)
+    int32_t n_start_parts;    // energy partials of the start kernel
+    int32_t n_end_parts;      // energy partials of the last reduce
+    const double *start_part;
+    const double *end_part;
+    double lambda;
+    int32_t u_src;            // 1: Philox, 2: injected
+    const double *u_inj;      // [n_iter]
+    uint64_t seed;
+    uint32_t chain;
+    void *x;
+    void *xneg;
+    const void *x0;
+    double *grad;
+    const double *grad0;
+    double *scal;
+    int64_t *counters;
+    int32_t *acc_out;         // [n_iter] per-iteration decision (optional)
+    double *dh_out;           // [n_iter] per-iteration H1 - H0 (optional)
+    unsigned *err;
+};
+cudaError_t launch_traj_end(const AcceptArgs &a, cudaStream_t s);
+
+// Y ingest: rows [r0, r1) of the caller's Y (full or packed layout; the
+// pointer addresses row r0) into the tile-packed FP32 layout.  Entries read
+// must be finite and >= 0; the first bad (i, j) is recorded in *bad (i*N+j,
+// atomicMin) and kErrBadInput is set.
+struct IngestArgs {
+    const void *src;
+    bool src_f64;
+    bool packed;
+    int64_t ld;               // full layout: row stride (elements)
+    int64_t n;
+    int32_t nt;
+    int64_t r0, r1;           // rows present at src
+    float *y;                 // tile-packed destination
+    unsigned long long *bad;
+    unsigned *err;
+};
+cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s);
+
+// Locations in: src (N x D, f32/f64) -> x [n_pad][D] (T, zero padded) and xneg.
+cudaError_t launch_set_x(const void *src, bool src_f64, int64_t n, int64_t n_pad, int d, bool fp64, void *x,
+                         void *xneg, unsigned *err, cudaStream_t s);
+// Copy / convert an N x D array between element types (device to device).
+cudaError_t launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t count, cudaStream_t s);
+
+}  // namespace mds

@@ -1,0 +1,249 @@
+"""Python front end of the C ABI: an ``MDS`` context object and a
+``torch.autograd.Function`` over (X, sigma).
+
+Arguments are marshalled to the C entry points (numpy arrays as host
+pointers, CUDA torch tensors as device pointers); all arithmetic of the
+likelihood, gradient and HMC runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi
+from .capi import check
+
+try:  # torch is plumbing (device memory, streams); the library works without it
+    import torch
+except ImportError:  # pragma: no cover
+    torch = None
+
+
+def _is_torch(a):
+    return torch is not None and isinstance(a, torch.Tensor)
+
+
+def _buf(a, writable=False):
+    """(pointer, dtype code, where code, keepalive) for a numpy array or torch tensor."""
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if a.dtype == torch.float32:
+            dt = capi.MDS_F32
+        elif a.dtype == torch.float64:
+            dt = capi.MDS_F64
+        else:
+            raise TypeError(f"unsupported dtype {a.dtype}")
+        where = capi.MDS_DEVICE if a.is_cuda else capi.MDS_HOST
+        return ctypes.c_void_p(a.data_ptr()), dt, where, a
+    arr = np.asarray(a)
+    if arr.dtype not in (np.float32, np.float64):
+        arr = arr.astype(np.float64)
+    if not arr.flags.c_contiguous:
+        if writable:
+            raise ValueError("output array must be C-contiguous")
+        arr = np.ascontiguousarray(arr)
+    dt = capi.MDS_F32 if arr.dtype == np.float32 else capi.MDS_F64
+    return arr.ctypes.data_as(ctypes.c_void_p), dt, capi.MDS_HOST, arr
+
+
+class MDS:
+    """One MDS problem (N items, D latent dimensions) resident on the GPU."""
+
+    def __init__(self, n, d, precision="fp32c", strip=None, stream=None):
+        flags = {"fp32c": capi.MDS_PREC_FP32C, "fp64": capi.MDS_PREC_FP64}[precision]
+        self._lib = capi.lib()
+        h = ctypes.c_void_p()
+        check(self._lib.mds_create(int(n), int(d), flags, ctypes.byref(h)), None)
+        self._h = h
+        self.n, self.d, self.precision = int(n), int(d), precision
+        if strip is not None:
+            self.set_strip(strip)
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mds_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        return check(st, self._h)
+
+    # -- configuration
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        if stream is None:
+            ptr = None
+        elif torch is not None and isinstance(stream, torch.cuda.Stream):
+            ptr = stream.cuda_stream
+        else:
+            ptr = int(stream)
+        self._check(self._lib.mds_set_stream(self._h, ctypes.c_void_p(ptr)))
+
+    def set_data(self, y, layout="packed", ld=None):
+        """y: packed strict upper triangle (M values) or full N x N matrix."""
+        p, dt, where, keep = _buf(y)
+        lay = {"packed": capi.MDS_Y_PACKED_UPPER, "full": capi.MDS_Y_FULL}[layout]
+        if ld is None:
+            ld = self.n
+        self._check(self._lib.mds_set_data(self._h, p, dt, lay, int(ld), where))
+        del keep
+
+    def set_locations(self, x):
+        p, dt, where, keep = _buf(x)
+        self._check(self._lib.mds_set_locations(self._h, p, dt, where))
+
+    def get_locations(self, out=None, dtype=np.float64):
+        if out is None:
+            out = np.empty((self.n, self.d), dtype=dtype)
+        p, dt, where, keep = _buf(out, writable=True)
+        self._check(self._lib.mds_get_locations(self._h, p, dt, where))
+        return out
+
+    def set_sigma(self, sigma):
+        self._check(self._lib.mds_set_sigma(self._h, float(sigma)))
+
+    def set_prior(self, lam):
+        self._check(self._lib.mds_set_prior(self._h, float(lam)))
+
+    def set_strip(self, strip):
+        self._check(self._lib.mds_set_strip(self._h, int(strip)))
+
+    def get_strip(self):
+        s = ctypes.c_int32()
+        self._check(self._lib.mds_get_strip(self._h, ctypes.byref(s)))
+        return s.value
+
+    def problem_size(self):
+        m = ctypes.c_int64()
+        b = ctypes.c_int64()
+        self._check(self._lib.mds_problem_size(self._h, ctypes.byref(m), ctypes.byref(b)))
+        return m.value, b.value
+
+    # -- evaluation
+    def log_likelihood(self):
+        """(L, sum_r) of Eq. (2) at the current locations."""
+        ll = ctypes.c_double()
+        sr = ctypes.c_double()
+        self._check(self._lib.mds_log_likelihood(self._h, ctypes.byref(ll), ctypes.byref(sr)))
+        return ll.value, sr.value
+
+    def gradient(self, out=None, dtype=np.float64):
+        """(L, dL/dX, dL/dsigma) from one fused pass.  `out` may be a numpy
+        array or a (CUDA) torch tensor of shape N x D."""
+        if out is None:
+            out = np.empty((self.n, self.d), dtype=dtype)
+        p, dt, where, keep = _buf(out, writable=True)
+        ll = ctypes.c_double()
+        ds = ctypes.c_double()
+        self._check(self._lib.mds_gradient(self._h, ctypes.byref(ll), p, dt, where, ctypes.byref(ds)))
+        return ll.value, out, ds.value
+
+    def time_pass(self, reps=20):
+        ms = ctypes.c_double()
+        self._check(self._lib.mds_time_pass(self._h, int(reps), ctypes.byref(ms)))
+        return ms.value
+
+    def set_profiling(self, on=True):
+        self._check(self._lib.mds_set_profiling(self._h, 1 if on else 0))
+
+    def pass_time(self):
+        """(number of timed pair-pass launches, their total ms) while profiling."""
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        self._check(self._lib.mds_get_pass_time(self._h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    # -- HMC
+    def set_momentum(self, p):
+        ptr, dt, where, keep = _buf(p)
+        self._check(self._lib.mds_set_momentum(self._h, ptr, dt, where))
+
+    def get_momentum(self, out=None, dtype=np.float64):
+        if out is None:
+            out = np.empty((self.n, self.d), dtype=dtype)
+        p, dt, where, keep = _buf(out, writable=True)
+        self._check(self._lib.mds_get_momentum(self._h, p, dt, where))
+        return out
+
+    def leapfrog(self, n_steps, eps, p0=None):
+        """n_steps leapfrog steps in place; returns H(end) - H(start)."""
+        dh = ctypes.c_double()
+        if p0 is None:
+            st = self._lib.mds_leapfrog(self._h, int(n_steps), float(eps), None, 0, 0, ctypes.byref(dh))
+        else:
+            ptr, dt, where, keep = _buf(p0)
+            st = self._lib.mds_leapfrog(self._h, int(n_steps), float(eps), ptr, dt, where, ctypes.byref(dh))
+        self._check(st)
+        return dh.value
+
+    def hmc(self, n_iter, n_steps, eps, seed=0, p_all=None, u_all=None):
+        """n_iter HMC iterations; returns (accepted[n_iter], dH[n_iter], stats)."""
+        acc = np.zeros(n_iter, dtype=np.int32)
+        dh = np.zeros(n_iter, dtype=np.float64)
+        stats = capi.mds_hmc_stats()
+        pp = uu = None
+        if p_all is not None:
+            pp = np.ascontiguousarray(p_all, dtype=np.float64)
+            uu = np.ascontiguousarray(u_all, dtype=np.float64)
+            if pp.shape != (n_iter, self.n, self.d) or uu.shape != (n_iter,):
+                raise ValueError("p_all must be n_iter x N x D and u_all n_iter")
+        st = self._lib.mds_hmc(self._h, int(n_iter), int(n_steps), float(eps), int(seed) & (2**64 - 1),
+                               None if pp is None else pp.ctypes.data_as(ctypes.c_void_p),
+                               None if uu is None else uu.ctypes.data_as(ctypes.c_void_p),
+                               acc.ctypes.data_as(ctypes.c_void_p), dh.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(stats))
+        self._check(st)
+        return acc.astype(bool), dh, {"iterations": stats.iterations, "accepted": stats.accepted,
+                                      "last_dh": stats.last_dh, "last_loglik": stats.last_loglik}
+
+
+if torch is not None:
+
+    class MDSLogLik(torch.autograd.Function):
+        """L(X, sigma) of Eq. (2) as a differentiable torch function.
+
+        forward runs one fused pass of the library (likelihood, dL/dX and
+        dL/dsigma together); backward scales the saved adjoints by the
+        incoming gradient.  X: [N, D] CUDA tensor, sigma: 0-d tensor."""
+
+        @staticmethod
+        def forward(ctx, x, sigma, model):
+            model.set_stream(torch.cuda.current_stream(x.device))
+            model.set_locations(x.detach().contiguous())
+            model.set_sigma(float(sigma))
+            g = torch.empty((model.n, model.d), dtype=torch.float64, device=x.device)
+            ll, _, ds = model.gradient(out=g)
+            ctx.save_for_backward(g)
+            ctx.ds = ds
+            ctx.x_dtype = x.dtype
+            ctx.s_dtype = sigma.dtype
+            return torch.tensor(ll, dtype=torch.float64, device=x.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            gx = (gout * g).to(ctx.x_dtype)
+            gs = (gout * ctx.ds).to(ctx.s_dtype)
+            return gx, gs, None
+
+    def mds_loglik(x, sigma, model):
+        """Differentiable L(X, sigma); `model` is an MDS context holding Y."""
+        if not torch.is_tensor(sigma):
+            sigma = torch.tensor(float(sigma), dtype=torch.float64, device=x.device)
+        return MDSLogLik.apply(x, sigma, model)
