@@ -58,12 +58,16 @@ struct mds_ctx {
 
     // device buffers
     float *y = nullptr;
-    void *x = nullptr, *xneg = nullptr, *p = nullptr, *x0 = nullptr;
-    double *grad = nullptr, *grad0 = nullptr;
+    void *x = nullptr, *p = nullptr, *x0 = nullptr;   // state (float on FP32C, double on FP64)
+    float4 *xrow = nullptr, *xcol = nullptr;          // FP32C split layouts
+    Split *split = nullptr;                           // FP32C split quantum (device)
+    unsigned *xmax_bits = nullptr;                    // FP32C running max |x|
+    float split_bound = 0.f;                          // largest |x| the current quantum serves exactly
+    void *grad = nullptr, *grad0 = nullptr;           // float2 (hi, lo) on FP32C, double on FP64
     void *col_part = nullptr;
-    double *row_part = nullptr;
+    void *row_part = nullptr;
     size_t row_part_bytes = 0;
-    double *scal_part = nullptr;
+    void *scal_part = nullptr;
     size_t scal_part_bytes = 0;
     Strip *strips = nullptr;
     size_t strips_bytes = 0;
@@ -149,6 +153,17 @@ void dev_free(void *p) {
 }
 
 size_t elem(const mds_ctx *c) { return c->fp64 ? sizeof(double) : sizeof(float); }
+size_t grad_elem(const mds_ctx *c) { return c->fp64 ? sizeof(double) : sizeof(float2); }
+
+XState xstate(const mds_ctx *c) {
+    XState xs{};
+    xs.x = c->x;
+    xs.xrow = c->xrow;
+    xs.xcol = c->xcol;
+    xs.split = c->split;
+    xs.xmax_bits = c->xmax_bits;
+    return xs;
+}
 
 int check_ctx(mds_ctx *c) {
     if (!c) return MDS_ERR_INVALID_ARG;
@@ -202,14 +217,14 @@ int build_strips(mds_ctx *c, int strip) {
         CHECK(dev_alloc_t(c, &c->strips, sb));
         c->strips_bytes = sb;
     }
-    const size_t rb = static_cast<size_t>(slot) * kTile * c->d * sizeof(double);
+    const size_t rb = static_cast<size_t>(slot) * kTile * c->d * elem(c);
     if (rb > c->row_part_bytes) {
         dev_free(c->row_part);
         c->row_part = nullptr;
         CHECK(dev_alloc_t(c, &c->row_part, rb));
         c->row_part_bytes = rb;
     }
-    const size_t spb = v.size() * kScalarParts * sizeof(double);
+    const size_t spb = v.size() * kScalarParts * elem(c);
     if (spb > c->scal_part_bytes) {
         dev_free(c->scal_part);
         c->scal_part = nullptr;
@@ -226,10 +241,34 @@ int build_strips(mds_ctx *c, int strip) {
     return MDS_OK;
 }
 
-int max_strip_for_smem(const mds_ctx *c) {
-    int s = 1;
-    while (s < 64 && pair_smem_bytes(c->d, s + 1, c->fp64) <= 40 * 1024) ++s;
-    return s;
+constexpr int kMaxStrip = 64;  // bounds the FP32 row sums of a lane (<= 256 terms)
+
+// Choose the split quantum from max |x| (4x headroom for the moves of a
+// trajectory) and rewrite the split layouts when it changes.  Called at the
+// start of every call that runs passes.
+int refresh_split(mds_ctx *c, bool force) {
+    if (c->fp64) return MDS_OK;
+    unsigned bits = 0;
+    CU(cudaMemcpyAsync(&bits, c->xmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    float m;
+    std::memcpy(&m, &bits, sizeof(m));
+    if (!force && m <= c->split_bound && m * 64.f >= c->split_bound) return MDS_OK;
+    const int b = split_bits(c->d);
+    const double lim = std::ldexp(1.0, b - 1) - 1.0;  // |xh| / q must stay below 2^(B-1)
+    const double mm = std::max(static_cast<double>(m), 1e-30) * 4.0;
+    const int ex = static_cast<int>(std::ceil(std::log2(mm / lim)));
+    Split sp;
+    sp.q = static_cast<float>(std::ldexp(1.0, ex));
+    sp.magic = static_cast<float>(std::ldexp(1.5, ex + 23));
+    if (!std::isfinite(sp.magic) || sp.q < std::ldexp(1.0f, -100))
+        return fail(c, MDS_ERR_INVALID_ARG, "locations out of the FP32C range (max |x| = %g)", m);
+    c->split_bound = static_cast<float>(lim * std::ldexp(1.0, ex));
+    CU(cudaMemcpyAsync(c->split, &sp, sizeof(sp), cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = launch_resplit(xstate(c), c->n_pad, c->d, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "resplit: %s", cudaGetErrorString(e));
+    CU(cudaStreamSynchronize(c->stream));
+    return MDS_OK;
 }
 
 // --------------------------------------------------------------- passes
@@ -237,8 +276,9 @@ int max_strip_for_smem(const mds_ctx *c) {
 PairArgs pair_args(const mds_ctx *c) {
     PairArgs a{};
     a.y = c->y;
-    a.xrow = c->x;
-    a.xneg = c->xneg;
+    a.xrow = c->xrow;
+    a.xcol = c->xcol;
+    a.x64 = c->fp64 ? static_cast<const double *>(c->x) : nullptr;
     a.strips = c->strips;
     a.n_strips = c->n_strips;
     a.nt = static_cast<int32_t>(c->nt);
@@ -284,10 +324,9 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.sigma = c->sigma;
     r.lambda = c->lambda;
     r.eps = eps;
-    r.grad = c->grad;
+    r.grad = static_cast<double *>(c->grad);
     r.scal = c->scal;
-    r.x = c->x;
-    r.xneg = c->xneg;
+    r.xs = xstate(c);
     r.p = c->p;
     r.energy_part = c->e_end;
     r.err = c->err;
@@ -330,7 +369,7 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s) {
         }
         CHECK(record_prof(c, c->prof_a[pk], s));
     }
-    cudaError_t e = c->fp64 ? launch_pair_pass_f64(a, c->d, c->strip, s) : launch_pair_pass_f32(a, c->d, c->strip, s);
+    cudaError_t e = c->fp64 ? launch_pair_pass_f64(a, c->d, s) : launch_pair_pass_f32(a, c->d, s);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
     if (c->profiling) {
         CHECK(record_prof(c, c->prof_b[pk], s));
@@ -362,7 +401,7 @@ int autotune(mds_ctx *c) {
     if (const char *env = getenv("MDS_STRIP")) {
         const int s = atoi(env);
         if (s > 0) {
-            if (c->strip != s) CHECK(build_strips(c, std::min(s, max_strip_for_smem(c))));
+            if (c->strip != s) CHECK(build_strips(c, std::min(s, kMaxStrip)));
             return MDS_OK;
         }
     }
@@ -375,9 +414,9 @@ int autotune(mds_ctx *c) {
             return MDS_OK;
         }
     }
-    const int smax = max_strip_for_smem(c);
+    const int smax = kMaxStrip;
     std::vector<int> cands;
-    for (int s : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+    for (int s : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
         if (s > smax || s > c->nt) continue;
         const int64_t strips_est = (c->tiles + s - 1) / s;
         // keep enough CTAs for every SM, unless the problem is tiny anyway
@@ -419,6 +458,7 @@ int autotune(mds_ctx *c) {
 // Evaluate at the current x (gradient + scalars) and wait.
 int evaluate(mds_ctx *c) {
     CHECK(ready(c));
+    CHECK(refresh_split(c, false));
     CHECK(autotune(c));
     CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
     CU(cudaGetLastError());
@@ -428,15 +468,17 @@ int evaluate(mds_ctx *c) {
     return MDS_OK;
 }
 
-int copy_out(mds_ctx *c, const void *dev_src, bool src_f64, void *dst, int dtype, int where, int64_t count) {
+// src_kind: 0 f32, 1 f64, 2 float2 (hi, lo) pairs
+int copy_out(mds_ctx *c, const void *dev_src, int src_kind, void *dst, int dtype, int where, int64_t count) {
     const bool dst_f64 = dtype == MDS_F64;
     const size_t eb = dst_f64 ? 8 : 4;
+    const int64_t cnt = src_kind == 2 ? -count : count;
     if (where == MDS_DEVICE) {
-        cudaError_t e = launch_convert(dev_src, src_f64, dst, dst_f64, count, c->stream);
+        cudaError_t e = launch_convert(dev_src, src_kind == 1, dst, dst_f64, cnt, c->stream);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "convert: %s", cudaGetErrorString(e));
         return MDS_OK;
     }
-    cudaError_t e = launch_convert(dev_src, src_f64, c->stage, dst_f64, count, c->stream);
+    cudaError_t e = launch_convert(dev_src, src_kind == 1, c->stage, dst_f64, cnt, c->stream);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "convert: %s", cudaGetErrorString(e));
     CU(cudaMemcpyAsync(dst, c->stage, count * eb, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -477,12 +519,11 @@ int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, in
     t.p_inj = c->p_inj;
     t.seed = seed;
     t.chain = 0;
-    t.x = c->x;
-    t.xneg = c->xneg;
+    t.xs = xstate(c);
     t.p = c->p;
     t.x0 = c->x0;
-    t.grad = c->grad;
-    t.grad0 = c->grad0;
+    t.grad = static_cast<double *>(c->grad);
+    t.grad0 = static_cast<double *>(c->grad0);
     t.scal = c->scal;
     t.counters = c->counters;
     t.energy_part = c->e_start;
@@ -512,11 +553,10 @@ int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, in
     a.u_inj = c->u_inj;
     a.seed = seed;
     a.chain = 0;
-    a.x = c->x;
-    a.xneg = c->xneg;
+    a.xs = xstate(c);
     a.x0 = c->x0;
-    a.grad = c->grad;
-    a.grad0 = c->grad0;
+    a.grad = static_cast<double *>(c->grad);
+    a.grad0 = static_cast<double *>(c->grad0);
     a.scal = c->scal;
     a.counters = c->counters;
     // per-iteration outputs only for Metropolis runs (their index is the
@@ -586,11 +626,16 @@ int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out) {
     int st = MDS_OK;
     if ((st = dev_alloc_t(c, &c->y, static_cast<size_t>(c->tiles) * kTileElems * sizeof(float)))) return cleanup(st);
     if ((st = dev_alloc(c, &c->x, nd_pad * eb))) return cleanup(st);
-    if ((st = dev_alloc(c, &c->xneg, nd_pad * eb))) return cleanup(st);
     if ((st = dev_alloc(c, &c->p, nd_pad * eb))) return cleanup(st);
     if ((st = dev_alloc(c, &c->x0, nd_pad * eb))) return cleanup(st);
-    if ((st = dev_alloc_t(c, &c->grad, nd_pad * sizeof(double)))) return cleanup(st);
-    if ((st = dev_alloc_t(c, &c->grad0, nd_pad * sizeof(double)))) return cleanup(st);
+    if (!c->fp64) {
+        if ((st = dev_alloc_t(c, &c->xrow, nd_pad / 2 * sizeof(float4)))) return cleanup(st);
+        if ((st = dev_alloc_t(c, &c->xcol, nd_pad * sizeof(float4)))) return cleanup(st);
+        if ((st = dev_alloc_t(c, &c->split, sizeof(Split)))) return cleanup(st);
+        if ((st = dev_alloc_t(c, &c->xmax_bits, sizeof(unsigned)))) return cleanup(st);
+    }
+    if ((st = dev_alloc(c, &c->grad, nd_pad * grad_elem(c)))) return cleanup(st);
+    if ((st = dev_alloc(c, &c->grad0, nd_pad * grad_elem(c)))) return cleanup(st);
     if ((st = dev_alloc(c, &c->col_part, static_cast<size_t>(c->tiles) * kTile * d * eb))) return cleanup(st);
     if ((st = dev_alloc_t(c, &c->row_first, (c->nt + 1) * sizeof(int32_t)))) return cleanup(st);
     if ((st = dev_alloc_t(c, &c->scal, kScalars * sizeof(double)))) return cleanup(st);
@@ -606,10 +651,19 @@ int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out) {
         c->last_error = "stream/event creation failed";
         return cleanup(MDS_ERR_CUDA);
     }
-    if (cudaMemset(c->x, 0, nd_pad * eb) != cudaSuccess || cudaMemset(c->xneg, 0, nd_pad * eb) != cudaSuccess ||
-        cudaMemset(c->p, 0, nd_pad * eb) != cudaSuccess || cudaMemset(c->grad, 0, nd_pad * 8) != cudaSuccess ||
-        cudaMemset(c->scal, 0, kScalars * 8) != cudaSuccess || cudaMemset(c->counters, 0, kCounters * 8) != cudaSuccess ||
-        cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess) {
+    bool ok = cudaMemset(c->x, 0, nd_pad * eb) == cudaSuccess && cudaMemset(c->p, 0, nd_pad * eb) == cudaSuccess &&
+              cudaMemset(c->grad, 0, nd_pad * grad_elem(c)) == cudaSuccess &&
+              cudaMemset(c->scal, 0, kScalars * 8) == cudaSuccess &&
+              cudaMemset(c->counters, 0, kCounters * 8) == cudaSuccess &&
+              cudaMemset(c->err, 0, sizeof(unsigned)) == cudaSuccess;
+    if (ok && !c->fp64) {
+        ok = cudaMemset(c->xrow, 0, nd_pad / 2 * sizeof(float4)) == cudaSuccess &&
+             cudaMemset(c->xcol, 0, nd_pad * sizeof(float4)) == cudaSuccess &&
+             cudaMemset(c->xmax_bits, 0, sizeof(unsigned)) == cudaSuccess;
+        Split sp{1.0f, 12582912.0f};  // q = 1 until locations are set
+        ok = ok && cudaMemcpy(c->split, &sp, sizeof(sp), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
         c->last_error = "initial memset failed";
         return cleanup(MDS_ERR_CUDA);
     }
@@ -623,10 +677,11 @@ int mds_destroy(mds_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *bufs[] = {c->y,     c->x,        c->xneg,   c->p,        c->x0,     c->grad,    c->grad0,
-                    c->col_part, c->row_part, c->scal_part, c->strips, c->row_first, c->scal, c->counters,
-                    c->err,   c->bad,      c->e_start, c->e_end,    c->stage,  c->p_inj,   c->u_inj,
-                    c->acc_out, c->dh_out};
+    void *bufs[] = {c->y,        c->x,        c->p,         c->x0,       c->xrow,      c->xcol,
+                    c->split,    c->xmax_bits, c->grad,     c->grad0,    c->col_part,  c->row_part,
+                    c->scal_part, c->strips,  c->row_first, c->scal,     c->counters,  c->err,
+                    c->bad,      c->e_start,  c->e_end,     c->stage,    c->p_inj,     c->u_inj,
+                    c->acc_out,  c->dh_out};
     for (void *b : bufs) dev_free(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -735,7 +790,15 @@ int mds_set_locations(mds_ctx *c, const void *x, int dtype, int where) {
     const void *dev = nullptr;
     CHECK(stage_in(c, x, dtype, where, c->n * c->d, &dev));
     CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
-    cudaError_t e = launch_set_x(dev, dtype == MDS_F64, c->n, c->n_pad, c->d, c->fp64, c->x, c->xneg, c->err, c->stream);
+    if (!c->fp64) {
+        // quantum of the exact-difference split from the incoming values
+        CU(cudaMemsetAsync(c->xmax_bits, 0, sizeof(unsigned), c->stream));
+        cudaError_t e = launch_xmax(dev, dtype == MDS_F64, c->n * c->d, c->xmax_bits, c->stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_locations: %s", cudaGetErrorString(e));
+        c->split_bound = 0.f;
+        CHECK(refresh_split(c, true));
+    }
+    cudaError_t e = launch_set_x(dev, dtype == MDS_F64, c->n, c->n_pad, c->d, c->fp64, xstate(c), c->err, c->stream);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_locations: %s", cudaGetErrorString(e));
     unsigned h = 0;
     CU(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -756,7 +819,7 @@ int mds_get_locations(mds_ctx *c, void *x, int dtype, int where) {
     if (!x) return fail(c, MDS_ERR_INVALID_ARG, "X is NULL");
     CHECK(valid_enums(c, dtype, where));
     if (!c->have_x) return fail(c, MDS_ERR_STATE, "no locations set");
-    return copy_out(c, c->x, c->fp64, x, dtype, where, c->n * c->d);
+    return copy_out(c, c->x, c->fp64 ? 1 : 0, x, dtype, where, c->n * c->d);
 }
 
 int mds_set_sigma(mds_ctx *c, double sigma) {
@@ -800,7 +863,7 @@ int mds_gradient(mds_ctx *c, double *loglik, void *grad, int dtype, int where, d
     CHECK(check_ctx(c));
     if (grad) CHECK(valid_enums(c, dtype, where));
     CHECK(evaluate(c));
-    if (grad) CHECK(copy_out(c, c->grad, true, grad, dtype, where, c->n * c->d));
+    if (grad) CHECK(copy_out(c, c->grad, c->fp64 ? 1 : 2, grad, dtype, where, c->n * c->d));
     if (loglik || dsigma) {
         double s[kScalars];
         CU(cudaMemcpyAsync(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
@@ -827,7 +890,7 @@ int mds_get_momentum(mds_ctx *c, void *p, int dtype, int where) {
     CHECK(check_ctx(c));
     if (!p) return fail(c, MDS_ERR_INVALID_ARG, "p is NULL");
     CHECK(valid_enums(c, dtype, where));
-    return copy_out(c, c->p, c->fp64, p, dtype, where, c->n * c->d);
+    return copy_out(c, c->p, c->fp64 ? 1 : 0, p, dtype, where, c->n * c->d);
 }
 
 int mds_leapfrog(mds_ctx *c, int n_steps, double eps, const void *p0, int p0_dtype, int p0_where, double *dh) {
@@ -836,6 +899,7 @@ int mds_leapfrog(mds_ctx *c, int n_steps, double eps, const void *p0, int p0_dty
     if (!std::isfinite(eps)) return fail(c, MDS_ERR_INVALID_ARG, "eps must be finite");
     CHECK(ready(c));
     if (p0) CHECK(mds_set_momentum(c, p0, p0_dtype, p0_where));
+    CHECK(refresh_split(c, false));
     if (!c->grad_valid) CHECK(evaluate(c));
     CHECK(autotune(c));
     CHECK(enqueue_trajectory(c, n_steps, eps, 0, 1, 0, 0, c->stream));
@@ -858,6 +922,7 @@ int mds_hmc(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, cons
     if ((p_all == nullptr) != (u_all == nullptr))
         return fail(c, MDS_ERR_INVALID_ARG, "p_all and u_all must be given together");
     CHECK(ready(c));
+    CHECK(refresh_split(c, false));
     if (!c->grad_valid) CHECK(evaluate(c));
     CHECK(autotune(c));
     if (n_iter == 0) return MDS_OK;
@@ -958,8 +1023,7 @@ int mds_problem_size(const mds_ctx *c, int64_t *pairs, int64_t *y_bytes) {
 int mds_set_strip(mds_ctx *c, int32_t strip) {
     CHECK(check_ctx(c));
     if (strip < 0) return fail(c, MDS_ERR_INVALID_ARG, "strip must be >= 0");
-    const int smax = max_strip_for_smem(c);
-    if (strip > smax) return fail(c, MDS_ERR_INVALID_ARG, "strip %d exceeds the shared-memory limit %d", strip, smax);
+    if (strip > kMaxStrip) return fail(c, MDS_ERR_INVALID_ARG, "strip %d exceeds the limit %d", strip, kMaxStrip);
     c->strip_req = strip;
     if (strip > 0 && strip != c->strip) CHECK(build_strips(c, strip));
     return MDS_OK;
@@ -975,6 +1039,7 @@ int mds_time_pass(mds_ctx *c, int reps, double *ms_per_pass) {
     CHECK(check_ctx(c));
     if (reps < 1 || !ms_per_pass) return fail(c, MDS_ERR_INVALID_ARG, "reps must be >= 1 and ms_per_pass non-NULL");
     CHECK(ready(c));
+    CHECK(refresh_split(c, false));
     CHECK(autotune(c));
     const bool prof = c->profiling;
     c->profiling = false;

@@ -15,24 +15,40 @@ namespace mds {
 // Diagonal tiles (I == J) hold the full square; pairs with j <= i, and items
 // past N in the last block, are masked.  Tiles are stored back to back in
 // row-block order, t(I, J) = I*nt - I*(I-1)/2 + (J - I), so the tiles of one
-// row block are contiguous.  Inside a tile, Y is column-chunk major:
-//   element (row r, column c) at  (c / 4) * 256 + r * 4 + (c % 4),
-// i.e. 16 chunks of 4 columns, each chunk 64 rows x 4 floats (1 KB).  A lane
-// owning rows r and r + 32 reads each chunk with two coalesced 128-bit loads.
+// row block are contiguous.
+//
+// Work split inside a tile (one CTA of 4 warps): warp w takes columns
+// [16w, 16w+16); lane l = 8b + a takes the 4 columns 16w + 4b + {0..3} and
+// the 8 rows 2(a + 8q) + {0, 1}, q = 0..3 (4 row pairs).  Y inside a tile is
+// stored in exactly the order the lanes read it:
+//   element (r, c) at  ((w * 8 + t) * 32 + lane) * 4 + e,
+//   w = c / 16, b = (c / 4) % 4, half = (c % 4) / 2, rp = r / 2, a = rp % 8,
+//   q = rp / 8, lane = 8b + a, t = 2q + half, e = 2 (c % 2) + (r % 2),
+// so that warp w's quarter of a tile is 4 KB contiguous (one bulk TMA copy)
+// and every 128-bit shared-memory load of the 32 lanes reads 512 contiguous
+// bytes (no bank conflicts), giving {y(r,c), y(r+1,c), y(r,c+1), y(r+1,c+1)}
+// -- two row-packed operands of the f32x2 instructions.
 // ---------------------------------------------------------------------------
 constexpr int kTile = 64;
 constexpr int kTileElems = kTile * kTile;   // 4096 FP32 values = 16 KB
-constexpr int kChunkCols = 4;
-constexpr int kChunksPerTile = kTile / kChunkCols;  // 16
 constexpr int kPairWarps = 4;               // warps per CTA in the pair kernel
 constexpr int kPairThreads = 32 * kPairWarps;
-constexpr int kChunksPerWarp = kChunksPerTile / kPairWarps;  // 4 chunks = 16 columns per tile
+constexpr int kWarpCols = kTile / kPairWarps;  // 16 columns per warp
+constexpr int kWarpTileElems = kTileElems / kPairWarps;  // 1024 floats = 4 KB per warp
 
 __host__ __device__ inline int64_t tile_index(int64_t I, int64_t J, int64_t nt) {
     return I * nt - I * (I - 1) / 2 + (J - I);
 }
 
 __host__ __device__ inline int64_t tile_count(int64_t nt) { return nt * (nt + 1) / 2; }
+
+// Offset of (r, c) inside a tile (see above).
+__host__ __device__ inline int tile_offset(int r, int c) {
+    const int w = c >> 4, b = (c >> 2) & 3, half = (c >> 1) & 1, ec = c & 1;
+    const int rp = r >> 1, a = rp & 7, q = rp >> 3;
+    const int lane = 8 * b + a, t = 2 * q + half, e = 2 * ec + (r & 1);
+    return ((w * 8 + t) * 32 + lane) * 4 + e;
+}
 
 // Offset of row i in the packed strict upper triangle (row-major (0,1),(0,2),...).
 __host__ __device__ inline int64_t packed_row_start(int64_t i, int64_t n) { return i * n - i * (i + 1) / 2; }
@@ -44,7 +60,7 @@ struct Strip {
     int32_t I, j0, j1, row_slot;
 };
 
-// Scalar partial sums per strip (FP64), in this order.
+// Scalar partial sums per strip, in this order.
 enum ScalarPart : int {
     kSumE2 = 0,     // sum (y - delta)^2
     kSumMDelta,     // FP32C: sum m' delta, m' = sqrt(2 pi) phi(z)/Phi(z);  FP64: sum (phi/Phi) delta
@@ -53,18 +69,38 @@ enum ScalarPart : int {
     kScalarParts
 };
 
+// ---------------------------------------------------------------------------
+// Location layouts of the FP32C path.
+//
+// Exact differences: every coordinate is split x = xh + xl, xh the nearest
+// multiple of a power-of-two quantum q (chosen from max |x| so that
+// |xh_i - xh_j| / q < 2^B, B = 11 for D <= 4 and 10 for D <= 8).  Then
+// Dh = xh_i - xh_j and Dh^2 are exact in FP32, sum_k Dh_k^2 is exact, and
+// the squared distance is sum_k Dh^2 + Dl (2 Dh + Dl) with Dl = xl_i - xl_j,
+// a small correction computed in FP32 -- which keeps y - delta accurate where
+// y and delta nearly cancel.
+//   xrow[(rp * D + k)] (float4) = { xh_{2rp,k}, xh_{2rp+1,k}, xl_{2rp,k}, xl_{2rp+1,k} }
+//   xcol[(j  * D + k)] (float4) = { -xh_{j,k}, -xh_{j,k}, -xl_{j,k}, -xl_{j,k} }
+// A tile's column block J is 64 * D float4, contiguous (bulk-copied per warp).
+// ---------------------------------------------------------------------------
+struct Split {
+    float q;       // quantum
+    float magic;   // 1.5 * 2^23 * q: (x + magic) - magic rounds x to a multiple of q
+};
+
 // Arguments of the fused pair pass.
 struct PairArgs {
     const float *y;          // tile-packed Y (FP32)
-    const void *xrow;        // plain locations [n_pad][D] (float or double)
-    const void *xneg;        // negated locations, column-pair interleaved (see xneg layout below)
+    const float4 *xrow;      // FP32C: row-pair split layout;  FP64: unused
+    const float4 *xcol;      // FP32C: column split layout;   FP64: unused
+    const double *x64;       // FP64: plain locations [n_pad][D]
     const Strip *strips;     // work list, one strip per CTA, largest first
     int32_t n_strips;
     int32_t nt;              // blocks per side
     int64_t n;               // N
-    double *row_part;        // [row slots][64][D] FP64: sum_j w (x_i - x_j) / delta over the strip
-    void *col_part;          // [tiles][64][D] (float or double): sum_i w (x_i - x_j) / delta over the tile
-    double *scal_part;       // [n_strips][kScalarParts]
+    void *row_part;          // [row slots][64][D] (float / double)
+    void *col_part;          // [tiles][64][D]     (float / double)
+    void *scal_part;         // [n_strips][kScalarParts] (float / double)
     unsigned *err;           // device error word (see ErrBits)
     // FP32C constants (sigma folded in on the host), each duplicated {c, c}
     // so that it is a ready operand of the packed f32x2 instructions
@@ -79,11 +115,6 @@ struct PairArgs {
     double inv_s2;
 };
 
-// xneg layout: for column pair cp = j/2 and coordinate k, the float2 (or
-// double2) { -x[2cp][k], -x[2cp+1][k] } at element (cp * D + k).  A strip of
-// columns [64 j0, 64 j1) is one contiguous byte range, copied to shared
-// memory with one bulk TMA copy.
-
 enum ErrBits : unsigned {
     kErrTimeout = 1u,     // a bounded mbarrier wait gave up
     kErrNonfinite = 2u,   // a partial sum was NaN / Inf
@@ -92,9 +123,8 @@ enum ErrBits : unsigned {
 };
 
 // Kernel launchers (pair_kernel.cu).
-cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, int strip_len, cudaStream_t s);
-cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, int strip_len, cudaStream_t s);
-size_t pair_smem_bytes(int d, int strip_len, bool fp64);
+cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s);
+cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Reduction, leapfrog updates and HMC bookkeeping (reduce_kernel.cu).
@@ -132,26 +162,34 @@ enum ReduceMode : int {
     kModeHalfKick,      // + p += eps/2 g(x); kinetic / ||x||^2 partials (last step)
 };
 
+// Location state shared by the update kernels.
+struct XState {
+    void *x;                  // [n_pad][D] (float / double): the state
+    float4 *xrow;             // FP32C split layouts (null on the FP64 path)
+    float4 *xcol;
+    const Split *split;       // FP32C quantum (device)
+    unsigned *xmax_bits;      // FP32C: running max |x| (float bits, atomicMax)
+};
+
 struct ReduceArgs {
-    const double *row_part;
-    const void *col_part;     // float or double
-    const double *scal_part;
+    const void *row_part;
+    const void *col_part;
+    const void *scal_part;
     const int32_t *row_first_slot;  // [nt + 1]
     int32_t n_strips;
     int32_t nt;
     int64_t n;
     int32_t d;
     int32_t mode;
-    bool fp64;                // context precision (x, p, col_part type)
+    bool fp64;                // context precision (x, p, partial types)
     double sigma;
     double lambda;            // prior precision
     double eps;               // leapfrog step
-    double *grad;             // [N][D] dL/dx (FP64)
+    double *grad;             // [N][D] dL/dx (FP64 copy for the API)
     double *scal;             // [kScalars]
-    void *x;                  // [n_pad][D] (T)
-    void *xneg;               // column-pair layout (T2)
-    void *p;                  // [N][D] (T)
-    double *energy_part;      // [gridDim][2]: kinetic, ||x||^2 per CTA (kModeHalfKick)
+    XState xs;
+    void *p;                  // [N][D]
+    double *energy_part;      // [nt][2] (kModeHalfKick): kinetic, ||x||^2
     unsigned *err;
 };
 
@@ -169,8 +207,7 @@ struct TrajArgs {
     const double *p_inj;      // [n_iter][N][D] when momentum_src == 2 (indexed by kIterLocal)
     uint64_t seed;
     uint32_t chain;
-    void *x;
-    void *xneg;
+    XState xs;
     void *p;
     void *x0;
     double *grad;
@@ -199,8 +236,7 @@ struct AcceptArgs {
     const double *u_inj;      // [n_iter]
     uint64_t seed;
     uint32_t chain;
-    void *x;
-    void *xneg;
+    XState xs;
     const void *x0;
     double *grad;
     const double *grad0;
@@ -230,10 +266,18 @@ struct IngestArgs {
 };
 cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s);
 
-// Locations in: src (N x D, f32/f64) -> x [n_pad][D] (T, zero padded) and xneg.
-cudaError_t launch_set_x(const void *src, bool src_f64, int64_t n, int64_t n_pad, int d, bool fp64, void *x,
-                         void *xneg, unsigned *err, cudaStream_t s);
-// Copy / convert an N x D array between element types (device to device).
+// Locations in: src (N x D, f32/f64) -> the state x (zero padded to n_pad)
+// and, on the FP32C path, the split layouts (quantum from *split).
+cudaError_t launch_set_x(const void *src, bool src_f64, int64_t n, int64_t n_pad, int d, bool fp64, const XState &xs,
+                         unsigned *err, cudaStream_t s);
+// Recompute the split layouts of the FP32C path from x (after a quantum change).
+cudaError_t launch_resplit(const XState &xs, int64_t n_pad, int d, cudaStream_t s);
+// max |x| over the state (float bits into *out via atomicMax; *out must be 0).
+cudaError_t launch_xmax(const void *x, bool fp64, int64_t count, unsigned *out, cudaStream_t s);
+// Copy / convert an array between element types (device to device).
 cudaError_t launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t count, cudaStream_t s);
+
+// Bits B of the exact-difference split for D dimensions (see above).
+__host__ __device__ inline int split_bits(int d) { return d <= 1 ? 12 : d <= 4 ? 11 : 10; }
 
 }  // namespace mds

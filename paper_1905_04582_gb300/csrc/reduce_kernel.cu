@@ -2,13 +2,16 @@
 // (arXiv:1905.04582, section 2.3 "Hamiltonian Monte Carlo", Eq. (6)-(9);
 // the final, serial reduction of Algorithm 1 moved onto the device).
 //
-// reduce:     per column block J of 64 items, gradient of x_k =
+// reduce:     per column block J of 64 items, the gradient of x_k is
 //               sum over tiles (I, J), I <= J, of the column partials
 //             - sum over the strips of row block J of the row partials,
-//             summed in FP64 in a fixed order (4 interleaved splits, then the
-//             splits in order), so results are bitwise reproducible.  The
-//             last CTA sums the strips' scalar partials into L, sum r and
-//             dL/dsigma.  Leapfrog modes also update p and x of the block.
+//             summed in a fixed order (8 interleaved splits, then the splits
+//             in order) so results are bitwise reproducible.  FP32C: the
+//             partials are FP32 and the sums FP32 two-sums (a double-float
+//             accumulator); FP64: plain FP64.  The last CTA sums the strips'
+//             scalar partials into L, sum r and dL/dsigma (FP64 only in its
+//             final few operations).  Leapfrog modes also update p and x of
+//             the block and rewrite the split location layouts.
 // traj_start: momentum draw (Philox4x32-10 + Box-Muller) or injection,
 //             saves the start state, first half kick + drift.
 // traj_end:   energies H = -log pi + p^T p / 2 (FP64), Metropolis decision,
@@ -24,84 +27,172 @@
 namespace mds {
 namespace {
 
-constexpr int kRedThreads = 256;  // 64 items x 4 splits
+constexpr int kRedThreads = 512;  // 64 items x 8 splits
 constexpr int kSplits = kRedThreads / kTile;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kSqrt2Pi = 2.50662827463100050242;
-constexpr double kTwoPi = 6.28318530717958647693;
 
-template <typename T>
-struct Vec2;
-template <>
-struct Vec2<float> {
-    using type = float2;
-};
-template <>
-struct Vec2<double> {
-    using type = double2;
+// ------------------------------------------------- double-float accumulator
+
+// hi + lo with |lo| <= ulp(hi)/2, updated with Knuth's two-sum.
+struct DF {
+    float hi, lo;
 };
 
-// Write one coordinate of item k into the negated, column-pair interleaved copy.
-template <typename T>
-__device__ __forceinline__ void store_xneg(void *xneg, int64_t k, int d, int kk, T v) {
-    T *base = reinterpret_cast<T *>(xneg);
-    base[((k >> 1) * d + kk) * 2 + (k & 1)] = -v;
+__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
+
+__device__ __forceinline__ void df_add(DF &a, float v) {
+    const float s = __fadd_rn(a.hi, v);
+    const float bp = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, err);
 }
 
-// Fixed-order block sum of two doubles per thread (power-of-two blockDim).
+__device__ __forceinline__ void df_add(DF &a, const DF &b) {
+    df_add(a, b.hi);
+    a.lo = __fadd_rn(a.lo, b.lo);
+}
+
+__device__ __forceinline__ float df_float(const DF &a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ double df_double(const DF &a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
+
+__device__ __forceinline__ DF df_shfl_xor(const DF &a, int o) {
+    return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// Fixed-order block sums (blockDim a multiple of 32, at most 1024 threads).
 template <int NT>
-__device__ __forceinline__ void block_sum2(double &a, double &b, double *sm) {
-    const int tid = threadIdx.x;
-    sm[tid] = a;
-    sm[NT + tid] = b;
-    __syncthreads();
+__device__ __forceinline__ DF block_sum_df(DF v, DF *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = NT / 2; o >= 1; o >>= 1) {
-        if (tid < o) {
-            sm[tid] += sm[tid + o];
-            sm[NT + tid] += sm[NT + tid + o];
-        }
-        __syncthreads();
-    }
-    a = sm[0];
-    b = sm[NT];
+    for (int o = 16; o >= 1; o >>= 1) df_add(v, df_shfl_xor(v, o));
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    DF t = sm[0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) df_add(t, sm[w]);
+    __syncthreads();
+    return t;
 }
+
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v, double *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    double t = sm[0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) t += sm[w];
+    __syncthreads();
+    return t;
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    float t = sm[0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) t = fmaxf(t, sm[w]);
+    __syncthreads();
+    return t;
+}
+
+// ------------------------------------------------------------ locations
+
+// Rewrite item k, coordinate kk of the FP32C split layouts from value v.
+__device__ __forceinline__ void write_split(const XState &xs, int64_t k, int d, int kk, float v) {
+    const Split sp = *xs.split;
+    const float h = __fsub_rn(__fadd_rn(v, sp.magic), sp.magic);  // nearest multiple of q
+    const float l = __fsub_rn(v, h);                               // exact
+    float *xr = reinterpret_cast<float *>(xs.xrow + ((k >> 1) * d + kk));
+    xr[k & 1] = h;
+    xr[2 + (k & 1)] = l;
+    xs.xcol[k * d + kk] = make_float4(-h, -h, -l, -l);
+}
+
+// Store a coordinate of the state (and the split layouts on the FP32C path).
+template <typename T>
+__device__ __forceinline__ void store_x(const XState &xs, int64_t k, int d, int kk, T v) {
+    reinterpret_cast<T *>(xs.x)[k * d + kk] = v;
+    if constexpr (std::is_same<T, float>::value) write_split(xs, k, d, kk, v);
+}
+
+// Gradient storage: FP32C keeps (hi, lo) float pairs, FP64 doubles.
+template <typename T>
+struct GradT;
+template <>
+struct GradT<float> {
+    using type = float2;
+    __device__ static float value(const float2 &g) { return __fadd_rn(g.x, g.y); }
+};
+template <>
+struct GradT<double> {
+    using type = double;
+    __device__ static double value(const double &g) { return g; }
+};
 
 // --------------------------------------------------------------- reduce
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_constant__ ReduceArgs a) {
-    __shared__ double sm[kSplits * kTile * D > 2 * kRedThreads ? kSplits * kTile * D : 2 * kRedThreads];
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    using Acc = typename std::conditional<kF32, DF, double>::type;
+    using G = typename GradT<T>::type;
+    __shared__ Acc sm[kSplits * kTile * D > 64 ? kSplits * kTile * D : 64];
     const int tid = threadIdx.x;
     const int nt = a.nt;
 
     if (blockIdx.x == static_cast<unsigned>(nt)) {
-        // scalar partials of all strips -> L, sum r, dL/dsigma (FP64, fixed order)
-        double e2 = 0.0, md = 0.0, lp = 0.0;
-        for (int s = tid; s < a.n_strips; s += kRedThreads) {
-            const double *sp = a.scal_part + static_cast<int64_t>(s) * kScalarParts;
-            e2 += sp[kSumE2];
-            md += sp[kSumMDelta];
-            lp += sp[kSumLogPhi];
+        // scalar partials of all strips -> L, sum r, dL/dsigma (fixed order)
+        const T *sp = reinterpret_cast<const T *>(a.scal_part);
+        Acc e2{}, md{}, lp{};
+        for (int s0 = tid; s0 < a.n_strips; s0 += 4 * kRedThreads) {
+            T v[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int s = s0 + u * kRedThreads;
+                const T *q = sp + static_cast<int64_t>(s) * kScalarParts;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) v[u][i] = s < a.n_strips ? q[i] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if constexpr (kF32) {
+                    df_add(e2, v[u][kSumE2]);
+                    df_add(md, v[u][kSumMDelta]);
+                    df_add(lp, v[u][kSumLogPhi]);
+                } else {
+                    e2 += v[u][kSumE2];
+                    md += v[u][kSumMDelta];
+                    lp += v[u][kSumLogPhi];
+                }
+            }
         }
-        double dummy = 0.0;
-        block_sum2<kRedThreads>(e2, md, sm);
-        __syncthreads();
-        block_sum2<kRedThreads>(lp, dummy, sm);
+        double de2, dmd, dlp;
+        if constexpr (kF32) {
+            de2 = df_double(block_sum_df<kRedThreads>(e2, sm));
+            dmd = df_double(block_sum_df<kRedThreads>(md, sm));
+            dlp = df_double(block_sum_df<kRedThreads>(lp, sm));
+        } else {
+            de2 = block_sum_d<kRedThreads>(e2, sm);
+            dmd = block_sum_d<kRedThreads>(md, sm);
+            dlp = block_sum_d<kRedThreads>(lp, sm);
+        }
         if (tid == 0) {
             const double sg = a.sigma;
             const double m = 0.5 * static_cast<double>(a.n) * static_cast<double>(a.n - 1);
-            double sum_logphi, sum_mdelta;
-            if (a.fp64) {
-                sum_logphi = lp;
-                sum_mdelta = md;
-            } else {
-                sum_logphi = -kLn2 * lp;         // lp = sum log2(1/Phi)
-                sum_mdelta = md / kSqrt2Pi;      // md = sum sqrt(2 pi) (phi/Phi) delta
-            }
-            const double sum_r = e2 / (2.0 * sg * sg) + sum_logphi;
+            const double sum_logphi = kF32 ? -kLn2 * dlp : dlp;      // FP32C: sum log2(1/Phi)
+            const double sum_mdelta = kF32 ? dmd / kSqrt2Pi : dmd;   // FP32C: sqrt(2 pi) (phi/Phi) delta
+            const double sum_r = de2 / (2.0 * sg * sg) + sum_logphi;
             const double ll = -m * log(sg) - sum_r;
-            const double ds = -m / sg + e2 / (sg * sg * sg) + sum_mdelta / (sg * sg);
+            const double ds = -m / sg + de2 / (sg * sg * sg) + sum_mdelta / (sg * sg);
             a.scal[kLogLik] = ll;
             a.scal[kSumR] = sum_r;
             a.scal[kDSigma] = ds;
@@ -115,51 +206,102 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_consta
     const int r = tid & (kTile - 1);
     const int s = tid / kTile;
     const int64_t k = static_cast<int64_t>(J) * kTile + r;
-    double acc[D];
+    Acc acc[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) acc[d] = 0.0;
+    for (int d = 0; d < D; ++d) acc[d] = Acc{};
+    // loads are issued four at a time (independent of the running sums) so
+    // that the latency of the L2 reads overlaps
+    constexpr int kU = 4;
     const T *cp = reinterpret_cast<const T *>(a.col_part);
-    for (int I = s; I <= J; I += kSplits) {
-        const T *c = cp + (tile_index(I, J, nt) * kTile + r) * D;
+    for (int I0 = s; I0 <= J; I0 += kSplits * kU) {
+        T v[kU][D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) acc[d] += static_cast<double>(c[d]);
+        for (int u = 0; u < kU; ++u) {
+            const int I = I0 + u * kSplits;
+            const T *c = cp + (tile_index(I, J, nt) * kTile + r) * D;
+#pragma unroll
+            for (int d = 0; d < D; ++d) v[u][d] = I <= J ? c[d] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                if constexpr (kF32)
+                    df_add(acc[d], v[u][d]);
+                else
+                    acc[d] += v[u][d];
+            }
     }
+    const T *rpart = reinterpret_cast<const T *>(a.row_part);
     const int s0 = a.row_first_slot[J], s1 = a.row_first_slot[J + 1];
-    for (int slot = s0 + s; slot < s1; slot += kSplits) {
-        const double *rp = a.row_part + (static_cast<int64_t>(slot) * kTile + r) * D;
+    for (int sl0 = s0 + s; sl0 < s1; sl0 += kSplits * kU) {
+        T v[kU][D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) acc[d] -= rp[d];
+        for (int u = 0; u < kU; ++u) {
+            const int slot = sl0 + u * kSplits;
+            const T *rp = rpart + (static_cast<int64_t>(slot) * kTile + r) * D;
+#pragma unroll
+            for (int d = 0; d < D; ++d) v[u][d] = slot < s1 ? rp[d] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                if constexpr (kF32)
+                    df_add(acc[d], -v[u][d]);
+                else
+                    acc[d] -= v[u][d];
+            }
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) sm[(s * kTile + r) * D + d] = acc[d];
     __syncthreads();
 
-    double ke = 0.0, xx = 0.0;
+    Acc ke{}, xx{};
+    float xmax = 0.f;
     if (s == 0 && k < a.n) {
-        T *x = reinterpret_cast<T *>(a.x);
+        T *x = reinterpret_cast<T *>(a.xs.x);
         T *p = reinterpret_cast<T *>(a.p);
+        G *grad = reinterpret_cast<G *>(a.grad);
         bool bad = false;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            double g = sm[r * D + d];
+            Acc g = sm[r * D + d];
 #pragma unroll
-            for (int q = 1; q < kSplits; ++q) g += sm[(q * kTile + r) * D + d];
-            a.grad[k * D + d] = g;
-            bad |= !isfinite(g);
+            for (int q = 1; q < kSplits; ++q) {
+                if constexpr (kF32)
+                    df_add(g, sm[(q * kTile + r) * D + d]);
+                else
+                    g += sm[(q * kTile + r) * D + d];
+            }
+            T gv;
+            if constexpr (kF32) {
+                grad[k * D + d] = make_float2(g.hi, g.lo);
+                gv = df_float(g);
+            } else {
+                grad[k * D + d] = g;
+                gv = g;
+            }
+            bad |= !isfinite(gv);
             if (a.mode != kModeEval) {
-                const double xv = static_cast<double>(x[k * D + d]);
-                const double tg = g - a.lambda * xv;  // gradient of log pi
+                const T xv = x[k * D + d];
+                const T tg = gv - static_cast<T>(a.lambda) * xv;  // gradient of log pi
                 if (a.mode == kModeKickDrift) {
-                    const T pn = static_cast<T>(static_cast<double>(p[k * D + d]) + a.eps * tg);
-                    const T xn = static_cast<T>(xv + a.eps * static_cast<double>(pn));
+                    const T pn = p[k * D + d] + static_cast<T>(a.eps) * tg;
+                    const T xn = xv + static_cast<T>(a.eps) * pn;
                     p[k * D + d] = pn;
-                    x[k * D + d] = xn;
-                    store_xneg<T>(a.xneg, k, D, d, xn);
+                    store_x<T>(a.xs, k, D, d, xn);
+                    xmax = fmaxf(xmax, fabsf(static_cast<float>(xn)));
                 } else {  // kModeHalfKick
-                    const T pn = static_cast<T>(static_cast<double>(p[k * D + d]) + 0.5 * a.eps * tg);
+                    const T pn = p[k * D + d] + static_cast<T>(0.5 * a.eps) * tg;
                     p[k * D + d] = pn;
-                    ke += 0.5 * static_cast<double>(pn) * static_cast<double>(pn);
-                    xx += xv * xv;
+                    if constexpr (kF32) {
+                        df_add(ke, 0.5f * pn * pn);
+                        df_add(xx, xv * xv);
+                    } else {
+                        ke += 0.5 * pn * pn;
+                        xx += xv * xv;
+                    }
                 }
             }
         }
@@ -167,10 +309,27 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_consta
     }
     if (a.mode == kModeHalfKick) {
         __syncthreads();
-        block_sum2<kRedThreads>(ke, xx, sm);
-        if (tid == 0) {
-            a.energy_part[2 * J] = ke;
-            a.energy_part[2 * J + 1] = xx;
+        if constexpr (kF32) {
+            const DF tk = block_sum_df<kRedThreads>(ke, sm);
+            const DF tx = block_sum_df<kRedThreads>(xx, sm);
+            if (tid == 0) {
+                a.energy_part[2 * J] = df_double(tk);
+                a.energy_part[2 * J + 1] = df_double(tx);
+            }
+        } else {
+            const double tk = block_sum_d<kRedThreads>(ke, sm);
+            const double tx = block_sum_d<kRedThreads>(xx, sm);
+            if (tid == 0) {
+                a.energy_part[2 * J] = tk;
+                a.energy_part[2 * J + 1] = tx;
+            }
+        }
+    }
+    if constexpr (kF32) {
+        if (a.mode == kModeKickDrift) {
+            __syncthreads();
+            const float m = block_max<kRedThreads>(xmax, reinterpret_cast<float *>(sm));
+            if (tid == 0 && m > 0.f) atomicMax(a.xs.xmax_bits, __float_as_uint(m));
         }
     }
 }
@@ -205,65 +364,104 @@ __device__ __forceinline__ void philox10(uint32_t (&c)[4], uint64_t key) {
 
 __device__ __forceinline__ double open_unit(uint32_t b) { return (static_cast<double>(b) + 0.5) * (1.0 / 4294967296.0); }
 
+// Box-Muller pair from two 32-bit words, u = (b + 1/2) / 2^32.
+__device__ __forceinline__ void box_muller(uint32_t b1, uint32_t b2, double &z0, double &z1) {
+    const double u1 = open_unit(b1), u2 = open_unit(b2);
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    z0 = rad * cs;
+    z1 = rad * sn;
+}
+
+// FP32 version: -log(u1) through log1p for u1 >= 1/2 (1 - u1 exact from the
+// integer), so the radius keeps full relative precision near u1 = 1.
+__device__ __forceinline__ void box_muller(uint32_t b1, uint32_t b2, float &z0, float &z1) {
+    float nl;
+    if (b1 < 0x80000000u)
+        nl = -logf((static_cast<float>(b1) + 0.5f) * 2.3283064365386963e-10f);
+    else
+        nl = -log1pf(-(static_cast<float>(0xFFFFFFFFu - b1) + 0.5f) * 2.3283064365386963e-10f);
+    const float rad = sqrtf(2.0f * nl);
+    float sn, cs;
+    sincospif(2.0f * ((static_cast<float>(b2) + 0.5f) * 2.3283064365386963e-10f), &sn, &cs);
+    z0 = rad * cs;
+    z1 = rad * sn;
+}
+
 // ----------------------------------------------------------- traj start
 
-constexpr int kTrajThreads = 256;
+constexpr int kTrajThreads = 128;
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kTrajThreads) traj_start_kernel(const __grid_constant__ TrajArgs a) {
-    __shared__ double sm[2 * kTrajThreads];
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    using Acc = typename std::conditional<kF32, DF, double>::type;
+    using G = typename GradT<T>::type;
+    __shared__ Acc sm[kTrajThreads / 32];
     const int64_t nd = a.n * D;
     const int64_t q = static_cast<int64_t>(blockIdx.x) * kTrajThreads + threadIdx.x;  // 4 elements each
-    T *x = reinterpret_cast<T *>(a.x);
+    T *x = reinterpret_cast<T *>(a.xs.x);
     T *p = reinterpret_cast<T *>(a.p);
     T *x0 = reinterpret_cast<T *>(a.x0);
+    G *grad = reinterpret_cast<G *>(a.grad);
+    G *grad0 = reinterpret_cast<G *>(a.grad0);
     const int64_t iter = a.counters[kIter];
     const int64_t iter_local = a.counters[kIterLocal];
-    double ke = 0.0, xx = 0.0;
-    double z[4] = {0.0, 0.0, 0.0, 0.0};
+    Acc ke{}, xx{};
+    T z[4] = {T(0), T(0), T(0), T(0)};
     if (a.momentum_src == 1 && 4 * q < nd) {
         uint32_t c[4] = {static_cast<uint32_t>(q), static_cast<uint32_t>(iter), a.chain, 0u};
         philox10(c, a.seed);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const double u1 = open_unit(c[2 * h]);
-            const double u2 = open_unit(c[2 * h + 1]);
-            const double rad = sqrt(-2.0 * log(u1));
-            double sn, cs;
-            sincos(kTwoPi * u2, &sn, &cs);
-            z[2 * h] = rad * cs;
-            z[2 * h + 1] = rad * sn;
-        }
+        box_muller(c[0], c[1], z[0], z[1]);
+        box_muller(c[2], c[3], z[2], z[3]);
     }
+    float xmax = 0.f;
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
         const int64_t e = 4 * q + h;
         if (e >= nd) break;
         T pv;
         if (a.momentum_src == 1)
-            pv = static_cast<T>(z[h]);
+            pv = z[h];
         else if (a.momentum_src == 2)
             pv = static_cast<T>(a.p_inj[iter_local * nd + e]);
         else
             pv = p[e];
         const T xv = x[e];
         x0[e] = xv;
-        a.grad0[e] = a.grad[e];
-        ke += 0.5 * static_cast<double>(pv) * static_cast<double>(pv);
-        xx += static_cast<double>(xv) * static_cast<double>(xv);
+        grad0[e] = grad[e];
+        if constexpr (kF32) {
+            df_add(ke, 0.5f * pv * pv);
+            df_add(xx, xv * xv);
+        } else {
+            ke += 0.5 * pv * pv;
+            xx += xv * xv;
+        }
         if (a.drift) {
-            const double tg = a.grad[e] - a.lambda * static_cast<double>(xv);
-            pv = static_cast<T>(static_cast<double>(pv) + 0.5 * a.eps * tg);
-            const T xn = static_cast<T>(static_cast<double>(xv) + a.eps * static_cast<double>(pv));
-            x[e] = xn;
-            store_xneg<T>(a.xneg, e / D, D, static_cast<int>(e % D), xn);
+            const T tg = GradT<T>::value(grad[e]) - static_cast<T>(a.lambda) * xv;
+            pv = pv + static_cast<T>(0.5 * a.eps) * tg;
+            const T xn = xv + static_cast<T>(a.eps) * pv;
+            store_x<T>(a.xs, e / D, D, static_cast<int>(e % D), xn);
+            xmax = fmaxf(xmax, fabsf(static_cast<float>(xn)));
         }
         p[e] = pv;
     }
-    block_sum2<kTrajThreads>(ke, xx, sm);
+    double tk, tx;
+    if constexpr (kF32) {
+        tk = df_double(block_sum_df<kTrajThreads>(ke, sm));
+        tx = df_double(block_sum_df<kTrajThreads>(xx, sm));
+        if (a.drift) {
+            const float m = block_max<kTrajThreads>(xmax, reinterpret_cast<float *>(sm));
+            if (threadIdx.x == 0 && m > 0.f) atomicMax(a.xs.xmax_bits, __float_as_uint(m));
+        }
+    } else {
+        tk = block_sum_d<kTrajThreads>(ke, sm);
+        tx = block_sum_d<kTrajThreads>(xx, sm);
+    }
     if (threadIdx.x == 0) {
-        a.energy_part[2 * blockIdx.x] = ke;
-        a.energy_part[2 * blockIdx.x + 1] = xx;
+        a.energy_part[2 * blockIdx.x] = tk;
+        a.energy_part[2 * blockIdx.x + 1] = tx;
         if (blockIdx.x == 0) {
             a.scal[kLogLik0] = a.scal[kLogLik];
             a.scal[kSumR0] = a.scal[kSumR];
@@ -278,50 +476,60 @@ __global__ void __launch_bounds__(kTrajThreads) traj_start_kernel(const __grid_c
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kTrajThreads) traj_end_kernel(const __grid_constant__ AcceptArgs a) {
+    using G = typename GradT<T>::type;
     // every CTA sums the same partials in the same order -> same decision
     __shared__ int keep_s;
     __shared__ double dh_s;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         double ke0 = 0.0, xx0 = 0.0, ke1 = 0.0, xx1 = 0.0;
-        for (int i = 0; i < a.n_start_parts; ++i) {
+        for (int i = lane; i < a.n_start_parts; i += 32) {
             ke0 += a.start_part[2 * i];
             xx0 += a.start_part[2 * i + 1];
         }
-        for (int i = 0; i < a.n_end_parts; ++i) {
+        for (int i = lane; i < a.n_end_parts; i += 32) {
             ke1 += a.end_part[2 * i];
             xx1 += a.end_part[2 * i + 1];
         }
-        const double h0 = -(a.scal[kLogLik0] - 0.5 * a.lambda * xx0) + ke0;
-        const double h1 = -(a.scal[kLogLikEnd] - 0.5 * a.lambda * xx1) + ke1;
-        const double dh = h1 - h0;
-        int keep = 1;
-        if (a.metropolis) {
-            const int64_t iter = a.counters[kIterCur];
-            double u;
-            if (a.u_src == 2) {
-                u = a.u_inj[a.counters[kIterLocalCur]];
-            } else {
-                uint32_t c[4] = {0u, static_cast<uint32_t>(iter), a.chain, 1u};
-                philox10(c, a.seed);
-                u = open_unit(c[0]);
-            }
-            keep = (isfinite(dh) && log(u) < -dh) ? 1 : 0;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            ke0 += __shfl_xor_sync(0xffffffffu, ke0, o);
+            xx0 += __shfl_xor_sync(0xffffffffu, xx0, o);
+            ke1 += __shfl_xor_sync(0xffffffffu, ke1, o);
+            xx1 += __shfl_xor_sync(0xffffffffu, xx1, o);
         }
-        keep_s = keep;
-        dh_s = dh;
+        if (lane == 0) {
+            const double h0 = -(a.scal[kLogLik0] - 0.5 * a.lambda * xx0) + ke0;
+            const double h1 = -(a.scal[kLogLikEnd] - 0.5 * a.lambda * xx1) + ke1;
+            const double dh = h1 - h0;
+            int keep = 1;
+            if (a.metropolis) {
+                const int64_t iter = a.counters[kIterCur];
+                double u;
+                if (a.u_src == 2) {
+                    u = a.u_inj[a.counters[kIterLocalCur]];
+                } else {
+                    uint32_t c[4] = {0u, static_cast<uint32_t>(iter), a.chain, 1u};
+                    philox10(c, a.seed);
+                    u = open_unit(c[0]);
+                }
+                keep = (isfinite(dh) && log(u) < -dh) ? 1 : 0;
+            }
+            keep_s = keep;
+            dh_s = dh;
+        }
     }
     __syncthreads();
     const int keep = keep_s;
     const int64_t nd = a.n * D;
     if (!keep) {
-        T *x = reinterpret_cast<T *>(a.x);
         const T *x0 = reinterpret_cast<const T *>(a.x0);
+        G *grad = reinterpret_cast<G *>(a.grad);
+        const G *grad0 = reinterpret_cast<const G *>(a.grad0);
         for (int64_t e = static_cast<int64_t>(blockIdx.x) * kTrajThreads + threadIdx.x; e < nd;
              e += static_cast<int64_t>(gridDim.x) * kTrajThreads) {
-            const T xv = x0[e];
-            x[e] = xv;
-            a.grad[e] = a.grad0[e];
-            store_xneg<T>(a.xneg, e / D, D, static_cast<int>(e % D), xv);
+            store_x<T>(a.xs, e / D, D, static_cast<int>(e % D), x0[e]);
+            grad[e] = grad0[e];
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -359,6 +567,15 @@ __global__ void __launch_bounds__(kTrajThreads) traj_end_kernel(const __grid_con
 
 // ----------------------------------------------------------------- ingest
 
+// Inverse of tile_offset(): (row, column) inside a tile of element `off`.
+__device__ __forceinline__ void tile_rc(int off, int &r, int &c) {
+    const int e = off & 3, lane = (off >> 2) & 31, wt = off >> 7;
+    const int t = wt & 7, w = wt >> 3;
+    const int a = lane & 7, b = lane >> 3, q = t >> 1, half = t & 1;
+    r = 2 * (a + 8 * q) + (e & 1);
+    c = 16 * w + 4 * b + 2 * half + (e >> 1);
+}
+
 // One thread per destination element of the tiles of row blocks covering
 // rows [r0, r1).
 __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
@@ -372,7 +589,7 @@ __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t t = t_begin + g / kTileElems;
         const int off = static_cast<int>(g % kTileElems);
-        // locate tile (I, J): row block I is the largest with tile_index(I, I) <= t
+        // row block I is the largest with tile_index(I, I) <= t
         int64_t lo = b0, hi = b1 - 1;
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) / 2;
@@ -383,14 +600,13 @@ __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
         }
         const int64_t I = lo;
         const int64_t J = I + (t - tile_index(I, I, nt));
-        const int chunk = off / (kTile * kChunkCols);
-        const int rem = off % (kTile * kChunkCols);
-        const int rr = rem / kChunkCols;
-        const int cc = chunk * kChunkCols + rem % kChunkCols;
+        int rr, cc;
+        tile_rc(off, rr, cc);
         const int64_t i = I * kTile + rr;
         const int64_t j = J * kTile + cc;
+        const bool in_rows = i >= a.r0 && i < a.r1;
         float v = 0.0f;
-        if (i < j && j < a.n && i >= a.r0 && i < a.r1) {
+        if (i < j && j < a.n && in_rows) {
             double y;
             int64_t idx;
             if (a.packed)
@@ -407,15 +623,14 @@ __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
             }
             v = static_cast<float>(y);
         }
-        if (i >= a.r0 && i < a.r1) a.y[t * kTileElems + off] = v;
-        else if (i >= a.n) a.y[t * kTileElems + off] = 0.0f;  // padding rows of the last block
+        if (in_rows || i >= a.n) a.y[t * kTileElems + off] = v;  // rows past N: padding of the last block
     }
 }
 
 // --------------------------------------------------------------- set x
 
 template <typename T, typename S>
-__global__ void set_x_kernel(const S *src, int64_t n, int64_t n_pad, int d, T *x, T *xneg, unsigned *err) {
+__global__ void set_x_kernel(const S *src, int64_t n, int64_t n_pad, int d, XState xs, unsigned *err) {
     const int64_t total = n_pad * d;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -426,16 +641,42 @@ __global__ void set_x_kernel(const S *src, int64_t n, int64_t n_pad, int d, T *x
             if (!isfinite(sv)) atomicOr(err, kErrBadInput);
             v = static_cast<T>(sv);
         }
-        x[e] = v;
-        store_xneg<T>(xneg, k, d, static_cast<int>(e % d), v);
+        store_x<T>(xs, k, d, static_cast<int>(e % d), v);
     }
 }
 
-template <typename S, typename T>
-__global__ void convert_kernel(const S *src, T *dst, int64_t count) {
+__global__ void resplit_kernel(XState xs, int64_t total, int d) {
+    const float *x = reinterpret_cast<const float *>(xs.x);
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        write_split(xs, e / d, d, static_cast<int>(e % d), x[e]);
+}
+
+template <typename T>
+__global__ void xmax_kernel(const T *x, int64_t count, unsigned *out) {
+    __shared__ float sm[8];
+    float m = 0.f;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        dst[e] = static_cast<T>(src[e]);
+        m = fmaxf(m, fabsf(static_cast<float>(x[e])));
+    m = block_max<256>(m, sm);
+    if (threadIdx.x == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+// src kind: 0 f32, 1 f64, 2 float2 (hi, lo) pairs
+template <typename T>
+__global__ void convert_kernel(const void *src, int kind, T *dst, int64_t count) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (kind == 0)
+            dst[e] = static_cast<T>(reinterpret_cast<const float *>(src)[e]);
+        else if (kind == 1)
+            dst[e] = static_cast<T>(reinterpret_cast<const double *>(src)[e]);
+        else {
+            const float2 g = reinterpret_cast<const float2 *>(src)[e];
+            dst[e] = static_cast<T>(static_cast<double>(g.x) + static_cast<double>(g.y));
+        }
+    }
 }
 
 int grid_for(int64_t work, int threads) {
@@ -486,37 +727,50 @@ cudaError_t launch_ingest(const IngestArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_x(const void *src, bool src_f64, int64_t n, int64_t n_pad, int d, bool fp64, void *x,
-                         void *xneg, unsigned *err, cudaStream_t s) {
+cudaError_t launch_set_x(const void *src, bool src_f64, int64_t n, int64_t n_pad, int d, bool fp64, const XState &xs,
+                         unsigned *err, cudaStream_t s) {
     const int g = grid_for(n_pad * d, 256);
     if (fp64) {
         if (src_f64)
-            set_x_kernel<double, double><<<g, 256, 0, s>>>(static_cast<const double *>(src), n, n_pad, d,
-                                                            static_cast<double *>(x), static_cast<double *>(xneg), err);
+            set_x_kernel<double, double><<<g, 256, 0, s>>>(static_cast<const double *>(src), n, n_pad, d, xs, err);
         else
-            set_x_kernel<double, float><<<g, 256, 0, s>>>(static_cast<const float *>(src), n, n_pad, d,
-                                                           static_cast<double *>(x), static_cast<double *>(xneg), err);
+            set_x_kernel<double, float><<<g, 256, 0, s>>>(static_cast<const float *>(src), n, n_pad, d, xs, err);
     } else {
         if (src_f64)
-            set_x_kernel<float, double><<<g, 256, 0, s>>>(static_cast<const double *>(src), n, n_pad, d,
-                                                           static_cast<float *>(x), static_cast<float *>(xneg), err);
+            set_x_kernel<float, double><<<g, 256, 0, s>>>(static_cast<const double *>(src), n, n_pad, d, xs, err);
         else
-            set_x_kernel<float, float><<<g, 256, 0, s>>>(static_cast<const float *>(src), n, n_pad, d,
-                                                          static_cast<float *>(x), static_cast<float *>(xneg), err);
+            set_x_kernel<float, float><<<g, 256, 0, s>>>(static_cast<const float *>(src), n, n_pad, d, xs, err);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t count, cudaStream_t s) {
+cudaError_t launch_resplit(const XState &xs, int64_t n_pad, int d, cudaStream_t s) {
+    resplit_kernel<<<grid_for(n_pad * d, 256), 256, 0, s>>>(xs, n_pad * d, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xmax(const void *x, bool fp64, int64_t count, unsigned *out, cudaStream_t s) {
     const int g = grid_for(count, 256);
-    if (src_f64 && dst_f64)
-        convert_kernel<double, double><<<g, 256, 0, s>>>(static_cast<const double *>(src), static_cast<double *>(dst), count);
-    else if (src_f64)
-        convert_kernel<double, float><<<g, 256, 0, s>>>(static_cast<const double *>(src), static_cast<float *>(dst), count);
-    else if (dst_f64)
-        convert_kernel<float, double><<<g, 256, 0, s>>>(static_cast<const float *>(src), static_cast<double *>(dst), count);
+    if (fp64)
+        xmax_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(x), count, out);
     else
-        convert_kernel<float, float><<<g, 256, 0, s>>>(static_cast<const float *>(src), static_cast<float *>(dst), count);
+        xmax_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(x), count, out);
+    return cudaGetLastError();
+}
+
+// src_f64: false -> f32, true -> f64; a float2 (hi, lo) source is passed
+// with src_f64 = false and count < 0 (|count| elements).
+cudaError_t launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t count, cudaStream_t s) {
+    int kind = src_f64 ? 1 : 0;
+    if (count < 0) {
+        kind = 2;
+        count = -count;
+    }
+    const int g = grid_for(count, 256);
+    if (dst_f64)
+        convert_kernel<double><<<g, 256, 0, s>>>(src, kind, static_cast<double *>(dst), count);
+    else
+        convert_kernel<float><<<g, 256, 0, s>>>(src, kind, static_cast<float *>(dst), count);
     return cudaGetLastError();
 }
 
