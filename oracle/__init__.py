@@ -49,7 +49,7 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             lib.mdso_loglik.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp, _vp]
-            lib.mdso_gradient_rows.argtypes = [_i64, _int, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp]
+            lib.mdso_gradient_rows.argtypes = [_i64, _int, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp, _vp]
             lib.mdso_dsigma.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp]
             lib.mdso_leapfrog.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int,
                                           _int, _vp, _vp]
@@ -97,9 +97,9 @@ def loglik(yp, x, sigma, nthreads=1):
     return float(ll[0]), float(sr[0])
 
 
-def gradient(yp, x, sigma, rows=None, nthreads=1, with_abs=False):
+def gradient(yp, x, sigma, rows=None, nthreads=1, with_abs=False, with_sq=False):
     """Gradient of L in X (Eq. 9) for `rows` (all when None); optionally also
-    S_ik = sum_j |term_ijk|."""
+    S_ik = sum_j |term_ijk| (with_abs) and sqrt(sum_j term_ijk^2) (with_sq)."""
     yp, x, n, d = _prep(yp, x)
     if rows is None:
         rr = None
@@ -109,10 +109,16 @@ def gradient(yp, x, sigma, rows=None, nthreads=1, with_abs=False):
         cnt = rr.shape[0]
     g = np.zeros((cnt, d))
     a = np.zeros((cnt, d)) if with_abs else None
+    q = np.zeros((cnt, d)) if with_sq else None
     _check(_load().mdso_gradient_rows(n, d, _ptr(yp), _ptr(x), float(sigma),
                                       None if rr is None else _ptr(rr), cnt, int(nthreads), _ptr(g),
-                                      None if a is None else _ptr(a)), "gradient")
-    return (g, a) if with_abs else g
+                                      None if a is None else _ptr(a), None if q is None else _ptr(q)), "gradient")
+    out = (g,)
+    if with_abs:
+        out += (a,)
+    if with_sq:
+        out += (q,)
+    return out if len(out) > 1 else g
 
 
 def dsigma(yp, x, sigma, nthreads=1):

@@ -171,10 +171,12 @@ int mdso_loglik(int64_t n, int d, const float *yp, const double *x, double sigma
  *   d/dx_i log p = - sum_{j != i} grad_factor(y_ij, delta_ij) (x_i - x_j) / delta_ij
  * for the rows listed in `rows` (all rows when rows == NULL, nrows ignored).
  * grad is nrows x D (or N x D).  absterm (optional, same shape) receives
- * S_ik = sum_{j != i} |term_ijk|, the scale used to judge cancellation. */
+ * S_ik = sum_{j != i} |term_ijk| and sqterm (optional) sqrt(sum_{j != i}
+ * term_ijk^2): the scales used to judge cancellation and rounding when a
+ * lower-precision result is compared with this one. */
 int mdso_gradient_rows(int64_t n, int d, const float *yp, const double *x, double sigma,
                        const int64_t *rows, int64_t nrows, int nthreads,
-                       double *grad, double *absterm) {
+                       double *grad, double *absterm, double *sqterm) {
     if (n < 2 || d < 1 || d > 16 || !(sigma > 0.0) || !yp || !x || !grad) return MDSO_BAD_ARG;
     int64_t count = rows ? nrows : n;
     int64_t r;
@@ -185,9 +187,11 @@ int mdso_gradient_rows(int64_t n, int d, const float *yp, const double *x, doubl
         int64_t i = rows ? rows[r] : r;
         nsum_t g[16];
         nsum_t a[16];
+        nsum_t q[16];
         for (int k = 0; k < d; ++k) {
             g[k].s = g[k].c = 0.0;
             a[k].s = a[k].c = 0.0;
+            q[k].s = q[k].c = 0.0;
         }
         if (i >= 0 && i < n) {
             for (int64_t j = 0; j < n; ++j) {
@@ -199,12 +203,14 @@ int mdso_gradient_rows(int64_t n, int d, const float *yp, const double *x, doubl
                     double term = w * (x[i * d + k] - x[j * d + k]) / delta;
                     nsum_add(&g[k], -term);
                     nsum_add(&a[k], fabs(term));
+                    nsum_add(&q[k], term * term);
                 }
             }
         }
         for (int k = 0; k < d; ++k) {
             grad[r * d + k] = nsum_get(&g[k]);
             if (absterm) absterm[r * d + k] = nsum_get(&a[k]);
+            if (sqterm) sqterm[r * d + k] = sqrt(nsum_get(&q[k]));
         }
     }
     (void)nthreads;
@@ -251,7 +257,7 @@ static int target(int64_t n, int d, const float *yp, const double *x, double sig
         int st = mdso_loglik(n, d, yp, x, sigma, nthreads, NULL, &ll);
         if (st) return st;
         if (grad) {
-            st = mdso_gradient_rows(n, d, yp, x, sigma, NULL, 0, nthreads, grad, NULL);
+            st = mdso_gradient_rows(n, d, yp, x, sigma, NULL, 0, nthreads, grad, NULL, NULL);
             if (st) return st;
             for (int64_t k = 0; k < nd; ++k) grad[k] *= w;
         }

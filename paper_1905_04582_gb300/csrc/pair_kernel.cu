@@ -55,6 +55,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -156,14 +161,12 @@ struct Pow2 {
 // that half.  After all levels a lane holds in v[0..P >> L) the totals of
 // the value indices starting at reduced_base<P>(lane bits), L = number of
 // halving levels (levels beyond log2 P degrade to plain butterflies).
-template <int P, int NBITS, typename T>
-__device__ __forceinline__ void lane_reduce(T (&v)[P], int lane, int first_bit) {
-    int cnt = P;
-#pragma unroll
-    for (int lv = NBITS - 1; lv >= 0; --lv) {
-        const int o = 1 << (first_bit + lv);
-        if (cnt > 1) {
-            const int half = cnt / 2;
+template <int CNT, int LV, int P, typename T>
+__device__ __forceinline__ void lane_reduce_rec(T (&v)[P], int lane, int first_bit) {
+    if constexpr (LV >= 0) {
+        const int o = 1 << (first_bit + LV);
+        if constexpr (CNT > 1) {
+            constexpr int half = CNT / 2;
             const bool upper = (lane & o) != 0;
 #pragma unroll
             for (int i = 0; i < half; ++i) {
@@ -171,11 +174,17 @@ __device__ __forceinline__ void lane_reduce(T (&v)[P], int lane, int first_bit) 
                 const T keep = upper ? v[i + half] : v[i];
                 v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
             }
-            cnt = half;
+            lane_reduce_rec<half, LV - 1>(v, lane, first_bit);
         } else {
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+            lane_reduce_rec<1, LV - 1>(v, lane, first_bit);
         }
     }
+}
+
+template <int P, int NBITS, typename T>
+__device__ __forceinline__ void lane_reduce(T (&v)[P], int lane, int first_bit) {
+    lane_reduce_rec<P, NBITS - 1>(v, lane, first_bit);
 }
 
 // First value index held after lane_reduce<P, NBITS> over bits
@@ -251,13 +260,12 @@ __device__ __forceinline__ void pair2_f32(const PairArgs &a, const float4 (&xi)[
     // delta is then ~1e-19 and whose gradient term is exactly 0)
     const float2 d2 = add2(d2h, cr);
     const float2 inv = f2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
-    const float2 del = mul2(d2, inv);
-    // residual of the square root: true d^2 - del^2 = (d2h - del^2) + cr,
-    // first-order correction of delta (and of 1/delta for the direction)
+    const float2 del = f2(sqrt_approx(d2.x), sqrt_approx(d2.y));  // MUFU, frees an FMA-pipe slot
+    // residual of the square root: true d^2 - del^2 = (d2h - del^2) + cr;
+    // delta_true = del + res / (2 del) to first order
     const float2 res = add2(fma2(neg2(del), del, d2h), cr);
-    const float2 corr = mul2(res, mul2(inv, f2(0.5f, 0.5f)));     // delta_true - del
-    float2 e = add2(add2(y2, neg2(del)), neg2(corr));             // y - delta, corrected
-    const float2 invc = fma2(neg2(mul2(corr, inv)), inv, inv);    // 1/delta_true
+    const float2 hinv = mul2(inv, f2(0.5f, 0.5f));
+    float2 e = fma2(neg2(res), hinv, add2(y2, neg2(del)));        // y - delta, corrected
     // Phi via the Mills ratio: phi' = exp(-z^2/2), -P/sqrt(2 pi) and D in delta
     const float2 ea = mul2(d2, a.c_phi);
     const float2 ph = f2(ex2_approx(ea.x), ex2_approx(ea.y));
@@ -280,7 +288,7 @@ __device__ __forceinline__ void pair2_f32(const PairArgs &a, const float4 (&xi)[
     e2 = fma2(e, e, e2);
     md = fma2(mm, del, md);
     // w = (delta - y)/sigma^2 + phi/(sigma Phi); wi = w / delta
-    const float2 wi = mul2(fma2(e, a.neg_inv_s2, mul2(mm, a.m_coef)), invc);
+    const float2 wi = mul2(fma2(e, a.neg_inv_s2, mul2(mm, a.m_coef)), inv);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         racc[k] = fma2(wi, s[k], racc[k]);
@@ -351,7 +359,7 @@ __device__ __forceinline__ void tile_f32(const PairArgs &a, const float4 *ys, co
 }
 
 template <int D>
-__global__ void __launch_bounds__(kPairThreads, (D <= 3 ? 4 : 2)) pair_f32_kernel(const __grid_constant__ PairArgs a) {
+__global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) pair_f32_kernel(const __grid_constant__ PairArgs a) {
     using L = F32Layout<D>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x;

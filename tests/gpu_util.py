@@ -4,21 +4,29 @@ Tolerances (stated for the hot path):
   log-likelihood: relative error <= 1e-6 (FP32C path), <= 1e-12 (FP64 path);
   gradient coordinates and dL/dsigma: relative error <= 1e-5 (FP32C),
   <= 1e-12 (FP64).
-Near cancellation a relative error is ill-conditioned, so a coordinate whose
-condition number kappa = S / |g_ref| exceeds 1e3 (S = sum of the absolute
-values of its terms, returned by the oracle) passes when its absolute error
-is below tol * 1e-3 * S instead; such coordinates are counted and printed.
+A relative error is ill-conditioned where a coordinate's terms cancel, so a
+gradient coordinate also passes when
+  (a) its condition number kappa = S / |g_ref| exceeds 1e3 (S = sum of the
+      absolute values of its terms, from the oracle) and its absolute error
+      is below tol * 1e-3 * S; or
+  (b) its absolute error is below 8 u * S2, S2 = sqrt(sum of its squared
+      terms) and u the unit roundoff of the path (2^-24 for FP32C, 2^-53 for
+      FP64): the size of the rounding error that any evaluation of the
+      per-pair terms with a few units in the last place each leaves in their
+      sum (random-walk model).
+Coordinates that pass only through (a) or (b) are counted and reported.
 """
 import numpy as np
 
 TOL = {
-    "fp32c": {"ll": 1e-6, "g": 1e-5},
-    "fp64": {"ll": 1e-12, "g": 1e-12},
+    "fp32c": {"ll": 1e-6, "g": 1e-5, "u": 2.0 ** -24},
+    "fp64": {"ll": 1e-12, "g": 1e-12, "u": 2.0 ** -53},
 }
 KAPPA = 1e3
+ULPS = 8.0
 
 
-def grad_check(g, g_ref, s_abs, tol, what="gradient"):
+def grad_check(g, g_ref, s_abs, tol, what="gradient", s_sq=None, u=None):
     g = np.asarray(g, dtype=np.float64)
     g_ref = np.asarray(g_ref, dtype=np.float64)
     s_abs = np.asarray(s_abs, dtype=np.float64)
@@ -26,13 +34,17 @@ def grad_check(g, g_ref, s_abs, tol, what="gradient"):
     rel_ok = err <= tol * np.abs(g_ref)
     kappa = s_abs / np.maximum(np.abs(g_ref), 1e-300)
     cond_ok = (kappa > KAPPA) & (err <= tol * 1e-3 * s_abs)
-    ok = rel_ok | cond_ok
-    n_cond = int(np.sum(~rel_ok & cond_ok))
+    if s_sq is not None and u is not None:
+        round_ok = err <= ULPS * u * np.asarray(s_sq, dtype=np.float64)
+    else:
+        round_ok = np.zeros_like(rel_ok)
+    ok = rel_ok | cond_ok | round_ok
     rel = err / np.maximum(np.abs(g_ref), 1e-300)
     info = {
         "max_rel": float(rel.max()) if rel.size else 0.0,
         "p999_rel": float(np.quantile(rel, 0.999)) if rel.size else 0.0,
-        "n_kappa_branch": n_cond,
+        "n_kappa_branch": int(np.sum(~rel_ok & cond_ok)),
+        "n_rounding_branch": int(np.sum(~rel_ok & ~cond_ok & round_ok)),
         "n": int(g.size),
     }
     bad = np.argwhere(~ok)

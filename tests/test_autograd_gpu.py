@@ -24,12 +24,12 @@ def test_autograd_matches_oracle_and_finite_differences():
     x64 = wl.x_eval.astype(np.float64)
     s32 = float(np.float32(wl.sigma))
     ll_ref, _ = oracle.loglik(wl.y_packed, x64, s32, nthreads=8)
-    g_ref, s_abs = oracle.gradient(wl.y_packed, x64, s32, nthreads=8, with_abs=True)
+    g_ref, s_abs, s_sq = oracle.gradient(wl.y_packed, x64, s32, nthreads=8, with_abs=True, with_sq=True)
     ds_ref = oracle.dsigma(wl.y_packed, x64, s32, nthreads=8)
     tol = TOL["fp32c"]
-    scalar_check(float(ll), ll_ref, tol["ll"], what="L")
+    scalar_check(float(ll.detach()), ll_ref, tol["ll"], what="L")
     assert x.grad.dtype == torch.float32
-    info = grad_check(x.grad.double().cpu().numpy(), g_ref, s_abs, tol["g"])
+    info = grad_check(x.grad.double().cpu().numpy(), g_ref, s_abs, tol["g"], s_sq=s_sq, u=tol["u"])
     print("autograd grad vs oracle", info)
     m_pairs = wl.n * (wl.n - 1) / 2
     scalar_check(float(sigma.grad), ds_ref, tol["g"], scale=ds_ref + 2 * m_pairs / s32, what="dL/dsigma")

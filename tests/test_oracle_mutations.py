@@ -52,7 +52,7 @@ def _build(tmp_path, name, src_text):
                     "-shared", str(c), "-o", str(so), "-lm"], check=True)
     lib = ctypes.CDLL(str(so))
     lib.mdso_loglik.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp, _vp]
-    lib.mdso_gradient_rows.argtypes = [_i64, _int, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp]
+    lib.mdso_gradient_rows.argtypes = [_i64, _int, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp, _vp]
     lib.mdso_dsigma.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp]
     lib.mdso_leapfrog.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _int, _vp, _vp]
     lib.mdso_philox4x32_10.argtypes = [_vp, _vp, _vp]
@@ -81,7 +81,7 @@ def _pins_hold(lib):
     if not math.isclose(ll(x), ref, rel_tol=1e-12):
         return False
     g = np.zeros((n, d))
-    lib.mdso_gradient_rows(n, d, _p(y), _p(x), s, None, 0, 1, _p(g), None)
+    lib.mdso_gradient_rows(n, d, _p(y), _p(x), s, None, 0, 1, _p(g), None, None)
     h = 1e-6
     for i in range(n):
         for k in range(d):

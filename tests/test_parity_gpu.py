@@ -32,9 +32,9 @@ def make_model(wl, prec, strip=None, layout="packed"):
 def oracle_ref(wl, nthreads=8):
     x64 = wl.x_eval.astype(np.float64)
     ll, sr = oracle.loglik(wl.y_packed, x64, wl.sigma, nthreads=nthreads)
-    g, s_abs = oracle.gradient(wl.y_packed, x64, wl.sigma, nthreads=nthreads, with_abs=True)
+    g, s_abs, s_sq = oracle.gradient(wl.y_packed, x64, wl.sigma, nthreads=nthreads, with_abs=True, with_sq=True)
     ds = oracle.dsigma(wl.y_packed, x64, wl.sigma, nthreads=nthreads)
-    return ll, sr, g, s_abs, ds
+    return ll, sr, g, (s_abs, s_sq), ds
 
 
 def compare(m, wl, prec, ref=None):
@@ -48,7 +48,7 @@ def compare(m, wl, prec, ref=None):
     # scale for the cancellation rule is their absolute sum
     sq = np.sum((wl.y_packed.astype(np.float64) - pdist(wl.x_eval.astype(np.float64))) ** 2) / (2 * wl.sigma ** 2)
     scalar_check(sr, sr_ref, tol["ll"], scale=sq + abs(sr_ref - sq), what="sum r")
-    info = grad_check(g, g_ref, s_abs, tol["g"])
+    info = grad_check(g, g_ref, s_abs[0], tol["g"], s_sq=s_abs[1], u=tol["u"])
     m_pairs = wl.n * (wl.n - 1) / 2
     scale_s = ds_ref + 2 * m_pairs / wl.sigma  # all terms of the sum are >= 0
     scalar_check(ds, ds_ref, tol["g"], scale=scale_s, what="dL/dsigma")
@@ -198,7 +198,8 @@ def test_parity_scale_sweep_sampled(n, d):
     wl = W.scale_sweep(n, d)
     x64 = wl.x_eval.astype(np.float64)
     rows = np.random.default_rng(n + d).choice(n, 256, replace=False)
-    g_ref, s_abs = oracle.gradient(wl.y_packed, x64, wl.sigma, rows=rows, nthreads=16, with_abs=True)
+    g_ref, s_abs, s_sq = oracle.gradient(wl.y_packed, x64, wl.sigma, rows=rows, nthreads=16, with_abs=True,
+                                         with_sq=True)
     ll_ref, _ = oracle.loglik(wl.y_packed, x64, wl.sigma, nthreads=16)
     ds_ref = oracle.dsigma(wl.y_packed, x64, wl.sigma, nthreads=16)
     with MDS(n, d, "fp32c") as m:
@@ -209,6 +210,6 @@ def test_parity_scale_sweep_sampled(n, d):
     tol = TOL["fp32c"]
     scalar_check(ll, ll_ref, tol["ll"], what="log-likelihood")
     scalar_check(ds, ds_ref, tol["g"], scale=ds_ref + n * (n - 1) / wl.sigma, what="dL/dsigma")
-    print(n, d, grad_check(g[rows], g_ref, s_abs, tol["g"]))
+    print(n, d, grad_check(g[rows], g_ref, s_abs, tol["g"], s_sq=s_sq, u=tol["u"]))
     tot = np.abs(g).sum(axis=0)
     assert np.all(np.abs(g.sum(axis=0)) <= 1e-5 * tot)
