@@ -195,6 +195,34 @@ int mds_time_pass(mds_ctx *ctx, int reps, double *ms_per_pass);
 int mds_set_profiling(mds_ctx *ctx, int on);
 int mds_get_pass_time(const mds_ctx *ctx, int64_t *launches, double *total_ms);
 
+/* Allocation-free evaluation, for callers that must not let a library
+ * allocate device memory: a host program that budgets every byte of the GPU
+ * itself, code running inside a memory allocator's callback (where a nested
+ * allocation could deadlock or recurse), or a real-time loop that must not
+ * allocate after start-up.  The paper has no counterpart to this call; it is
+ * a service of this library.
+ *
+ * Inputs (device memory, caller-owned): y, the full symmetric N x N matrix
+ * (FP32, row stride ld >= N elements, diagonal ignored, values not checked);
+ * x, the N x D locations (FP64).  Outputs: grad, N x D dL/dX (FP64, device);
+ * loglik and dlogl_dsigma (host, optional; when either is given the call
+ * synchronises `stream`).  Work goes on `stream` (NULL: legacy default).
+ * Limits: 2 <= N <= 65536, 1 <= D <= MDS_MAX_D; larger N is rejected with
+ * MDS_ERR_INVALID_ARG and a message from mds_last_error(NULL).
+ *
+ * It calls no cudaMalloc / cudaFree.  Its scratch is one fixed 256 KB array
+ * in the library's device memory (held by every GPU that loads the library
+ * until the process exits), shared by all calls: calls that overlap on the
+ * GPU (different streams, or threads) race on it and must be serialised by
+ * the caller.  Nothing in it needs clearing: every slot a call reads is
+ * written earlier in the same call.  The first call on each device looks up
+ * the scratch's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Each pair is
+ * evaluated twice in FP64 (once per row), so this call is slower than the
+ * context path. */
+int mds_loglik_grad_noalloc(int64_t n, int32_t d, const float *y, int64_t ld, const double *x, double sigma,
+                            double *grad, double *loglik, double *dlogl_dsigma, void *stream);
+
 /* Message of the last failed call on ctx (or of the last failed mds_create
  * in this thread when ctx is NULL).  Never NULL. */
 const char *mds_last_error(const mds_ctx *ctx);

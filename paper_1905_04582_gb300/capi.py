@@ -77,6 +77,7 @@ SIGNATURES = {
     "mds_time_pass": (_int, [_vp, _int, _pdbl]),
     "mds_set_profiling": (_int, [_vp, _int]),
     "mds_get_pass_time": (_int, [_vp, _pi64, _pdbl]),
+    "mds_loglik_grad_noalloc": (_int, [_i64, _i32, _vp, _i64, _vp, _dbl, _vp, _pdbl, _pdbl, _vp]),
     "mds_last_error": (ctypes.c_char_p, [_vp]),
 }
 

@@ -584,6 +584,15 @@ int ensure_out_cap(mds_ctx *c, size_t n_iter) {
 
 }  // namespace
 
+void mds::set_thread_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_create_error = buf;
+}
+
 // ====================================================================== ABI
 
 extern "C" {

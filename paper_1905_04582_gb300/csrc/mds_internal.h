@@ -277,6 +277,9 @@ cudaError_t launch_xmax(const void *x, bool fp64, int64_t count, unsigned *out, 
 // Copy / convert an array between element types (device to device).
 cudaError_t launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t count, cudaStream_t s);
 
+// Set the message mds_last_error(NULL) returns in the calling thread.
+void set_thread_error(const char *fmt, ...);
+
 // Bits B of the exact-difference split for D dimensions (see above).
 __host__ __device__ inline int split_bits(int d) { return d <= 1 ? 12 : d <= 4 ? 11 : 10; }
 
