@@ -195,6 +195,51 @@ int mds_time_pass(mds_ctx *ctx, int reps, double *ms_per_pass);
 int mds_set_profiling(mds_ctx *ctx, int on);
 int mds_get_pass_time(const mds_ctx *ctx, int64_t *launches, double *total_ms);
 
+/* ------------------------------------------------------------------------
+ * Batches: several independent datasets (own Y, N, sigma; the same D), each
+ * with several HMC chains, advanced together (the paper fits four virus
+ * subtypes, section 3; batching independent problems is this library's
+ * service).  Each leapfrog step of all chains is ONE persistent launch of the
+ * batched pair pass (every Y tile is read once per step and serves all chains
+ * of its dataset) plus one batched reduction; an HMC iteration of all chains
+ * is one CUDA graph.  FP32C arithmetic only.  Datasets are numbered
+ * 0..n_data-1, chains 0..chains[d]-1; "global chain" g counts chains dataset
+ * by dataset and keys each chain's Philox stream (counter word 2 = g).
+ * ------------------------------------------------------------------------ */
+typedef struct mds_batch mds_batch;
+
+/* n[n_data] item counts, chains[n_data] chains per dataset (1..1024), D for
+ * all, flags MDS_PREC_FP32C.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+int mds_batch_create(int32_t n_data, const int64_t *n, int32_t d, const int32_t *chains, uint32_t flags,
+                     mds_batch **out);
+int mds_batch_destroy(mds_batch *b);
+int mds_batch_set_stream(mds_batch *b, void *stream);
+/* As mds_set_data / mds_set_sigma, for one dataset (all its chains). */
+int mds_batch_set_data(mds_batch *b, int32_t dataset, const void *y, int dtype, int layout, int64_t ld, int where);
+int mds_batch_set_sigma(mds_batch *b, int32_t dataset, double sigma);
+/* As mds_set_locations / mds_get_locations, for one chain. */
+int mds_batch_set_locations(mds_batch *b, int32_t dataset, int32_t chain, const void *x, int dtype, int where);
+int mds_batch_get_locations(mds_batch *b, int32_t dataset, int32_t chain, void *x, int dtype, int where);
+/* dL/dX of one chain at its current locations (evaluates the batch if needed). */
+int mds_batch_get_gradient(mds_batch *b, int32_t dataset, int32_t chain, void *g, int dtype, int where);
+/* One batched pass for all chains: loglik[g] and dlogl_dsigma[g] (host, per
+ * global chain, optional).  Synchronises. */
+int mds_batch_evaluate(mds_batch *b, double *loglik, double *dlogl_dsigma);
+/* n_iter HMC iterations of n_steps leapfrog steps for every chain, eps[d] the
+ * step size of dataset d; momenta and uniforms from Philox keyed by `seed`
+ * (counters as in mds_hmc with chain = global chain).  accepted and dh
+ * (optional, host) receive n_iter x (total chains) values, iteration-major.
+ * Synchronises. */
+int mds_batch_hmc(mds_batch *b, int n_iter, int n_steps, const double *eps, uint64_t seed, int32_t *accepted,
+                  double *dh);
+/* Tiles per strip of the batched pass (0: autotune over 1..4 by timing). */
+int mds_batch_set_strip(mds_batch *b, int32_t strip);
+int mds_batch_get_strip(const mds_batch *b, int32_t *strip);
+/* Mean milliseconds of one batched evaluation (pair pass + reduction) over reps. */
+int mds_batch_time_pass(mds_batch *b, int reps, double *ms_per_pass);
+/* Message of the last failed batch call (NULL: last failed mds_batch_create). */
+const char *mds_batch_last_error(const mds_batch *b);
+
 /* Allocation-free evaluation, for callers that must not let a library
  * allocate device memory: a host program that budgets every byte of the GPU
  * itself, code running inside a memory allocator's callback (where a nested

@@ -77,6 +77,20 @@ SIGNATURES = {
     "mds_time_pass": (_int, [_vp, _int, _pdbl]),
     "mds_set_profiling": (_int, [_vp, _int]),
     "mds_get_pass_time": (_int, [_vp, _pi64, _pdbl]),
+    "mds_batch_create": (_int, [_i32, _vp, _i32, _vp, _u32, ctypes.POINTER(_vp)]),
+    "mds_batch_destroy": (_int, [_vp]),
+    "mds_batch_set_stream": (_int, [_vp, _vp]),
+    "mds_batch_set_data": (_int, [_vp, _i32, _vp, _int, _int, _i64, _int]),
+    "mds_batch_set_sigma": (_int, [_vp, _i32, _dbl]),
+    "mds_batch_set_locations": (_int, [_vp, _i32, _i32, _vp, _int, _int]),
+    "mds_batch_get_locations": (_int, [_vp, _i32, _i32, _vp, _int, _int]),
+    "mds_batch_get_gradient": (_int, [_vp, _i32, _i32, _vp, _int, _int]),
+    "mds_batch_evaluate": (_int, [_vp, _vp, _vp]),
+    "mds_batch_hmc": (_int, [_vp, _int, _int, _vp, _u64, _vp, _vp]),
+    "mds_batch_set_strip": (_int, [_vp, _i32]),
+    "mds_batch_get_strip": (_int, [_vp, _pi32]),
+    "mds_batch_time_pass": (_int, [_vp, _int, _pdbl]),
+    "mds_batch_last_error": (ctypes.c_char_p, [_vp]),
     "mds_loglik_grad_noalloc": (_int, [_i64, _i32, _vp, _i64, _vp, _dbl, _vp, _pdbl, _pdbl, _vp]),
     "mds_last_error": (ctypes.c_char_p, [_vp]),
 }

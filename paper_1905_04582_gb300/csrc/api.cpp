@@ -98,6 +98,9 @@ struct mds_ctx {
     std::tuple<uint64_t, int, double, int, int, uint64_t, int> graph_key{};
     int graph_prof = 0;       // event pairs inside the captured graph
 
+    bool y_owned = true;              // false for the chain contexts of a batch that share Y
+    std::vector<Strip> strips_host;   // the strip list as uploaded (batched launches reuse it)
+
     std::string last_error = "no error";
 };
 
@@ -231,6 +234,7 @@ int build_strips(mds_ctx *c, int strip) {
         CHECK(dev_alloc_t(c, &c->scal_part, spb));
         c->scal_part_bytes = spb;
     }
+    c->strips_host = v;
     CU(cudaMemcpyAsync(c->strips, v.data(), sb, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->row_first, first.data(), (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -505,10 +509,7 @@ int valid_enums(mds_ctx *c, int dtype, int where) {
     return MDS_OK;
 }
 
-// Enqueue one trajectory: start kernel, n_steps fused pair passes with their
-// leapfrog updates, end kernel (Metropolis when metropolis != 0).
-int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, int u_src, int metropolis,
-                       uint64_t seed, cudaStream_t s) {
+TrajArgs make_traj_args(const mds_ctx *c, int n_steps, double eps, int momentum_src, uint64_t seed, uint32_t chain) {
     TrajArgs t{};
     t.n = c->n;
     t.d = c->d;
@@ -518,7 +519,7 @@ int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, in
     t.momentum_src = momentum_src;
     t.p_inj = c->p_inj;
     t.seed = seed;
-    t.chain = 0;
+    t.chain = chain;
     t.xs = xstate(c);
     t.p = c->p;
     t.x0 = c->x0;
@@ -528,31 +529,30 @@ int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, in
     t.counters = c->counters;
     t.energy_part = c->e_start;
     t.drift = n_steps > 0 ? 1 : 0;
-    int grid = 0;
-    cudaError_t e = launch_traj_start(t, &grid, s);
-    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "trajectory start: %s", cudaGetErrorString(e));
-    c->start_grid = grid;
-    for (int k = 0; k < n_steps; ++k)
-        CHECK(enqueue_pass(c, k + 1 < n_steps ? kModeKickDrift : kModeHalfKick, eps, s));
+    return t;
+}
+
+AcceptArgs make_accept_args(const mds_ctx *c, int n_steps, int metropolis, int u_src, uint64_t seed, uint32_t chain,
+                            int start_grid, int32_t *acc_out, double *dh_out) {
     AcceptArgs a{};
     a.n = c->n;
     a.d = c->d;
     a.fp64 = c->fp64;
     a.metropolis = metropolis;
-    a.n_start_parts = grid;
+    a.n_start_parts = start_grid;
     a.start_part = c->e_start;
     if (n_steps > 0) {
         a.n_end_parts = static_cast<int32_t>(c->nt);
         a.end_part = c->e_end;
     } else {
-        a.n_end_parts = grid;
+        a.n_end_parts = start_grid;
         a.end_part = c->e_start;
     }
     a.lambda = c->lambda;
     a.u_src = u_src;
     a.u_inj = c->u_inj;
     a.seed = seed;
-    a.chain = 0;
+    a.chain = chain;
     a.xs = xstate(c);
     a.x0 = c->x0;
     a.grad = static_cast<double *>(c->grad);
@@ -560,10 +560,25 @@ int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, in
     a.scal = c->scal;
     a.counters = c->counters;
     // per-iteration outputs only for Metropolis runs (their index is the
-    // iteration within the current mds_hmc call, below out_cap)
-    a.acc_out = metropolis ? c->acc_out : nullptr;
-    a.dh_out = metropolis ? c->dh_out : nullptr;
+    // iteration within the current HMC call, below the output capacity)
+    a.acc_out = metropolis ? acc_out : nullptr;
+    a.dh_out = metropolis ? dh_out : nullptr;
     a.err = c->err;
+    return a;
+}
+
+// Enqueue one trajectory: start kernel, n_steps fused pair passes with their
+// leapfrog updates, end kernel (Metropolis when metropolis != 0).
+int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, int u_src, int metropolis,
+                       uint64_t seed, cudaStream_t s) {
+    TrajArgs t = make_traj_args(c, n_steps, eps, momentum_src, seed, 0);
+    int grid = 0;
+    cudaError_t e = launch_traj_start(t, &grid, s);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "trajectory start: %s", cudaGetErrorString(e));
+    c->start_grid = grid;
+    for (int k = 0; k < n_steps; ++k)
+        CHECK(enqueue_pass(c, k + 1 < n_steps ? kModeKickDrift : kModeHalfKick, eps, s));
+    AcceptArgs a = make_accept_args(c, n_steps, metropolis, u_src, seed, 0, grid, c->acc_out, c->dh_out);
     e = launch_traj_end(a, s);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "trajectory end: %s", cudaGetErrorString(e));
     return MDS_OK;
@@ -597,7 +612,11 @@ void mds::set_thread_error(const char *fmt, ...) {
 
 extern "C" {
 
-int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out) {
+}  // extern "C"
+
+namespace {
+
+int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out) {
     mds_ctx *c = nullptr;
     if (!out) return fail(c, MDS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -633,7 +652,9 @@ int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out) {
     const size_t eb = elem(c);
     const int64_t nd_pad = c->n_pad * d;
     int st = MDS_OK;
-    if ((st = dev_alloc_t(c, &c->y, static_cast<size_t>(c->tiles) * kTileElems * sizeof(float)))) return cleanup(st);
+    c->y_owned = alloc_y;
+    if (alloc_y && (st = dev_alloc_t(c, &c->y, static_cast<size_t>(c->tiles) * kTileElems * sizeof(float))))
+        return cleanup(st);
     if ((st = dev_alloc(c, &c->x, nd_pad * eb))) return cleanup(st);
     if ((st = dev_alloc(c, &c->p, nd_pad * eb))) return cleanup(st);
     if ((st = dev_alloc(c, &c->x0, nd_pad * eb))) return cleanup(st);
@@ -681,11 +702,18 @@ int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out) {
     return MDS_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int mds_create(int64_t n, int32_t d, uint32_t flags, mds_ctx **out) { return create_ctx(n, d, flags, true, out); }
+
 int mds_destroy(mds_ctx *c) {
     if (!c) return MDS_OK;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (!c->y_owned) c->y = nullptr;
     void *bufs[] = {c->y,        c->x,        c->p,         c->x0,       c->xrow,      c->xcol,
                     c->split,    c->xmax_bits, c->grad,     c->grad0,    c->col_part,  c->row_part,
                     c->scal_part, c->strips,  c->row_first, c->scal,     c->counters,  c->err,
@@ -1084,6 +1112,529 @@ int mds_get_pass_time(const mds_ctx *c, int64_t *launches, double *total_ms) {
 const char *mds_last_error(const mds_ctx *c) {
     if (!c) return g_create_error.c_str();
     return c->last_error.c_str();
+}
+
+}  // extern "C"
+
+// ====================================================================== batch
+//
+// A batch is a set of datasets, each with its own chains.  Every chain is a
+// full context (locations, momenta, gradient, partial sums, counters); the
+// chains of a dataset share that dataset's tile-packed Y (owned by its first
+// chain).  Batched launches read per-chain argument tables in device memory,
+// so one launch per step serves all chains.
+
+struct mds_batch {
+    int32_t n_data = 0, d = 0;
+    std::vector<int64_t> n;
+    std::vector<int32_t> chains, chain0;
+    std::vector<mds_ctx *> ctx;  // dataset-major
+    int device = 0, sm_count = 0;
+    std::string device_name;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int32_t strip = 0, strip_req = 0;
+    BatchDataset *ds_dev = nullptr;
+    BatchChain *ch_dev = nullptr;
+    BatchStrip *strips_dev = nullptr;
+    size_t strips_cap = 0;
+    int32_t n_strips = 0;
+    ReduceArgs *rcfg = nullptr;
+    int2 *jobs = nullptr;
+    size_t jobs_cap = 0;
+    int32_t n_jobs = 0;
+    TrajArgs *tcfg = nullptr;
+    AcceptArgs *acfg = nullptr;
+    int32_t *acc_out = nullptr;
+    double *dh_out = nullptr;
+    size_t out_cap = 0;
+    int grid = 0;              // persistent grid of the batched pair pass
+    int max_start_grid = 0;
+    int64_t max_nd = 0;
+    uint64_t gen = 1;
+    cudaGraphExec_t graph = nullptr;
+    std::tuple<uint64_t, int> graph_key{};
+    std::string last_error = "no error";
+};
+
+namespace {
+
+int bfail(mds_batch *b, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b)
+        b->last_error = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define BCU(call)                                                                                                 \
+    do {                                                                                                          \
+        cudaError_t e_ = (call);                                                                                  \
+        if (e_ != cudaSuccess)                                                                                    \
+            return bfail(b, MDS_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// Run a context-level call and carry its message up to the batch.
+int bpass(mds_batch *b, mds_ctx *c, int st) {
+    if (st != MDS_OK) b->last_error = c->last_error;
+    return st;
+}
+#define BCHECK(c, call)                      \
+    do {                                     \
+        int s_ = bpass(b, (c), (call));      \
+        if (s_ != MDS_OK) return s_;         \
+    } while (0)
+
+int batch_chain(mds_batch *b, int32_t dataset, int32_t chain, mds_ctx **c) {
+    if (!b) return MDS_ERR_INVALID_ARG;
+    if (dataset < 0 || dataset >= b->n_data) return bfail(b, MDS_ERR_INVALID_ARG, "dataset %d out of range", dataset);
+    if (chain < 0 || chain >= b->chains[dataset]) return bfail(b, MDS_ERR_INVALID_ARG, "chain %d out of range", chain);
+    *c = b->ctx[b->chain0[dataset] + chain];
+    BCU(cudaSetDevice(b->device));
+    return MDS_OK;
+}
+
+template <typename P>
+int bdev_alloc(mds_batch *b, P **p, size_t bytes) {
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, e == cudaErrorMemoryAllocation ? MDS_ERR_OOM : MDS_ERR_CUDA, "cudaMalloc of %zu bytes: %s",
+                     bytes, cudaGetErrorString(e));
+    }
+    *p = static_cast<P *>(v);
+    return MDS_OK;
+}
+
+// Bring every chain to the batch strip length, refresh the location splits,
+// and (re)build the device tables of the batched pair pass and reduction.
+int batch_tables(mds_batch *b, int strip) {
+    const int total = static_cast<int>(b->ctx.size());
+    for (mds_ctx *c : b->ctx) {
+        CHECK(bpass(b, c, ready(c)));
+        c->strip_req = strip;
+        if (c->strip != strip) CHECK(bpass(b, c, build_strips(c, strip)));
+        CHECK(bpass(b, c, refresh_split(c, false)));
+    }
+    std::vector<BatchDataset> ds(b->n_data);
+    std::vector<BatchChain> ch(total);
+    std::vector<BatchStrip> st;
+    std::vector<int2> jobs;
+    std::vector<ReduceArgs> rc(total);
+    for (int dd = 0; dd < b->n_data; ++dd) {
+        const mds_ctx *c0 = b->ctx[b->chain0[dd]];
+        const PairArgs pa = pair_args(c0);
+        BatchDataset &x = ds[dd];
+        x.y = c0->y;
+        x.n = c0->n;
+        x.nt = static_cast<int32_t>(c0->nt);
+        x.chain0 = b->chain0[dd];
+        x.n_chains = b->chains[dd];
+        for (int k = 0; k < 4; ++k) {
+            x.mp[k] = pa.mp[k];
+            x.md[k] = pa.md[k];
+        }
+        x.c_phi = pa.c_phi;
+        x.neg_inv_s2 = pa.neg_inv_s2;
+        x.m_coef = pa.m_coef;
+        for (size_t i = 0; i < c0->strips_host.size(); ++i) {
+            const Strip &s = c0->strips_host[i];
+            st.push_back(BatchStrip{dd, s.I, s.j0, s.j1, s.row_slot, static_cast<int32_t>(i)});
+        }
+    }
+    std::stable_sort(st.begin(), st.end(),
+                     [](const BatchStrip &p, const BatchStrip &q) { return (p.j1 - p.j0) > (q.j1 - q.j0); });
+    for (int g = 0; g < total; ++g) {
+        const mds_ctx *c = b->ctx[g];
+        ch[g] = BatchChain{c->xrow, c->xcol, static_cast<float *>(c->row_part), static_cast<float *>(c->col_part),
+                           static_cast<float *>(c->scal_part)};
+        rc[g] = reduce_args(c, kModeEval, 0.0);
+        for (int J = 0; J < c->nt; ++J) jobs.push_back(make_int2(g, J));
+        jobs.push_back(make_int2(g, -1));
+    }
+    if (st.size() > b->strips_cap) {
+        if (b->strips_dev) cudaFree(b->strips_dev);
+        b->strips_dev = nullptr;
+        CHECK(bdev_alloc(b, &b->strips_dev, st.size() * sizeof(BatchStrip)));
+        b->strips_cap = st.size();
+        b->gen++;
+    }
+    if (jobs.size() > b->jobs_cap) {
+        if (b->jobs) cudaFree(b->jobs);
+        b->jobs = nullptr;
+        CHECK(bdev_alloc(b, &b->jobs, jobs.size() * sizeof(int2)));
+        b->jobs_cap = jobs.size();
+        b->gen++;
+    }
+    BCU(cudaMemcpyAsync(b->ds_dev, ds.data(), ds.size() * sizeof(BatchDataset), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->ch_dev, ch.data(), ch.size() * sizeof(BatchChain), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->strips_dev, st.data(), st.size() * sizeof(BatchStrip), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->jobs, jobs.data(), jobs.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->rcfg, rc.data(), rc.size() * sizeof(ReduceArgs), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    if (static_cast<int32_t>(st.size()) != b->n_strips || static_cast<int32_t>(jobs.size()) != b->n_jobs ||
+        strip != b->strip)
+        b->gen++;
+    b->n_strips = static_cast<int32_t>(st.size());
+    b->n_jobs = static_cast<int32_t>(jobs.size());
+    b->strip = strip;
+    const int per_sm = pair_batch_blocks_per_sm(b->d, strip);
+    if (per_sm <= 0) return bfail(b, MDS_ERR_CUDA, "batched pass does not fit on an SM (strip %d)", strip);
+    b->grid = std::min(b->n_strips, per_sm * b->sm_count);
+    return MDS_OK;
+}
+
+BatchPairArgs batch_pair_args(const mds_batch *b) {
+    BatchPairArgs a{};
+    a.ds = b->ds_dev;
+    a.ch = b->ch_dev;
+    a.strips = b->strips_dev;
+    a.n_strips = b->n_strips;
+    a.strip_cap = b->strip;
+    a.err = b->ctx[0]->err;
+    return a;
+}
+
+int batch_enqueue_pass(mds_batch *b, int mode, cudaStream_t s) {
+    cudaError_t e = launch_pair_batch(batch_pair_args(b), b->d, b->grid, s);
+    if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batched pair pass: %s", cudaGetErrorString(e));
+    e = launch_reduce_batch(b->rcfg, b->jobs, b->n_jobs, b->d, mode, s);
+    if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batched reduction: %s", cudaGetErrorString(e));
+    return MDS_OK;
+}
+
+int batch_check_errors(mds_batch *b, const char *what) {
+    BCU(cudaStreamSynchronize(b->stream));
+    for (mds_ctx *c : b->ctx) CHECK(bpass(b, c, check_device_err(c, what)));
+    return MDS_OK;
+}
+
+std::mutex g_btune_mu;
+std::map<std::tuple<std::string, std::vector<int64_t>, int>, int> g_btune_cache;
+
+// Batch strip length: forced, cached, or timed over a few candidates.
+int batch_autotune(mds_batch *b) {
+    int s = b->strip_req;
+    if (s <= 0) {
+        const auto key = std::make_tuple(b->device_name, b->n, static_cast<int>(b->d));
+        {
+            std::lock_guard<std::mutex> lk(g_btune_mu);
+            auto it = g_btune_cache.find(key);
+            if (it != g_btune_cache.end()) s = it->second;
+        }
+        if (s <= 0) {
+            float best_ms = 1e30f;
+            for (int cand : {1, 2, 3, 4}) {
+                if (pair_batch_blocks_per_sm(b->d, cand) <= 0) continue;
+                CHECK(batch_tables(b, cand));
+                for (int w = 0; w < 2; ++w) CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
+                BCU(cudaEventRecord(b->ev0, b->stream));
+                for (int w = 0; w < 5; ++w) CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
+                BCU(cudaEventRecord(b->ev1, b->stream));
+                BCU(cudaEventSynchronize(b->ev1));
+                float ms = 0.f;
+                BCU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    s = cand;
+                }
+            }
+            CHECK(batch_check_errors(b, "batch autotune"));
+            std::lock_guard<std::mutex> lk(g_btune_mu);
+            g_btune_cache[key] = s;
+        }
+    }
+    return batch_tables(b, s);
+}
+
+int batch_evaluate(mds_batch *b) {
+    CHECK(batch_autotune(b));
+    CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
+    CHECK(batch_check_errors(b, "batch evaluation"));
+    for (mds_ctx *c : b->ctx) c->grad_valid = true;
+    return MDS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mds_batch_create(int32_t n_data, const int64_t *n, int32_t d, const int32_t *chains, uint32_t flags,
+                     mds_batch **out) {
+    mds_batch *b = nullptr;
+    if (!out) return bfail(b, MDS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_data < 1 || !n || !chains) return bfail(b, MDS_ERR_INVALID_ARG, "need n_data >= 1 and the N and chain arrays");
+    if (flags != MDS_PREC_FP32C) return bfail(b, MDS_ERR_UNSUPPORTED, "batches run the FP32C path only");
+    if (d < 1 || d > MDS_MAX_D) return bfail(b, MDS_ERR_INVALID_ARG, "D must be in [1, %d]", MDS_MAX_D);
+    for (int i = 0; i < n_data; ++i)
+        if (chains[i] < 1 || chains[i] > 1024 || n[i] < 2)
+            return bfail(b, MDS_ERR_INVALID_ARG, "dataset %d: need N >= 2 and 1 <= chains <= 1024", i);
+    b = new (std::nothrow) mds_batch();
+    if (!b) return bfail(nullptr, MDS_ERR_OOM, "host allocation failed");
+    b->n_data = n_data;
+    b->d = d;
+    int total = 0;
+    for (int i = 0; i < n_data; ++i) {
+        b->n.push_back(n[i]);
+        b->chains.push_back(chains[i]);
+        b->chain0.push_back(total);
+        total += chains[i];
+    }
+    auto cleanup = [&](int st) {
+        g_create_error = b->last_error;
+        mds_batch_destroy(b);
+        return st;
+    };
+    for (int i = 0; i < n_data; ++i) {
+        for (int c = 0; c < chains[i]; ++c) {
+            mds_ctx *x = nullptr;
+            const int st = create_ctx(n[i], d, MDS_PREC_FP32C, c == 0, &x);
+            if (st != MDS_OK) {
+                b->last_error = g_create_error;
+                return cleanup(st);
+            }
+            if (c > 0) x->y = b->ctx[b->chain0[i]]->y;  // shared, owned by the dataset's first chain
+            b->ctx.push_back(x);
+        }
+    }
+    b->device = b->ctx[0]->device;
+    b->sm_count = b->ctx[0]->sm_count;
+    b->device_name = b->ctx[0]->device_name;
+    int st = MDS_OK;
+    if ((st = bdev_alloc(b, &b->ds_dev, n_data * sizeof(BatchDataset)))) return cleanup(st);
+    if ((st = bdev_alloc(b, &b->ch_dev, total * sizeof(BatchChain)))) return cleanup(st);
+    if ((st = bdev_alloc(b, &b->rcfg, total * sizeof(ReduceArgs)))) return cleanup(st);
+    if ((st = bdev_alloc(b, &b->tcfg, total * sizeof(TrajArgs)))) return cleanup(st);
+    if ((st = bdev_alloc(b, &b->acfg, total * sizeof(AcceptArgs)))) return cleanup(st);
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+        b->last_error = "stream/event creation failed";
+        return cleanup(MDS_ERR_CUDA);
+    }
+    *out = b;
+    return MDS_OK;
+}
+
+int mds_batch_destroy(mds_batch *b) {
+    if (!b) return MDS_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    void *bufs[] = {b->ds_dev, b->ch_dev, b->strips_dev, b->rcfg, b->jobs, b->tcfg, b->acfg, b->acc_out, b->dh_out};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    // chains other than a dataset's first do not own Y
+    for (size_t g = 0; g < b->ctx.size(); ++g) mds_destroy(b->ctx[g]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+    return MDS_OK;
+}
+
+int mds_batch_set_stream(mds_batch *b, void *stream) {
+    if (!b) return MDS_ERR_INVALID_ARG;
+    b->stream = static_cast<cudaStream_t>(stream);
+    for (mds_ctx *c : b->ctx) c->stream = b->stream;
+    return MDS_OK;
+}
+
+int mds_batch_set_data(mds_batch *b, int32_t dataset, const void *y, int dtype, int layout, int64_t ld, int where) {
+    mds_ctx *c0 = nullptr;
+    CHECK(batch_chain(b, dataset, 0, &c0));
+    const int st = mds_set_data(c0, y, dtype, layout, ld, where);
+    for (int c = 0; c < b->chains[dataset]; ++c) {
+        mds_ctx *x = b->ctx[b->chain0[dataset] + c];
+        x->have_data = c0->have_data;
+        x->grad_valid = false;
+    }
+    return bpass(b, c0, st);
+}
+
+int mds_batch_set_sigma(mds_batch *b, int32_t dataset, double sigma) {
+    mds_ctx *c0 = nullptr;
+    CHECK(batch_chain(b, dataset, 0, &c0));
+    for (int c = 0; c < b->chains[dataset]; ++c) {
+        mds_ctx *x = b->ctx[b->chain0[dataset] + c];
+        BCHECK(x, mds_set_sigma(x, sigma));
+    }
+    return MDS_OK;
+}
+
+int mds_batch_set_locations(mds_batch *b, int32_t dataset, int32_t chain, const void *x, int dtype, int where) {
+    mds_ctx *c = nullptr;
+    CHECK(batch_chain(b, dataset, chain, &c));
+    return bpass(b, c, mds_set_locations(c, x, dtype, where));
+}
+
+int mds_batch_get_locations(mds_batch *b, int32_t dataset, int32_t chain, void *x, int dtype, int where) {
+    mds_ctx *c = nullptr;
+    CHECK(batch_chain(b, dataset, chain, &c));
+    return bpass(b, c, mds_get_locations(c, x, dtype, where));
+}
+
+int mds_batch_get_gradient(mds_batch *b, int32_t dataset, int32_t chain, void *g, int dtype, int where) {
+    mds_ctx *c = nullptr;
+    CHECK(batch_chain(b, dataset, chain, &c));
+    if (!g) return bfail(b, MDS_ERR_INVALID_ARG, "g is NULL");
+    CHECK(bpass(b, c, valid_enums(c, dtype, where)));
+    if (!c->grad_valid) CHECK(batch_evaluate(b));
+    return bpass(b, c, copy_out(c, c->grad, 2, g, dtype, where, c->n * c->d));
+}
+
+int mds_batch_evaluate(mds_batch *b, double *loglik, double *dlogl_dsigma) {
+    if (!b) return MDS_ERR_INVALID_ARG;
+    BCU(cudaSetDevice(b->device));
+    CHECK(batch_evaluate(b));
+    for (size_t g = 0; g < b->ctx.size(); ++g) {
+        double s[kScalars];
+        BCU(cudaMemcpyAsync(s, b->ctx[g]->scal, sizeof(s), cudaMemcpyDeviceToHost, b->stream));
+        BCU(cudaStreamSynchronize(b->stream));
+        if (loglik) loglik[g] = s[kLogLik];
+        if (dlogl_dsigma) dlogl_dsigma[g] = s[kDSigma];
+    }
+    return MDS_OK;
+}
+
+int mds_batch_hmc(mds_batch *b, int n_iter, int n_steps, const double *eps, uint64_t seed, int32_t *accepted,
+                  double *dh) {
+    if (!b) return MDS_ERR_INVALID_ARG;
+    BCU(cudaSetDevice(b->device));
+    if (n_iter < 0 || n_steps < 0 || !eps) return bfail(b, MDS_ERR_INVALID_ARG, "need n_iter, n_steps >= 0 and eps");
+    for (int i = 0; i < b->n_data; ++i)
+        if (!std::isfinite(eps[i])) return bfail(b, MDS_ERR_INVALID_ARG, "eps[%d] is not finite", i);
+    bool valid = true;
+    for (mds_ctx *c : b->ctx) valid = valid && c->grad_valid;
+    if (!valid)
+        CHECK(batch_evaluate(b));
+    else
+        CHECK(batch_autotune(b));
+    if (n_iter == 0) return MDS_OK;
+    const int total = static_cast<int>(b->ctx.size());
+    if (static_cast<size_t>(n_iter) > b->out_cap) {
+        if (b->acc_out) cudaFree(b->acc_out);
+        if (b->dh_out) cudaFree(b->dh_out);
+        b->acc_out = nullptr;
+        b->dh_out = nullptr;
+        CHECK(bdev_alloc(b, &b->acc_out, static_cast<size_t>(n_iter) * total * sizeof(int32_t)));
+        CHECK(bdev_alloc(b, &b->dh_out, static_cast<size_t>(n_iter) * total * sizeof(double)));
+        b->out_cap = n_iter;
+    }
+    // per-chain trajectory tables (contents may change between calls; the
+    // captured graph reads them from device memory)
+    std::vector<TrajArgs> tc(total);
+    std::vector<AcceptArgs> ac(total);
+    int max_grid = 0;
+    int64_t max_nd = 0;
+    for (int dd = 0; dd < b->n_data; ++dd) {
+        for (int k = 0; k < b->chains[dd]; ++k) {
+            const int g = b->chain0[dd] + k;
+            mds_ctx *c = b->ctx[g];
+            const int sg = traj_start_grid(c->n, c->d);
+            max_grid = std::max(max_grid, sg);
+            max_nd = std::max<int64_t>(max_nd, c->n * c->d);
+            tc[g] = make_traj_args(c, n_steps, eps[dd], 1, seed, static_cast<uint32_t>(g));
+            ac[g] = make_accept_args(c, n_steps, 1, 1, seed, static_cast<uint32_t>(g), sg,
+                                     b->acc_out + static_cast<size_t>(g) * n_iter,
+                                     b->dh_out + static_cast<size_t>(g) * n_iter);
+            BCU(cudaMemsetAsync(c->counters + kIterLocal, 0, sizeof(int64_t), b->stream));
+        }
+    }
+    std::vector<ReduceArgs> rc(total);
+    for (int dd = 0; dd < b->n_data; ++dd)
+        for (int k = 0; k < b->chains[dd]; ++k) {
+            const int g = b->chain0[dd] + k;
+            rc[g] = reduce_args(b->ctx[g], kModeEval, eps[dd]);
+        }
+    BCU(cudaMemcpyAsync(b->tcfg, tc.data(), total * sizeof(TrajArgs), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->acfg, ac.data(), total * sizeof(AcceptArgs), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->rcfg, rc.data(), total * sizeof(ReduceArgs), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    const auto key = std::make_tuple(b->gen, n_steps);
+    if (!b->graph || key != b->graph_key || max_grid != b->max_start_grid || max_nd != b->max_nd) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        BCU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_traj_start_batch(b->tcfg, total, max_grid, b->d, b->cap_stream);
+        int st = e == cudaSuccess ? MDS_OK : bfail(b, MDS_ERR_CUDA, "batched start: %s", cudaGetErrorString(e));
+        for (int k = 0; k < n_steps && st == MDS_OK; ++k)
+            st = batch_enqueue_pass(b, k + 1 < n_steps ? kModeKickDrift : kModeHalfKick, b->cap_stream);
+        if (st == MDS_OK) {
+            e = launch_traj_end_batch(b->acfg, total, max_nd, b->d, b->cap_stream);
+            if (e != cudaSuccess) st = bfail(b, MDS_ERR_CUDA, "batched end: %s", cudaGetErrorString(e));
+        }
+        e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (st != MDS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        b->graph_key = key;
+        b->max_start_grid = max_grid;
+        b->max_nd = max_nd;
+    }
+    for (int t = 0; t < n_iter; ++t) BCU(cudaGraphLaunch(b->graph, b->stream));
+    int st = batch_check_errors(b, "batch hmc");
+    if (accepted || dh) {
+        std::vector<int32_t> a(static_cast<size_t>(total) * n_iter);
+        std::vector<double> h(static_cast<size_t>(total) * n_iter);
+        BCU(cudaMemcpyAsync(a.data(), b->acc_out, a.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+        BCU(cudaMemcpyAsync(h.data(), b->dh_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        BCU(cudaStreamSynchronize(b->stream));
+        for (int t = 0; t < n_iter; ++t)
+            for (int g = 0; g < total; ++g) {
+                if (accepted) accepted[static_cast<size_t>(t) * total + g] = a[static_cast<size_t>(g) * n_iter + t];
+                if (dh) dh[static_cast<size_t>(t) * total + g] = h[static_cast<size_t>(g) * n_iter + t];
+            }
+    }
+    return st;
+}
+
+int mds_batch_set_strip(mds_batch *b, int32_t strip) {
+    if (!b) return MDS_ERR_INVALID_ARG;
+    if (strip < 0 || strip > 8) return bfail(b, MDS_ERR_INVALID_ARG, "batch strip must be in [0, 8]");
+    b->strip_req = strip;
+    return MDS_OK;
+}
+
+int mds_batch_get_strip(const mds_batch *b, int32_t *strip) {
+    if (!b || !strip) return MDS_ERR_INVALID_ARG;
+    *strip = b->strip;
+    return MDS_OK;
+}
+
+int mds_batch_time_pass(mds_batch *b, int reps, double *ms_per_pass) {
+    if (!b || reps < 1 || !ms_per_pass) return MDS_ERR_INVALID_ARG;
+    BCU(cudaSetDevice(b->device));
+    CHECK(batch_autotune(b));
+    CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
+    BCU(cudaEventRecord(b->ev0, b->stream));
+    for (int r = 0; r < reps; ++r) CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
+    BCU(cudaEventRecord(b->ev1, b->stream));
+    BCU(cudaEventSynchronize(b->ev1));
+    float ms = 0.f;
+    BCU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    *ms_per_pass = ms / reps;
+    for (mds_ctx *c : b->ctx) c->grad_valid = true;
+    return batch_check_errors(b, "batch time_pass");
+}
+
+const char *mds_batch_last_error(const mds_batch *b) {
+    if (!b) return g_create_error.c_str();
+    return b->last_error.c_str();
 }
 
 }  // extern "C"

@@ -122,6 +122,51 @@ enum ErrBits : unsigned {
     kErrBadInput = 8u,    // an input value was negative / NaN / Inf
 };
 
+// ---------------------------------------------------------------------------
+// Batched pair pass (batch_kernel.cu): several datasets (each its own Y, N,
+// sigma), each with several HMC chains, in one persistent launch.  A CTA
+// takes a strip of one dataset, loads its Y tiles into shared memory once and
+// runs the whole strip for every chain of that dataset in turn.
+// ---------------------------------------------------------------------------
+struct BatchDataset {
+    const float *y;            // tile-packed Y
+    int64_t n;
+    int32_t nt;
+    int32_t chain0, n_chains;  // its chains in the chain table
+    int32_t pad;
+    // FP32C constants (sigma folded in), as in PairArgs
+    float2 mp[4];
+    float2 md[4];
+    float2 c_phi;
+    float2 neg_inv_s2;
+    float2 m_coef;
+};
+
+struct BatchChain {
+    const float4 *xrow;
+    const float4 *xcol;
+    float *row_part;           // [slots][64][D]
+    float *col_part;           // [tiles][64][D]
+    float *scal_part;          // [strips of its dataset][kScalarParts]
+};
+
+struct BatchStrip {
+    int32_t dataset, I, j0, j1, row_slot, local;  // local: position in the dataset's strip list
+};
+
+struct BatchPairArgs {
+    const BatchDataset *ds;
+    const BatchChain *ch;
+    const BatchStrip *strips;
+    int32_t n_strips;
+    int32_t strip_cap;         // tiles per strip at most (sizes the shared memory)
+    unsigned *err;
+};
+
+cudaError_t launch_pair_batch(const BatchPairArgs &a, int d, int grid, cudaStream_t s);
+size_t pair_batch_smem(int d, int strip_cap);
+int pair_batch_blocks_per_sm(int d, int strip_cap);
+
 // Kernel launchers (pair_kernel.cu).
 cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s);
 cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s);
@@ -247,6 +292,13 @@ struct AcceptArgs {
     unsigned *err;
 };
 cudaError_t launch_traj_end(const AcceptArgs &a, cudaStream_t s);
+
+// Batched launches (one per step for all problems): per-problem argument
+// tables in device memory.  jobs[k] = (problem, column block J or -1).
+cudaError_t launch_reduce_batch(const ReduceArgs *cfg, const int2 *jobs, int n_jobs, int d, int mode, cudaStream_t s);
+int traj_start_grid(int64_t n, int d);
+cudaError_t launch_traj_start_batch(const TrajArgs *cfg, int n_chains, int max_grid, int d, cudaStream_t s);
+cudaError_t launch_traj_end_batch(const AcceptArgs *cfg, int n_chains, int64_t max_nd, int d, cudaStream_t s);
 
 // Y ingest: rows [r0, r1) of the caller's Y (full or packed layout; the
 // pointer addresses row r0) into the tile-packed FP32 layout.  Entries read

@@ -140,8 +140,10 @@ struct GradT<double> {
 
 // --------------------------------------------------------------- reduce
 
+// One CTA of the reduction: column block J of one problem, or its scalar
+// sums when J < 0.  `a` may live in global memory (batched launches).
 template <typename T, int D>
-__global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_constant__ ReduceArgs a) {
+__device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J) {
     constexpr bool kF32 = std::is_same<T, float>::value;
     using Acc = typename std::conditional<kF32, DF, double>::type;
     using G = typename GradT<T>::type;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_consta
     const int tid = threadIdx.x;
     const int nt = a.nt;
 
-    if (blockIdx.x == static_cast<unsigned>(nt)) {
+    if (J < 0) {
         // scalar partials of all strips -> L, sum r, dL/dsigma (fixed order)
         const T *sp = reinterpret_cast<const T *>(a.scal_part);
         Acc e2{}, md{}, lp{};
@@ -202,7 +204,6 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_consta
         return;
     }
 
-    const int J = blockIdx.x;
     const int r = tid & (kTile - 1);
     const int s = tid / kTile;
     const int64_t k = static_cast<int64_t>(J) * kTile + r;
@@ -283,10 +284,10 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_consta
                 gv = g;
             }
             bad |= !isfinite(gv);
-            if (a.mode != kModeEval) {
+            if (mode != kModeEval) {
                 const T xv = x[k * D + d];
                 const T tg = gv - static_cast<T>(a.lambda) * xv;  // gradient of log pi
-                if (a.mode == kModeKickDrift) {
+                if (mode == kModeKickDrift) {
                     const T pn = p[k * D + d] + static_cast<T>(a.eps) * tg;
                     const T xn = xv + static_cast<T>(a.eps) * pn;
                     p[k * D + d] = pn;
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_consta
         }
         if (bad) atomicOr(a.err, kErrNonfinite);
     }
-    if (a.mode == kModeHalfKick) {
+    if (mode == kModeHalfKick) {
         __syncthreads();
         if constexpr (kF32) {
             const DF tk = block_sum_df<kRedThreads>(ke, sm);
@@ -326,12 +327,24 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_consta
         }
     }
     if constexpr (kF32) {
-        if (a.mode == kModeKickDrift) {
+        if (mode == kModeKickDrift) {
             __syncthreads();
             const float m = block_max<kRedThreads>(xmax, reinterpret_cast<float *>(sm));
             if (tid == 0 && m > 0.f) atomicMax(a.xs.xmax_bits, __float_as_uint(m));
         }
     }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_constant__ ReduceArgs a) {
+    reduce_body<T, D>(a, a.mode, blockIdx.x == static_cast<unsigned>(a.nt) ? -1 : static_cast<int>(blockIdx.x));
+}
+
+// Batched: job (problem index, column block or -1) per CTA.
+template <int D>
+__global__ void __launch_bounds__(kRedThreads) reduce_batch_kernel(const ReduceArgs *cfg, const int2 *jobs, int mode) {
+    const int2 job = jobs[blockIdx.x];
+    reduce_body<float, D>(cfg[job.x], mode, job.y);
 }
 
 // ------------------------------------------------------------ Philox / RNG
@@ -394,13 +407,13 @@ __device__ __forceinline__ void box_muller(uint32_t b1, uint32_t b2, float &z0, 
 constexpr int kTrajThreads = 128;
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kTrajThreads) traj_start_kernel(const __grid_constant__ TrajArgs a) {
+__device__ __forceinline__ void traj_start_body(const TrajArgs &a, int bx) {
     constexpr bool kF32 = std::is_same<T, float>::value;
     using Acc = typename std::conditional<kF32, DF, double>::type;
     using G = typename GradT<T>::type;
     __shared__ Acc sm[kTrajThreads / 32];
     const int64_t nd = a.n * D;
-    const int64_t q = static_cast<int64_t>(blockIdx.x) * kTrajThreads + threadIdx.x;  // 4 elements each
+    const int64_t q = static_cast<int64_t>(bx) * kTrajThreads + threadIdx.x;  // 4 elements each
     T *x = reinterpret_cast<T *>(a.xs.x);
     T *p = reinterpret_cast<T *>(a.p);
     T *x0 = reinterpret_cast<T *>(a.x0);
@@ -460,9 +473,9 @@ __global__ void __launch_bounds__(kTrajThreads) traj_start_kernel(const __grid_c
         tx = block_sum_d<kTrajThreads>(xx, sm);
     }
     if (threadIdx.x == 0) {
-        a.energy_part[2 * blockIdx.x] = tk;
-        a.energy_part[2 * blockIdx.x + 1] = tx;
-        if (blockIdx.x == 0) {
+        a.energy_part[2 * bx] = tk;
+        a.energy_part[2 * bx + 1] = tx;
+        if (bx == 0) {
             a.scal[kLogLik0] = a.scal[kLogLik];
             a.scal[kSumR0] = a.scal[kSumR];
             a.scal[kDSigma0] = a.scal[kDSigma];
@@ -472,10 +485,24 @@ __global__ void __launch_bounds__(kTrajThreads) traj_start_kernel(const __grid_c
     }
 }
 
+template <typename T, int D>
+__global__ void __launch_bounds__(kTrajThreads) traj_start_kernel(const __grid_constant__ TrajArgs a) {
+    traj_start_body<T, D>(a, blockIdx.x);
+}
+
+// Batched: chain blockIdx.y; CTAs past that chain's own grid leave at once.
+template <int D>
+__global__ void __launch_bounds__(kTrajThreads) traj_start_batch_kernel(const TrajArgs *cfg) {
+    const TrajArgs &a = cfg[blockIdx.y];
+    const int64_t quads = (a.n * D + 3) / 4;
+    if (static_cast<int64_t>(blockIdx.x) * kTrajThreads >= quads) return;
+    traj_start_body<float, D>(a, blockIdx.x);
+}
+
 // ------------------------------------------------------------- traj end
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kTrajThreads) traj_end_kernel(const __grid_constant__ AcceptArgs a) {
+__device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int nbx) {
     using G = typename GradT<T>::type;
     // every CTA sums the same partials in the same order -> same decision
     __shared__ int keep_s;
@@ -526,13 +553,13 @@ __global__ void __launch_bounds__(kTrajThreads) traj_end_kernel(const __grid_con
         const T *x0 = reinterpret_cast<const T *>(a.x0);
         G *grad = reinterpret_cast<G *>(a.grad);
         const G *grad0 = reinterpret_cast<const G *>(a.grad0);
-        for (int64_t e = static_cast<int64_t>(blockIdx.x) * kTrajThreads + threadIdx.x; e < nd;
-             e += static_cast<int64_t>(gridDim.x) * kTrajThreads) {
+        for (int64_t e = static_cast<int64_t>(bx) * kTrajThreads + threadIdx.x; e < nd;
+             e += static_cast<int64_t>(nbx) * kTrajThreads) {
             store_x<T>(a.xs, e / D, D, static_cast<int>(e % D), x0[e]);
             grad[e] = grad0[e];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bx == 0 && threadIdx.x == 0) {
         const double dh = dh_s;
         if (!isfinite(dh)) atomicOr(a.err, kErrNonfinite);
         a.scal[kLastDH] = dh;
@@ -550,6 +577,16 @@ __global__ void __launch_bounds__(kTrajThreads) traj_end_kernel(const __grid_con
             a.counters[kAccepted] += keep;
         }
     }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kTrajThreads) traj_end_kernel(const __grid_constant__ AcceptArgs a) {
+    traj_end_body<T, D>(a, blockIdx.x, gridDim.x);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTrajThreads) traj_end_batch_kernel(const AcceptArgs *cfg) {
+    traj_end_body<float, D>(cfg[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
 #define MDS_SWITCH_D(KERNEL, T, GRID, BLOCK, STREAM, ARGS)                        \
@@ -717,6 +754,39 @@ cudaError_t launch_traj_end(const AcceptArgs &a, cudaStream_t s) {
     } else {
         MDS_SWITCH_D(traj_end_kernel, float, grid, kTrajThreads, s, a)
     }
+    return cudaGetLastError();
+}
+
+#define MDS_SWITCH_DB(KERNEL, GRID, BLOCK, STREAM, D, ...)                       \
+    switch (D) {                                                                 \
+        case 1: KERNEL<1><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        case 2: KERNEL<2><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        case 3: KERNEL<3><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        case 4: KERNEL<4><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        case 5: KERNEL<5><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        case 6: KERNEL<6><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        case 7: KERNEL<7><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        case 8: KERNEL<8><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;       \
+        default: return cudaErrorInvalidValue;                                   \
+    }
+
+cudaError_t launch_reduce_batch(const ReduceArgs *cfg, const int2 *jobs, int n_jobs, int d, int mode, cudaStream_t s) {
+    if (n_jobs <= 0) return cudaSuccess;
+    MDS_SWITCH_DB(reduce_batch_kernel, n_jobs, kRedThreads, s, d, cfg, jobs, mode)
+    return cudaGetLastError();
+}
+
+int traj_start_grid(int64_t n, int d) { return static_cast<int>(((n * d + 3) / 4 + kTrajThreads - 1) / kTrajThreads); }
+
+cudaError_t launch_traj_start_batch(const TrajArgs *cfg, int n_chains, int max_grid, int d, cudaStream_t s) {
+    const dim3 grid(max_grid, n_chains);
+    MDS_SWITCH_DB(traj_start_batch_kernel, grid, kTrajThreads, s, d, cfg)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_traj_end_batch(const AcceptArgs *cfg, int n_chains, int64_t max_nd, int d, cudaStream_t s) {
+    const dim3 grid(grid_for(max_nd, kTrajThreads), n_chains);
+    MDS_SWITCH_DB(traj_end_batch_kernel, grid, kTrajThreads, s, d, cfg)
     return cudaGetLastError();
 }
 

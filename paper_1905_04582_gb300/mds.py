@@ -213,6 +213,106 @@ class MDS:
                                       "last_dh": stats.last_dh, "last_loglik": stats.last_loglik}
 
 
+class Batch:
+    """Several datasets (uneven N, same D), each with several HMC chains,
+    advanced together: one batched pair pass per leapfrog step for all chains."""
+
+    def __init__(self, ns, d, chains, stream=None, strip=None):
+        self._lib = capi.lib()
+        ns = np.ascontiguousarray(ns, dtype=np.int64)
+        ch = np.ascontiguousarray(chains, dtype=np.int32)
+        h = ctypes.c_void_p()
+        st = self._lib.mds_batch_create(len(ns), ns.ctypes.data_as(ctypes.c_void_p), int(d),
+                                        ch.ctypes.data_as(ctypes.c_void_p), capi.MDS_PREC_FP32C, ctypes.byref(h))
+        if st != capi.MDS_OK:
+            raise capi.MDSError(st, self._lib.mds_batch_last_error(None).decode(errors="replace"))
+        self._h = h
+        self.ns = [int(v) for v in ns]
+        self.d = int(d)
+        self.chains = [int(v) for v in ch]
+        self.total = int(ch.sum())
+        if stream is not None:
+            ptr = stream.cuda_stream if (torch is not None and isinstance(stream, torch.cuda.Stream)) else int(stream)
+            self._check(self._lib.mds_batch_set_stream(self._h, ctypes.c_void_p(ptr)))
+        if strip is not None:
+            self._check(self._lib.mds_batch_set_strip(self._h, int(strip)))
+
+    def _check(self, st):
+        if st != capi.MDS_OK:
+            raise capi.MDSError(st, self._lib.mds_batch_last_error(self._h).decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mds_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_data(self, dataset, y, layout="packed", ld=None):
+        p, dt, where, keep = _buf(y)
+        lay = {"packed": capi.MDS_Y_PACKED_UPPER, "full": capi.MDS_Y_FULL}[layout]
+        self._check(self._lib.mds_batch_set_data(self._h, int(dataset), p, dt, lay,
+                                                 int(ld if ld is not None else self.ns[dataset]), where))
+
+    def set_sigma(self, dataset, sigma):
+        self._check(self._lib.mds_batch_set_sigma(self._h, int(dataset), float(sigma)))
+
+    def set_locations(self, dataset, chain, x):
+        p, dt, where, keep = _buf(x)
+        self._check(self._lib.mds_batch_set_locations(self._h, int(dataset), int(chain), p, dt, where))
+
+    def get_locations(self, dataset, chain, dtype=np.float64):
+        out = np.empty((self.ns[dataset], self.d), dtype=dtype)
+        p, dt, where, keep = _buf(out, writable=True)
+        self._check(self._lib.mds_batch_get_locations(self._h, int(dataset), int(chain), p, dt, where))
+        return out
+
+    def get_gradient(self, dataset, chain, dtype=np.float64):
+        out = np.empty((self.ns[dataset], self.d), dtype=dtype)
+        p, dt, where, keep = _buf(out, writable=True)
+        self._check(self._lib.mds_batch_get_gradient(self._h, int(dataset), int(chain), p, dt, where))
+        return out
+
+    def evaluate(self):
+        """(L[g], dL/dsigma[g]) for every global chain g (dataset-major)."""
+        ll = np.zeros(self.total)
+        ds = np.zeros(self.total)
+        self._check(self._lib.mds_batch_evaluate(self._h, ll.ctypes.data_as(ctypes.c_void_p),
+                                                 ds.ctypes.data_as(ctypes.c_void_p)))
+        return ll, ds
+
+    def hmc(self, n_iter, n_steps, eps, seed=0):
+        """n_iter HMC iterations for all chains; eps per dataset.  Returns
+        (accepted[n_iter, total], dH[n_iter, total])."""
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        acc = np.zeros((n_iter, self.total), dtype=np.int32)
+        dh = np.zeros((n_iter, self.total))
+        self._check(self._lib.mds_batch_hmc(self._h, int(n_iter), int(n_steps), e.ctypes.data_as(ctypes.c_void_p),
+                                            int(seed) & (2**64 - 1), acc.ctypes.data_as(ctypes.c_void_p),
+                                            dh.ctypes.data_as(ctypes.c_void_p)))
+        return acc.astype(bool), dh
+
+    def get_strip(self):
+        s = ctypes.c_int32()
+        self._check(self._lib.mds_batch_get_strip(self._h, ctypes.byref(s)))
+        return s.value
+
+    def time_pass(self, reps=10):
+        ms = ctypes.c_double()
+        self._check(self._lib.mds_batch_time_pass(self._h, int(reps), ctypes.byref(ms)))
+        return ms.value
+
+
 if torch is not None:
 
     class MDSLogLik(torch.autograd.Function):
