@@ -37,6 +37,52 @@ METRIC = "pairs/sec and HMC leapfrog steps/sec (loglik+grad) at N=5392, % HBM ro
 WORKLOAD = "paper-scale N=5392 D=2, 6-component Gaussian mixture, sigma=0.3, FP32 Y (synthetic)"
 
 
+SM_MAX_MHZ = 2070.0
+
+
+def fp32_ops_per_pair(d):
+    """FP32 lane operations per pair in pair2_f32 (pair_math.cuh), an FMA
+    counting once: per coordinate the exact-split differences (3), squares
+    (1), cross term (2) and the two gradient accumulations (2); fixed: d^2,
+    residual (2), half inverse, corrected e (2), exp argument, Mills ratio
+    P and D (3 + 3), D Phi, 1/Phi, phi/Phi, log-product, e^2, m delta, w (2),
+    w/delta."""
+    return 8 * d + 22
+
+
+PAIR_KERNEL_SOURCES = ("pair_kernel.cu", "pair_math.cuh", "mds_internal.h", "mills_ratio_coeffs.h")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_f32_kernel_N5392_D2_traffic.txt")
+
+
+def pair_kernel_sha256():
+    """Hash of the sources the FP32C pair kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in PAIR_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1905_04582_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(n, d):
+    """DRAM bytes per launch of the pair pass from the committed ncu capture
+    (`key: value` lines), if it was taken on the current kernel source at
+    this N and D; else None."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for ln in f:
+                if ":" in ln and not ln.startswith("#"):
+                    k, v = ln.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sha256") == pair_kernel_sha256() and int(kv.get("n", -1)) == n \
+                and int(kv.get("d", -1)) == d:
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -108,13 +154,21 @@ def dist_env():
 
 
 def reduce_max(value, world):
+    """Max of a per-rank number over the ranks (NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(units_per_rank, seconds, world):
+    """Whole-job throughput of `world` independent replicas: all ranks' units
+    over the slowest rank's time (max over ranks)."""
+    return world * units_per_rank / reduce_max(seconds, world)
 
 
 def barrier(world):
@@ -203,10 +257,11 @@ def run_gpu(args):
     model.log_likelihood()
     model.hmc(max(args.warmup, 1), N_LEAPFROG, eps, seed=seed)
 
-    # timed region: K HMC iterations, L2 flushed before each (untimed)
+    # timed region: K HMC iterations queued back to back on the stream (no
+    # host round trip between them), each bracketed by its own CUDA events,
+    # L2 flushed before each one outside the brackets
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    acc_total = 0
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
@@ -214,11 +269,12 @@ def run_gpu(args):
         for k in range(args.steps):
             flush_l2()
             ev_s[k].record(stream)
-            acc, dh, stats = model.hmc(1, N_LEAPFROG, eps, seed=seed)
+            model.hmc_enqueue(1, N_LEAPFROG, eps, seed=seed)
             ev_e[k].record(stream)
-            acc_total += int(acc.sum())
+        acc, dh, stats = model.hmc_collect()
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+    acc_total = int(acc.sum())
     barrier(world)
     step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
     dev_ms = sum(step_ms)
@@ -236,25 +292,26 @@ def run_gpu(args):
     model.set_profiling(False)
 
     pairs_per_step = N_LEAPFROG * wl.m
-    value = world * args.steps * pairs_per_step / (dev_ms_max / 1e3)
+    value = replica_rate(args.steps * pairs_per_step, dev_ms / 1e3, world)
     lf_steps = world * args.steps * N_LEAPFROG / (dev_ms_max / 1e3)
 
-    # roofline of the dominant kernel (the fused pair pass), timed live
-    peak, peak_kind = load_peaks()
+    # roofline of the dominant kernel (the fused pair pass), timed live.  It
+    # is bound by the FP32 pipe: FP32_OPS_PER_PAIR lane operations per pair
+    # (counted from the kernel source; an FMA counts once) against
+    # SMs x 128 FP32 lanes x the SM clock.  The HBM view (4 B of Y per pair
+    # against the measured copy bandwidth) is reported beside it.
+    hbm_peak, peak_kind = load_peaks()
     m_pairs, y_bytes = model.problem_size()
     pass_avg_ms = pass_ms / max(n_pass, 1)
     alg_bytes = 4.0 * m_pairs  # one FP32 y_ij per pair per pass
-    achieved = alg_bytes / (pass_avg_ms / 1e3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "pair_pass_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            with open(tr_path) as f:
-                tr = json.load(f)
-            if tr.get("kernel_rev") == "v1" and tr.get("n") == wl.n:
-                traffic = tr.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    achieved_gbs = alg_bytes / (pass_avg_ms / 1e3) / 1e9
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = clocks.summary()
+    sm_mhz = (clk or {}).get("sm_max_mhz") or SM_MAX_MHZ
+    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12  # TFP32-op/s
+    ops = fp32_ops_per_pair(wl.d)
+    alu_achieved = m_pairs * ops / (pass_avg_ms / 1e3) / 1e12
+    traffic = kernel_traffic(wl.n, wl.d)
 
     # the plain FP64 GPU path on the same data (one pass, timed alone)
     with MDS(wl.n, wl.d, "fp64", stream=stream) as m64:
@@ -276,8 +333,7 @@ def run_gpu(args):
         model.hmc(1, N_LEAPFROG, eps, seed=seed)
         model.get_locations(out=x_out)
     torch.cuda.synchronize()
-    e2e_s = reduce_max(time.perf_counter() - t0, world)
-    e2e_value = world * e2e_steps * pairs_per_step / e2e_s
+    e2e_value = replica_rate(e2e_steps * pairs_per_step, time.perf_counter() - t0, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -300,13 +356,17 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "leapfrog_steps_per_s": lf_steps,
             "accept_rate": acc_total / args.steps,
-            "hbm_fraction_of_pairs_rate": value * 4.0 / 1e9 / peak,
+            "hbm_fraction_of_pairs_rate": value * 4.0 / 1e9 / hbm_peak,
             "pass_alone": {"fp32c_ms": ms32, "fp64_ms": ms64, "fp32c_pairs_per_s": m_pairs / (ms32 / 1e3),
                            "fp64_pairs_per_s": m_pairs / (ms64 / 1e3), "speedup_vs_fp64": ms64 / ms32},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs",
-                         "kernel": "pair_f32_kernel<2>", "launches_timed": n_pass,
-                         "avg_launch_ms": pass_avg_ms, "algorithmic_bytes_per_launch": alg_bytes},
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFP32-op/s",
+                         "frac": alu_achieved / alu_peak, "traffic": traffic,
+                         "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
+                         "ops_per_pair": ops, "kernel": f"pair_f32_kernel<{wl.d}>", "launches_timed": n_pass,
+                         "avg_launch_ms": pass_avg_ms, "pairs_per_launch": m_pairs,
+                         "hbm_view": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                      "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                                      "algorithmic_bytes_per_launch": alg_bytes}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": wl.n * wl.d * 4,
                     "d2h_bytes_per_step": wl.n * wl.d * 4 + 8 + 8 + 4,
@@ -364,7 +424,11 @@ def main():
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--strip", type=int, default=None)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--kernel-hash", action="store_true", help="print the pair kernel's source hash and exit")
     args = ap.parse_args()
+    if args.kernel_hash:
+        print(pair_kernel_sha256())
+        return 0
     if args.pass_only:
         return run_pass_only(args)
     if args.warmup < 3:

@@ -172,6 +172,26 @@ typedef struct mds_hmc_stats {
 int mds_hmc(mds_ctx *ctx, int n_iter, int n_steps, double eps, uint64_t seed, const double *p_all,
             const double *u_all, int *accepted, double *dh, mds_hmc_stats *stats);
 
+/* Asynchronous HMC (Algorithm 1 of arXiv:1905.04582, as mds_hmc, Philox
+ * momenta only): queue n_iter iterations on the context's stream and return
+ * without waiting for the device.  The chain state stays on the device; the
+ * per-iteration decisions and H1 - H0 accumulate there (moved to the host
+ * automatically when the queue outgrows its buffer, which then waits once).
+ * Any number of enqueue calls may precede one mds_hmc_collect.  mds_hmc
+ * refuses to run (STATE) while queued results are uncollected.  Errors found
+ * by the device during queued iterations are reported by the collect. */
+int mds_hmc_enqueue(mds_ctx *ctx, int n_iter, int n_steps, double eps, uint64_t seed);
+
+/* Wait for the queued iterations and return their results in queue order:
+ * accepted (optional, int32, host) and dh (optional, FP64, host) receive up
+ * to `cap` entries (the rest are dropped), *count (optional) the number of
+ * iterations collected, stats (optional) their totals and the state after
+ * the last one.  One device-to-host read-back.  Errors: NONFINITE (an energy
+ * was not finite; that proposal was rejected), INVALID_ARG (the locations
+ * left the FP32C range), TIMEOUT, CUDA. */
+int mds_hmc_collect(mds_ctx *ctx, int64_t cap, int32_t *accepted, double *dh, int64_t *count,
+                    mds_hmc_stats *stats);
+
 /* Number of pairs M = N(N-1)/2 and the bytes of tile-packed Y resident on
  * the device. */
 int mds_problem_size(const mds_ctx *ctx, int64_t *pairs, int64_t *y_bytes);

@@ -71,6 +71,8 @@ SIGNATURES = {
     "mds_get_momentum": (_int, [_vp, _vp, _int, _int]),
     "mds_leapfrog": (_int, [_vp, _int, _dbl, _vp, _int, _int, _pdbl]),
     "mds_hmc": (_int, [_vp, _int, _int, _dbl, _u64, _vp, _vp, _vp, _vp, ctypes.POINTER(mds_hmc_stats)]),
+    "mds_hmc_enqueue": (_int, [_vp, _int, _int, _dbl, _u64]),
+    "mds_hmc_collect": (_int, [_vp, _i64, _vp, _vp, _pi64, ctypes.POINTER(mds_hmc_stats)]),
     "mds_problem_size": (_int, [_vp, _pi64, _pi64]),
     "mds_set_strip": (_int, [_vp, _i32]),
     "mds_get_strip": (_int, [_vp, _pi32]),

@@ -62,7 +62,6 @@ struct mds_ctx {
     float4 *xrow = nullptr, *xcol = nullptr;          // FP32C split layouts
     Split *split = nullptr;                           // FP32C split quantum (device)
     unsigned *xmax_bits = nullptr;                    // FP32C running max |x|
-    float split_bound = 0.f;                          // largest |x| the current quantum serves exactly
     void *grad = nullptr, *grad0 = nullptr;           // float2 (hi, lo) on FP32C, double on FP64
     void *col_part = nullptr;
     void *row_part = nullptr;
@@ -85,6 +84,11 @@ struct mds_ctx {
     int32_t *acc_out = nullptr;
     double *dh_out = nullptr;
     size_t out_cap = 0;
+    int64_t hmc_pending = 0;          // iterations queued since the last collect (results on the device)
+    std::vector<int32_t> acc_spill;   // results moved to the host to make room (oldest first)
+    std::vector<double> dh_spill;
+    void *host_stage = nullptr;       // pinned host memory for the one read-back of a collect
+    size_t host_stage_bytes = 0;
 
     // pair-pass timing (mds_set_profiling)
     bool profiling = false;
@@ -175,6 +179,16 @@ int check_ctx(mds_ctx *c) {
     return MDS_OK;
 }
 
+// Map device error bits to a status and message.
+int err_status(mds_ctx *c, unsigned h, const char *what) {
+    if (h & kErrTimeout) return fail(c, MDS_ERR_TIMEOUT, "%s: a device-side wait timed out", what);
+    if (h & kErrBadArgs) return fail(c, MDS_ERR_CUDA, "%s: kernel argument check failed", what);
+    if (h & kErrNonfinite) return fail(c, MDS_ERR_NONFINITE, "%s: non-finite result (NaN/Inf)", what);
+    if (h & kErrRange) return fail(c, MDS_ERR_INVALID_ARG, "%s: locations moved beyond the FP32C range", what);
+    if (h & kErrOverflow) return fail(c, MDS_ERR_STATE, "%s: HMC result buffer overflow", what);
+    return fail(c, MDS_ERR_INVALID_ARG, "%s: invalid input value", what);
+}
+
 // Read and clear the device error word; map it to a status.
 int check_device_err(mds_ctx *c, const char *what) {
     unsigned h = 0;
@@ -183,10 +197,7 @@ int check_device_err(mds_ctx *c, const char *what) {
     if (h == 0) return MDS_OK;
     CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    if (h & kErrTimeout) return fail(c, MDS_ERR_TIMEOUT, "%s: a device-side wait timed out", what);
-    if (h & kErrBadArgs) return fail(c, MDS_ERR_CUDA, "%s: kernel argument check failed", what);
-    if (h & kErrNonfinite) return fail(c, MDS_ERR_NONFINITE, "%s: non-finite result (NaN/Inf)", what);
-    return fail(c, MDS_ERR_INVALID_ARG, "%s: invalid input value", what);
+    return err_status(c, h, what);
 }
 
 // ---------------------------------------------------------------- strips
@@ -247,27 +258,20 @@ int build_strips(mds_ctx *c, int strip) {
 
 constexpr int kMaxStrip = 64;  // bounds the FP32 row sums of a lane (<= 256 terms)
 
-// Choose the split quantum from max |x| (4x headroom for the moves of a
-// trajectory) and rewrite the split layouts when it changes.  Called at the
-// start of every call that runs passes.
-int refresh_split(mds_ctx *c, bool force) {
+// Choose the split quantum from max |x| of locations the caller sets and
+// rewrite the split layouts.  During trajectories the end-of-trajectory
+// reduction grows the quantum on the device by the same rule (choose_split),
+// so no call that runs passes has to read max |x| back.
+int set_split_from_xmax(mds_ctx *c) {
     if (c->fp64) return MDS_OK;
     unsigned bits = 0;
     CU(cudaMemcpyAsync(&bits, c->xmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     float m;
     std::memcpy(&m, &bits, sizeof(m));
-    if (!force && m <= c->split_bound && m * 64.f >= c->split_bound) return MDS_OK;
-    const int b = split_bits(c->d);
-    const double lim = std::ldexp(1.0, b - 1) - 1.0;  // |xh| / q must stay below 2^(B-1)
-    const double mm = std::max(static_cast<double>(m), 1e-30) * 4.0;
-    const int ex = static_cast<int>(std::ceil(std::log2(mm / lim)));
     Split sp;
-    sp.q = static_cast<float>(std::ldexp(1.0, ex));
-    sp.magic = static_cast<float>(std::ldexp(1.5, ex + 23));
-    if (!std::isfinite(sp.magic) || sp.q < std::ldexp(1.0f, -100))
+    if (!choose_split(m, c->d, sp))
         return fail(c, MDS_ERR_INVALID_ARG, "locations out of the FP32C range (max |x| = %g)", m);
-    c->split_bound = static_cast<float>(lim * std::ldexp(1.0, ex));
     CU(cudaMemcpyAsync(c->split, &sp, sizeof(sp), cudaMemcpyHostToDevice, c->stream));
     cudaError_t e = launch_resplit(xstate(c), c->n_pad, c->d, c->stream);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "resplit: %s", cudaGetErrorString(e));
@@ -462,7 +466,6 @@ int autotune(mds_ctx *c) {
 // Evaluate at the current x (gradient + scalars) and wait.
 int evaluate(mds_ctx *c) {
     CHECK(ready(c));
-    CHECK(refresh_split(c, false));
     CHECK(autotune(c));
     CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
     CU(cudaGetLastError());
@@ -533,7 +536,7 @@ TrajArgs make_traj_args(const mds_ctx *c, int n_steps, double eps, int momentum_
 }
 
 AcceptArgs make_accept_args(const mds_ctx *c, int n_steps, int metropolis, int u_src, uint64_t seed, uint32_t chain,
-                            int start_grid, int32_t *acc_out, double *dh_out) {
+                            int start_grid, int32_t *acc_out, double *dh_out, int64_t out_cap) {
     AcceptArgs a{};
     a.n = c->n;
     a.d = c->d;
@@ -563,6 +566,7 @@ AcceptArgs make_accept_args(const mds_ctx *c, int n_steps, int metropolis, int u
     // iteration within the current HMC call, below the output capacity)
     a.acc_out = metropolis ? acc_out : nullptr;
     a.dh_out = metropolis ? dh_out : nullptr;
+    a.out_cap = out_cap;
     a.err = c->err;
     return a;
 }
@@ -578,7 +582,8 @@ int enqueue_trajectory(mds_ctx *c, int n_steps, double eps, int momentum_src, in
     c->start_grid = grid;
     for (int k = 0; k < n_steps; ++k)
         CHECK(enqueue_pass(c, k + 1 < n_steps ? kModeKickDrift : kModeHalfKick, eps, s));
-    AcceptArgs a = make_accept_args(c, n_steps, metropolis, u_src, seed, 0, grid, c->acc_out, c->dh_out);
+    AcceptArgs a = make_accept_args(c, n_steps, metropolis, u_src, seed, 0, grid, c->acc_out, c->dh_out,
+                                    static_cast<int64_t>(c->out_cap));
     e = launch_traj_end(a, s);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "trajectory end: %s", cudaGetErrorString(e));
     return MDS_OK;
@@ -595,6 +600,135 @@ int ensure_out_cap(mds_ctx *c, size_t n_iter) {
     c->out_cap = n_iter;
     c->gen++;
     return MDS_OK;
+}
+
+// Pinned host memory for read-backs (grown on demand, kept).
+int ensure_host_stage(mds_ctx *c, size_t bytes) {
+    if (bytes <= c->host_stage_bytes) return MDS_OK;
+    if (c->host_stage) {
+        CU(cudaStreamSynchronize(c->stream));
+        cudaFreeHost(c->host_stage);
+        c->host_stage = nullptr;
+        c->host_stage_bytes = 0;
+    }
+    const size_t nb = std::max<size_t>(bytes, 4096);
+    CU(cudaMallocHost(&c->host_stage, nb));
+    c->host_stage_bytes = nb;
+    return MDS_OK;
+}
+
+// Move the results of the queued iterations to the host (waits) and restart
+// the device-side iteration index, making room in the result buffers.
+int hmc_spill(mds_ctx *c) {
+    const int64_t k = c->hmc_pending;
+    if (k <= 0) return MDS_OK;
+    CHECK(ensure_host_stage(c, static_cast<size_t>(k) * (sizeof(int32_t) + sizeof(double))));
+    double *hd = static_cast<double *>(c->host_stage);
+    int32_t *ha = reinterpret_cast<int32_t *>(hd + k);
+    CU(cudaMemcpyAsync(hd, c->dh_out, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(ha, c->acc_out, k * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemsetAsync(c->counters + kIterLocal, 0, sizeof(int64_t), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->acc_spill.insert(c->acc_spill.end(), ha, ha + k);
+    c->dh_spill.insert(c->dh_spill.end(), hd, hd + k);
+    c->hmc_pending = 0;
+    return MDS_OK;
+}
+
+// Queue n_iter HMC iterations (one CUDA graph launch each) without waiting.
+// inj: momenta / uniforms from p_inj / u_inj (indexed by the iteration
+// within the queue, which must then start empty).
+int hmc_enqueue(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, int inj) {
+    if (inj && c->hmc_pending != 0) return fail(c, MDS_ERR_STATE, "injected momenta need an empty queue");
+    if (c->hmc_pending + n_iter > static_cast<int64_t>(c->out_cap)) {
+        CHECK(hmc_spill(c));
+        CHECK(ensure_out_cap(c, static_cast<size_t>(n_iter)));
+    }
+    // one HMC iteration as a CUDA graph, captured once per configuration
+    const auto key = std::make_tuple(c->gen, n_steps, eps, inj ? 2 : 1, c->profiling ? 1 : 0, seed, c->strip);
+    if (!c->graph || key != c->graph_key) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        c->prof_used = 0;
+        int st = enqueue_trajectory(c, n_steps, eps, inj ? 2 : 1, inj ? 2 : 1, 1, seed, c->cap_stream);
+        c->graph_prof = c->prof_used;
+        c->prof_used = 0;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (st != MDS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        c->graph_key = key;
+    }
+    for (int t = 0; t < n_iter; ++t) {
+        CU(cudaGraphLaunch(c->graph, c->stream));
+        c->hmc_pending++;
+        if (c->profiling) {
+            CU(cudaStreamSynchronize(c->stream));
+            c->prof_used = c->graph_prof;
+            CHECK(harvest_prof(c));
+        }
+    }
+    return MDS_OK;
+}
+
+// Wait for the queued iterations and hand back their results (spilled ones
+// first), with one read-back: error word, scalars, counters, per-iteration
+// decisions and H1 - H0.  Entries beyond cap are dropped; *count gets the
+// number of iterations collected.
+int hmc_collect(mds_ctx *c, int64_t cap, int32_t *accepted, double *dh, int64_t *count, mds_hmc_stats *stats,
+                const char *what) {
+    const int64_t k = c->hmc_pending;
+    const size_t bytes = 8 + kScalars * 8 + kCounters * 8 + static_cast<size_t>(k) * (8 + 4);
+    CHECK(ensure_host_stage(c, bytes));
+    double *hs = static_cast<double *>(c->host_stage);  // [scalars][counters][dh][acc][err]
+    int64_t *hc = reinterpret_cast<int64_t *>(hs + kScalars);
+    double *hd = reinterpret_cast<double *>(hc + kCounters);
+    int32_t *ha = reinterpret_cast<int32_t *>(hd + k);
+    unsigned *he = reinterpret_cast<unsigned *>(ha + k + (k & 1));
+    CU(cudaMemcpyAsync(hs, c->scal, kScalars * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hc, c->counters, kCounters * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (k > 0) {
+        CU(cudaMemcpyAsync(hd, c->dh_out, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(ha, c->acc_out, k * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CU(cudaMemcpyAsync(he, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemsetAsync(c->counters + kIterLocal, 0, sizeof(int64_t), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> acc = std::move(c->acc_spill);
+    std::vector<double> dhv = std::move(c->dh_spill);
+    c->acc_spill.clear();
+    c->dh_spill.clear();
+    acc.insert(acc.end(), ha, ha + k);
+    dhv.insert(dhv.end(), hd, hd + k);
+    c->hmc_pending = 0;
+    const int64_t total = static_cast<int64_t>(acc.size());
+    for (int64_t t = 0; t < total && t < cap; ++t) {
+        if (accepted) accepted[t] = acc[t];
+        if (dh) dh[t] = dhv[t];
+    }
+    *count = total;
+    if (stats) {
+        int64_t na = 0;
+        for (int32_t v : acc) na += v;
+        stats->iterations = total;
+        stats->accepted = na;
+        stats->last_dh = hs[kLastDH];
+        stats->last_loglik = hs[kLogLik];
+    }
+    const unsigned h = *he;
+    if (h == 0) return MDS_OK;
+    CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return err_status(c, h, what);
 }
 
 }  // namespace
@@ -690,7 +824,7 @@ int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out
         ok = cudaMemset(c->xrow, 0, nd_pad / 2 * sizeof(float4)) == cudaSuccess &&
              cudaMemset(c->xcol, 0, nd_pad * sizeof(float4)) == cudaSuccess &&
              cudaMemset(c->xmax_bits, 0, sizeof(unsigned)) == cudaSuccess;
-        Split sp{1.0f, 12582912.0f};  // q = 1 until locations are set
+        Split sp{1.0f, 12582912.0f, 0.0f, 0};  // q = 1 until locations are set
         ok = ok && cudaMemcpy(c->split, &sp, sizeof(sp), cudaMemcpyHostToDevice) == cudaSuccess;
     }
     if (!ok) {
@@ -720,6 +854,7 @@ int mds_destroy(mds_ctx *c) {
                     c->bad,      c->e_start,  c->e_end,     c->stage,    c->p_inj,     c->u_inj,
                     c->acc_out,  c->dh_out};
     for (void *b : bufs) dev_free(b);
+    if (c->host_stage) cudaFreeHost(c->host_stage);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -832,8 +967,7 @@ int mds_set_locations(mds_ctx *c, const void *x, int dtype, int where) {
         CU(cudaMemsetAsync(c->xmax_bits, 0, sizeof(unsigned), c->stream));
         cudaError_t e = launch_xmax(dev, dtype == MDS_F64, c->n * c->d, c->xmax_bits, c->stream);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_locations: %s", cudaGetErrorString(e));
-        c->split_bound = 0.f;
-        CHECK(refresh_split(c, true));
+        CHECK(set_split_from_xmax(c));
     }
     cudaError_t e = launch_set_x(dev, dtype == MDS_F64, c->n, c->n_pad, c->d, c->fp64, xstate(c), c->err, c->stream);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_locations: %s", cudaGetErrorString(e));
@@ -936,7 +1070,6 @@ int mds_leapfrog(mds_ctx *c, int n_steps, double eps, const void *p0, int p0_dty
     if (!std::isfinite(eps)) return fail(c, MDS_ERR_INVALID_ARG, "eps must be finite");
     CHECK(ready(c));
     if (p0) CHECK(mds_set_momentum(c, p0, p0_dtype, p0_where));
-    CHECK(refresh_split(c, false));
     if (!c->grad_valid) CHECK(evaluate(c));
     CHECK(autotune(c));
     CHECK(enqueue_trajectory(c, n_steps, eps, 0, 1, 0, 0, c->stream));
@@ -958,14 +1091,17 @@ int mds_hmc(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, cons
     if (!std::isfinite(eps)) return fail(c, MDS_ERR_INVALID_ARG, "eps must be finite");
     if ((p_all == nullptr) != (u_all == nullptr))
         return fail(c, MDS_ERR_INVALID_ARG, "p_all and u_all must be given together");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
     CHECK(ready(c));
-    CHECK(refresh_split(c, false));
     if (!c->grad_valid) CHECK(evaluate(c));
     CHECK(autotune(c));
     if (n_iter == 0) return MDS_OK;
     const int inj = p_all != nullptr;
-    const int64_t nd = c->n * c->d;
     if (inj) {
+        const int64_t nd = c->n * c->d;
+        for (int t = 0; t < n_iter; ++t)
+            if (!(u_all[t] > 0.0 && u_all[t] < 1.0)) return fail(c, MDS_ERR_INVALID_ARG, "u_all[%d] not in (0,1)", t);
         const size_t pb = static_cast<size_t>(n_iter) * nd * sizeof(double);
         if (pb > c->p_inj_bytes) {
             dev_free(c->p_inj);
@@ -982,71 +1118,31 @@ int mds_hmc(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, cons
             c->u_inj_bytes = ub;
             c->gen++;
         }
-        for (int t = 0; t < n_iter; ++t)
-            if (!(u_all[t] > 0.0 && u_all[t] < 1.0)) return fail(c, MDS_ERR_INVALID_ARG, "u_all[%d] not in (0,1)", t);
         CU(cudaMemcpyAsync(c->p_inj, p_all, pb, cudaMemcpyHostToDevice, c->stream));
         CU(cudaMemcpyAsync(c->u_inj, u_all, ub, cudaMemcpyHostToDevice, c->stream));
     }
-    CHECK(ensure_out_cap(c, static_cast<size_t>(n_iter)));
-    CU(cudaMemsetAsync(c->counters + kIterLocal, 0, sizeof(int64_t), c->stream));
-    int64_t acc_before = 0;
-    CU(cudaMemcpyAsync(&acc_before, c->counters + kAccepted, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    CHECK(hmc_enqueue(c, n_iter, n_steps, eps, seed, inj));
+    int64_t count = 0;
+    return hmc_collect(c, n_iter, accepted, dh, &count, stats, "hmc");
+}
 
-    // one HMC iteration as a CUDA graph, captured once per configuration
-    const auto key = std::make_tuple(c->gen, n_steps, eps, inj ? 2 : 1, c->profiling ? 1 : 0, seed, c->strip);
-    if (!c->graph || key != c->graph_key) {
-        if (c->graph) {
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
-        }
-        cudaGraph_t g = nullptr;
-        CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        c->prof_used = 0;
-        int st = enqueue_trajectory(c, n_steps, eps, inj ? 2 : 1, inj ? 2 : 1, 1, seed, c->cap_stream);
-        c->graph_prof = c->prof_used;
-        c->prof_used = 0;
-        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-        if (st != MDS_OK) {
-            if (g) cudaGraphDestroy(g);
-            return st;
-        }
-        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&c->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        c->graph_key = key;
-    }
-    for (int t = 0; t < n_iter; ++t) {
-        CU(cudaGraphLaunch(c->graph, c->stream));
-        if (c->profiling) {
-            CU(cudaStreamSynchronize(c->stream));
-            c->prof_used = c->graph_prof;
-            CHECK(harvest_prof(c));
-        }
-    }
-    int st = check_device_err(c, "hmc");
-    if (accepted) {
-        std::vector<int32_t> a(n_iter);
-        CU(cudaMemcpyAsync(a.data(), c->acc_out, n_iter * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        for (int t = 0; t < n_iter; ++t) accepted[t] = a[t];
-    }
-    if (dh) {
-        CU(cudaMemcpyAsync(dh, c->dh_out, n_iter * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-    }
-    if (stats) {
-        double s[kScalars];
-        int64_t cnt[kCounters];
-        CU(cudaMemcpyAsync(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
-        stats->iterations = n_iter;
-        stats->accepted = cnt[kAccepted] - acc_before;
-        stats->last_dh = s[kLastDH];
-        stats->last_loglik = s[kLogLik];
-    }
+int mds_hmc_enqueue(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed) {
+    CHECK(check_ctx(c));
+    if (n_iter < 0 || n_steps < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_iter and n_steps must be >= 0");
+    if (!std::isfinite(eps)) return fail(c, MDS_ERR_INVALID_ARG, "eps must be finite");
+    CHECK(ready(c));
+    if (!c->grad_valid) CHECK(evaluate(c));
+    CHECK(autotune(c));
+    if (n_iter == 0) return MDS_OK;
+    return hmc_enqueue(c, n_iter, n_steps, eps, seed, 0);
+}
+
+int mds_hmc_collect(mds_ctx *c, int64_t cap, int32_t *accepted, double *dh, int64_t *count, mds_hmc_stats *stats) {
+    CHECK(check_ctx(c));
+    if (cap < 0) return fail(c, MDS_ERR_INVALID_ARG, "cap must be >= 0");
+    int64_t n = 0;
+    int st = hmc_collect(c, cap, accepted, dh, &n, stats, "hmc");
+    if (count) *count = n;
     return st;
 }
 
@@ -1076,7 +1172,6 @@ int mds_time_pass(mds_ctx *c, int reps, double *ms_per_pass) {
     CHECK(check_ctx(c));
     if (reps < 1 || !ms_per_pass) return fail(c, MDS_ERR_INVALID_ARG, "reps must be >= 1 and ms_per_pass non-NULL");
     CHECK(ready(c));
-    CHECK(refresh_split(c, false));
     CHECK(autotune(c));
     const bool prof = c->profiling;
     c->profiling = false;
@@ -1220,7 +1315,6 @@ int batch_tables(mds_batch *b, int strip) {
         CHECK(bpass(b, c, ready(c)));
         c->strip_req = strip;
         if (c->strip != strip) CHECK(bpass(b, c, build_strips(c, strip)));
-        CHECK(bpass(b, c, refresh_split(c, false)));
     }
     std::vector<BatchDataset> ds(b->n_data);
     std::vector<BatchChain> ch(total);
@@ -1543,7 +1637,7 @@ int mds_batch_hmc(mds_batch *b, int n_iter, int n_steps, const double *eps, uint
             tc[g] = make_traj_args(c, n_steps, eps[dd], 1, seed, static_cast<uint32_t>(g));
             ac[g] = make_accept_args(c, n_steps, 1, 1, seed, static_cast<uint32_t>(g), sg,
                                      b->acc_out + static_cast<size_t>(g) * n_iter,
-                                     b->dh_out + static_cast<size_t>(g) * n_iter);
+                                     b->dh_out + static_cast<size_t>(g) * n_iter, n_iter);
             BCU(cudaMemsetAsync(c->counters + kIterLocal, 0, sizeof(int64_t), b->stream));
         }
     }

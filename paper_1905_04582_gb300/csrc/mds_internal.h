@@ -2,6 +2,7 @@
 // kernels.  Not part of the public ABI (include/mds.h).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -86,6 +87,9 @@ enum ScalarPart : int {
 struct Split {
     float q;       // quantum
     float magic;   // 1.5 * 2^23 * q: (x + magic) - magic rounds x to a multiple of q
+    float bound;   // largest |x| this quantum splits exactly: (2^(B-1) - 1) q
+    int resplit;   // set by the end-of-trajectory reduction when it chose a new
+                   // quantum; the trajectory-end kernel then rewrites the layouts
 };
 
 // Arguments of the fused pair pass.
@@ -120,6 +124,8 @@ enum ErrBits : unsigned {
     kErrNonfinite = 2u,   // a partial sum was NaN / Inf
     kErrBadArgs = 4u,     // kernel launched with inconsistent arguments
     kErrBadInput = 8u,    // an input value was negative / NaN / Inf
+    kErrRange = 16u,      // locations beyond the range the FP32C split serves
+    kErrOverflow = 32u,   // more HMC iterations queued than the result buffers hold
 };
 
 // ---------------------------------------------------------------------------
@@ -212,7 +218,7 @@ struct XState {
     void *x;                  // [n_pad][D] (float / double): the state
     float4 *xrow;             // FP32C split layouts (null on the FP64 path)
     float4 *xcol;
-    const Split *split;       // FP32C quantum (device)
+    Split *split;             // FP32C quantum (device; grown by the end-of-trajectory reduction)
     unsigned *xmax_bits;      // FP32C: running max |x| (float bits, atomicMax)
 };
 
@@ -287,8 +293,9 @@ struct AcceptArgs {
     const double *grad0;
     double *scal;
     int64_t *counters;
-    int32_t *acc_out;         // [n_iter] per-iteration decision (optional)
-    double *dh_out;           // [n_iter] per-iteration H1 - H0 (optional)
+    int32_t *acc_out;         // [out_cap] per-iteration decision (optional)
+    double *dh_out;           // [out_cap] per-iteration H1 - H0 (optional)
+    int64_t out_cap;          // entries of acc_out / dh_out
     unsigned *err;
 };
 cudaError_t launch_traj_end(const AcceptArgs &a, cudaStream_t s);
@@ -334,5 +341,56 @@ void set_thread_error(const char *fmt, ...);
 
 // Bits B of the exact-difference split for D dimensions (see above).
 __host__ __device__ inline int split_bits(int d) { return d <= 1 ? 12 : d <= 4 ? 11 : 10; }
+
+// The split quantum for max |x| = m: q = 2^e, the smallest power of two with
+// (2^(B-1) - 1) q >= 4 m (4x headroom for the moves of a trajectory).  The
+// same function runs on the host (locations set by the caller) and on the
+// device (growth during a trajectory), so both pick the same quantum for the
+// same m.  False when q would leave [2^-100, 2^103] (x beyond FP32C range).
+__host__ __device__ inline bool choose_split(float m, int d, Split &sp) {
+    const double lim = static_cast<double>((1 << (split_bits(d) - 1)) - 1);
+    const double v = (static_cast<double>(m) > 1e-30 ? static_cast<double>(m) : 1e-30) * 4.0 / lim;
+    int e = 0;
+    const double f = frexp(v, &e);          // v = f 2^e, f in [0.5, 1)
+    const int ex = f == 0.5 ? e - 1 : e;    // ceil(log2 v)
+    if (ex < -100 || ex > 103) return false;
+    sp.q = ldexpf(1.0f, ex);
+    sp.magic = ldexpf(1.5f, ex + 23);
+    sp.bound = static_cast<float>(lim * ldexp(1.0, ex));
+    sp.resplit = 0;
+    return true;
+}
+
+// Programmatic dependent launch.  The pair pass and the reduction alternate
+// 2 L times per trajectory; launched with launch_pdl, a kernel may become
+// resident while the previous kernel of the stream is still draining, runs
+// its prologue (barrier set-up, prefetch of the constant Y tiles), and must
+// call pdl_wait() before it reads anything the previous kernel writes or
+// writes anything the previous kernel reads.  pdl_wait() returns at once in
+// a kernel launched without the attribute.  pdl_trigger() lets the next
+// kernel be scheduled once every CTA of this one has called it (or exited);
+// each kernel that calls it is itself only launched after all CTAs of its
+// predecessor are resident, so early-resident waiting CTAs never hold back
+// a CTA that still has to start.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" : : : "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" : : : "memory"); }
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 }  // namespace mds

@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
+    pdl_trigger();
     if (blockIdx.x >= static_cast<unsigned>(a.n_strips)) return;
-    const Strip st = a.strips[blockIdx.x];
+    const Strip st = a.strips[blockIdx.x];  // the strip table is fixed between passes
     const int nst = st.j1 - st.j0;
     if (nst < 1 || st.j1 > a.nt || st.I > st.j0) {
         if (tid == 0) atomicOr(a.err, kErrBadArgs);
@@ -96,12 +97,23 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
     const float *ysrc0 = a.y + t0 * kTileElems + warp * kWarpTileElems;
     const float4 *xsrc0 = a.xcol + (static_cast<int64_t>(st.j0) * kTile + warp * kWarpCols) * D;
 
+    // prologue: the first stages' Y quarters (Y is constant) may stream in
+    // while the previous kernel drains; the locations and every partial
+    // buffer belong to it until pdl_wait() returns
+    constexpr uint32_t kXjBytes = kWarpCols * D * 16;
     if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
+        for (int s = 0; s < kStages && s < nst; ++s) {
+            mbar_expect_tx(&bars[s], kWarpTileElems * 4 + kXjBytes);
+            tma_load_1d(ring + s * L::kStageBytes, ysrc0 + s * kTileElems, kWarpTileElems * 4, &bars[s]);
+        }
+    }
+    pdl_wait();
+    if (lane == 0) {
         for (int s = 0; s < kStages && s < nst; ++s)
-            issue_stage<D>(ring + s * L::kStageBytes, &bars[s], ysrc0 + s * kTileElems, xsrc0 + s * kTile * D);
+            tma_load_1d(ring + s * L::kStageBytes + kWarpTileElems * 4, xsrc0 + s * kTile * D, kXjBytes, &bars[s]);
     }
     // x_i of the row block: 32 row pairs x D, stored [k][rp] in shared memory
     for (int idx = tid; idx < 32 * D; idx += kPairThreads) {
@@ -196,6 +208,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
         if (tid == 0) atomicOr(a.err, kErrBadArgs);
         return;
     }
+    pdl_wait();
     const int64_t nt = a.nt, n = a.n;
     const bool ragged = (n % kTile) != 0;
     const int64_t t0 = tile_index(st.I, st.j0, nt);
@@ -330,15 +343,15 @@ cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s) {
         attr_set = true;
     }
     if (a.n_strips <= 0) return cudaSuccess;
-    pair_f32_kernel<D><<<a.n_strips, kPairThreads, L::kBytes, s>>>(a);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(pair_f32_kernel<D>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_f64_d(const PairArgs &a, cudaStream_t s) {
     if (a.n_strips <= 0) return cudaSuccess;
-    pair_f64_kernel<D><<<a.n_strips, kPairThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(pair_f64_kernel<D>, dim3(a.n_strips), dim3(kPairThreads), 0, s, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace

@@ -150,6 +150,9 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     __shared__ Acc sm[kSplits * kTile * D > 64 ? kSplits * kTile * D : 64];
     const int tid = threadIdx.x;
     const int nt = a.nt;
+    // every input (partials, x, p) comes from the pass just before
+    pdl_trigger();
+    pdl_wait();
 
     if (J < 0) {
         // scalar partials of all strips -> L, sum r, dL/dsigma (fixed order)
@@ -200,6 +203,27 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             a.scal[kDSigma] = ds;
             a.scal[kLogLikEnd] = ll;
             if (!isfinite(ll) || !isfinite(ds)) atomicOr(a.err, kErrNonfinite);
+            if constexpr (kF32) {
+                if (mode == kModeHalfKick) {
+                    // end of a trajectory (no CTA of this launch reads the split):
+                    // grow the quantum if the running max |x| outgrew it; the
+                    // trajectory-end kernel rewrites the layouts
+                    Split sp = *a.xs.split;
+                    const float m = __uint_as_float(*a.xs.xmax_bits);
+                    int rs = 0;
+                    if (m > sp.bound) {
+                        Split ns;
+                        if (choose_split(m, D, ns)) {
+                            sp = ns;
+                            rs = 1;
+                        } else {
+                            atomicOr(a.err, kErrRange);
+                        }
+                    }
+                    sp.resplit = rs;
+                    *a.xs.split = sp;
+                }
+            }
         }
         return;
     }
@@ -549,6 +573,8 @@ __device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int n
     __syncthreads();
     const int keep = keep_s;
     const int64_t nd = a.n * D;
+    bool resplit = false;  // FP32C: the last reduction chose a new quantum
+    if constexpr (std::is_same<T, float>::value) resplit = a.xs.split->resplit != 0;
     if (!keep) {
         const T *x0 = reinterpret_cast<const T *>(a.x0);
         G *grad = reinterpret_cast<G *>(a.grad);
@@ -558,6 +584,11 @@ __device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int n
             store_x<T>(a.xs, e / D, D, static_cast<int>(e % D), x0[e]);
             grad[e] = grad0[e];
         }
+    } else if (resplit) {
+        const T *x = reinterpret_cast<const T *>(a.xs.x);
+        for (int64_t e = static_cast<int64_t>(bx) * kTrajThreads + threadIdx.x; e < nd;
+             e += static_cast<int64_t>(nbx) * kTrajThreads)
+            store_x<T>(a.xs, e / D, D, static_cast<int>(e % D), x[e]);
     }
     if (bx == 0 && threadIdx.x == 0) {
         const double dh = dh_s;
@@ -569,8 +600,12 @@ __device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int n
             a.scal[kDSigma] = a.scal[kDSigma0];
         }
         const int64_t il = a.counters[kIterLocalCur];
-        if (a.acc_out) a.acc_out[il] = keep;
-        if (a.dh_out) a.dh_out[il] = dh;
+        if (il >= 0 && il < a.out_cap) {
+            if (a.acc_out) a.acc_out[il] = keep;
+            if (a.dh_out) a.dh_out[il] = dh;
+        } else if (a.acc_out || a.dh_out) {
+            atomicOr(a.err, kErrOverflow);
+        }
         if (a.metropolis) {
             a.counters[kIter] = a.counters[kIterCur] + 1;
             a.counters[kIterLocal] = il + 1;
@@ -600,6 +635,19 @@ __global__ void __launch_bounds__(kTrajThreads) traj_end_batch_kernel(const Acce
         case 7: KERNEL<T, 7><<<GRID, BLOCK, 0, STREAM>>>(ARGS); break;           \
         case 8: KERNEL<T, 8><<<GRID, BLOCK, 0, STREAM>>>(ARGS); break;           \
         default: return cudaErrorInvalidValue;                                   \
+    }
+
+#define MDS_SWITCH_D_PDL(KERNEL, T, GRID, BLOCK, STREAM, ARGS)                               \
+    switch ((ARGS).d) {                                                                     \
+        case 1: e = launch_pdl(KERNEL<T, 1>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        case 2: e = launch_pdl(KERNEL<T, 2>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        case 3: e = launch_pdl(KERNEL<T, 3>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        case 4: e = launch_pdl(KERNEL<T, 4>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        case 5: e = launch_pdl(KERNEL<T, 5>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        case 6: e = launch_pdl(KERNEL<T, 6>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        case 7: e = launch_pdl(KERNEL<T, 7>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        case 8: e = launch_pdl(KERNEL<T, 8>, dim3(GRID), dim3(BLOCK), 0, STREAM, ARGS); break; \
+        default: return cudaErrorInvalidValue;                                              \
     }
 
 // ----------------------------------------------------------------- ingest
@@ -727,12 +775,13 @@ int grid_for(int64_t work, int threads) {
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t s) {
     const dim3 grid(a.nt + 1);  // one CTA per column block + one for the scalars
+    cudaError_t e = cudaSuccess;
     if (a.fp64) {
-        MDS_SWITCH_D(reduce_kernel, double, grid, kRedThreads, s, a)
+        MDS_SWITCH_D_PDL(reduce_kernel, double, grid, kRedThreads, s, a)
     } else {
-        MDS_SWITCH_D(reduce_kernel, float, grid, kRedThreads, s, a)
+        MDS_SWITCH_D_PDL(reduce_kernel, float, grid, kRedThreads, s, a)
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_traj_start(const TrajArgs &a, int *grid_out, cudaStream_t s) {

@@ -212,6 +212,25 @@ class MDS:
         return acc.astype(bool), dh, {"iterations": stats.iterations, "accepted": stats.accepted,
                                       "last_dh": stats.last_dh, "last_loglik": stats.last_loglik}
 
+    def hmc_enqueue(self, n_iter, n_steps, eps, seed=0):
+        """Queue n_iter HMC iterations on the context's stream; no waiting."""
+        self._check(self._lib.mds_hmc_enqueue(self._h, int(n_iter), int(n_steps), float(eps),
+                                              int(seed) & (2**64 - 1)))
+
+    def hmc_collect(self, cap=1 << 16):
+        """Wait for the queued iterations; returns (accepted, dH, stats) of
+        all of them in queue order (at most `cap` entries)."""
+        acc = np.zeros(cap, dtype=np.int32)
+        dh = np.zeros(cap, dtype=np.float64)
+        cnt = ctypes.c_int64()
+        stats = capi.mds_hmc_stats()
+        self._check(self._lib.mds_hmc_collect(self._h, int(cap), acc.ctypes.data_as(ctypes.c_void_p),
+                                              dh.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt),
+                                              ctypes.byref(stats)))
+        k = min(cnt.value, cap)
+        return acc[:k].astype(bool), dh[:k], {"iterations": stats.iterations, "accepted": stats.accepted,
+                                              "last_dh": stats.last_dh, "last_loglik": stats.last_loglik}
+
 
 class Batch:
     """Several datasets (uneven N, same D), each with several HMC chains,

@@ -150,3 +150,59 @@ def test_reject_restores_state_and_likelihood(prec):
             assert e.status == MDS_ERR_NONFINITE
         assert np.array_equal(m.get_locations(), x0)
         assert m.log_likelihood()[0] == ll0
+
+
+def test_enqueue_collect_matches_hmc():
+    """Queued iterations (two enqueues, the second outgrowing the result
+    buffer so the first results move to the host) give exactly the chain and
+    per-iteration results of one synchronous call with the same seed."""
+    from paper_1905_04582_gb300.capi import MDSError
+    wl = W.small()
+    with model_for(wl, "fp32c") as a:
+        acc_a, dh_a, st_a = a.hmc(6, 10, 1.5e-2, seed=5)
+        xa = a.get_locations()
+    with model_for(wl, "fp32c") as b:
+        b.hmc_enqueue(2, 10, 1.5e-2, seed=5)
+        b.hmc_enqueue(4, 10, 1.5e-2, seed=5)
+        with pytest.raises(MDSError):
+            b.hmc(1, 10, 1.5e-2, seed=5)  # refused while results are queued
+        acc_b, dh_b, st_b = b.hmc_collect()
+        xb = b.get_locations()
+        acc_c, dh_c, st_c = b.hmc_collect()  # nothing queued any more
+    assert np.array_equal(acc_a, acc_b) and np.array_equal(dh_a, dh_b)
+    assert np.array_equal(xa, xb)
+    assert st_b["iterations"] == 6 and st_b["accepted"] == int(acc_b.sum()) == st_a["accepted"]
+    assert st_b["last_loglik"] == st_a["last_loglik"]
+    assert len(acc_c) == 0 and st_c["iterations"] == 0
+
+
+def test_quantum_grows_on_device_during_trajectory():
+    """Locations that expand ~20x in one trajectory (a weak likelihood,
+    sigma = 50, and outward momenta) leave the 4x headroom of the split
+    chosen when they were set.  The end-of-trajectory reduction then picks
+    the quantum that a context given the end point picks, so a fresh
+    evaluation is bit-identical to one on such a context, and matches the
+    oracle."""
+    from paper_1905_04582_gb300.mds import MDS
+    from gpu_util import TOL, grad_check
+    n, d, sigma = 300, 2, 50.0
+    wl = W.custom(n, d, sigma=sigma, seed=77, noise=0.3)
+    x = (wl.x_eval / np.abs(wl.x_eval).max()).astype(np.float32)  # max |x| = 1
+    p0 = 40.0 * x.astype(np.float64)
+    with MDS(n, d, "fp32c", strip=2) as a:
+        a.set_data(wl.y_packed)
+        a.set_locations(x)
+        a.set_sigma(sigma)
+        a.leapfrog(10, 0.05, p0=p0)
+        xe = a.get_locations(dtype=np.float32)
+        ll_a, g_a, ds_a = a.gradient()
+    assert np.abs(xe).max() > 8.0  # well past the headroom of the first quantum
+    with MDS(n, d, "fp32c", strip=2) as b:
+        b.set_data(wl.y_packed)
+        b.set_locations(xe)
+        b.set_sigma(sigma)
+        ll_b, g_b, ds_b = b.gradient()
+    assert ll_a == ll_b and ds_a == ds_b
+    assert np.array_equal(g_a, g_b)
+    g_r, s_abs, s_sq = oracle.gradient(wl.y_packed, xe.astype(np.float64), sigma, with_abs=True, with_sq=True)
+    grad_check(g_a, g_r, s_abs, TOL["fp32c"]["g"], s_sq=s_sq, u=TOL["fp32c"]["u"])
