@@ -48,18 +48,20 @@ def _load():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
-            lib.mdso_loglik.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp, _vp]
-            lib.mdso_gradient_rows.argtypes = [_i64, _int, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp, _vp]
-            lib.mdso_dsigma.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp]
-            lib.mdso_leapfrog.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int,
-                                          _int, _vp, _vp]
-            lib.mdso_hmc.argtypes = [_i64, _int, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _int, _vp,
-                                     _vp, _int, _vp, _vp]
+            lib.mdso_loglik_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _int, _vp, _vp]
+            lib.mdso_gradient_rows_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _vp, _i64, _int, _vp,
+                                                    _vp, _vp]
+            lib.mdso_dsigma_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _int, _vp]
+            lib.mdso_leapfrog_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl,
+                                               _int, _int, _vp, _vp]
+            lib.mdso_hmc_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _int,
+                                          _vp, _vp, _int, _vp, _vp]
+            lib.mdso_lpd.argtypes = [_i64, _int, _vp, _i64, _vp, _int, _vp, _vp, _vp]
             lib.mdso_philox4x32_10.argtypes = [_vp, _vp, _vp]
             lib.mdso_draw_momentum.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.c_uint32, _i64, _vp, _vp]
-            for f in ("mdso_loglik", "mdso_gradient_rows", "mdso_dsigma", "mdso_leapfrog",
-                      "mdso_hmc"):
+            for f in ("mdso_loglik_kept", "mdso_gradient_rows_kept", "mdso_dsigma_kept",
+                      "mdso_leapfrog_kept", "mdso_hmc_kept", "mdso_lpd"):
                 getattr(lib, f).restype = _int
             lib.mdso_philox4x32_10.restype = None
             lib.mdso_draw_momentum.restype = None
@@ -87,20 +89,45 @@ def _check(st, what):
         raise RuntimeError(f"oracle {what} failed with status {st}")
 
 
-def loglik(yp, x, sigma, nthreads=1):
-    """Return (L, sum_r): L = -M log sigma - sum_{i<j} r_ij (Eq. 2)."""
+def keep_mask(n, heldout):
+    """Training mask for a cross-validation fold (section 2.4): one byte per
+    packed pair i < j, 0 for the held-out pairs (any order within a pair)."""
+    keep = np.ones(n * (n - 1) // 2, dtype=np.uint8)
+    for i, j in np.asarray(heldout, dtype=np.int64).reshape(-1, 2):
+        a, b = (i, j) if i < j else (j, i)
+        if a == b or a < 0 or b >= n:
+            raise ValueError(f"bad held-out pair ({i}, {j})")
+        keep[a * n - a * (a + 1) // 2 + (b - a - 1)] = 0
+    return keep
+
+
+def _keep_ptr(keep, n):
+    if keep is None:
+        return None, None
+    k = np.ascontiguousarray(keep, dtype=np.uint8)
+    if k.shape != (n * (n - 1) // 2,):
+        raise ValueError("keep must hold one byte per packed pair")
+    return k, _ptr(k)
+
+
+def loglik(yp, x, sigma, nthreads=1, keep=None):
+    """Return (L, sum_r): L = -M log sigma - sum_{i<j} r_ij (Eq. 2), over the
+    pairs with keep != 0 when a training mask is given (M = their count)."""
     yp, x, n, d = _prep(yp, x)
+    k, kp = _keep_ptr(keep, n)
     sr = np.zeros(1)
     ll = np.zeros(1)
-    _check(_load().mdso_loglik(n, d, _ptr(yp), _ptr(x), float(sigma), int(nthreads), _ptr(sr),
-                               _ptr(ll)), "loglik")
+    _check(_load().mdso_loglik_kept(n, d, _ptr(yp), kp, _ptr(x), float(sigma), int(nthreads), _ptr(sr),
+                                    _ptr(ll)), "loglik")
     return float(ll[0]), float(sr[0])
 
 
-def gradient(yp, x, sigma, rows=None, nthreads=1, with_abs=False, with_sq=False):
+def gradient(yp, x, sigma, rows=None, nthreads=1, with_abs=False, with_sq=False, keep=None):
     """Gradient of L in X (Eq. 9) for `rows` (all when None); optionally also
-    S_ik = sum_j |term_ijk| (with_abs) and sqrt(sum_j term_ijk^2) (with_sq)."""
+    S_ik = sum_j |term_ijk| (with_abs) and sqrt(sum_j term_ijk^2) (with_sq).
+    keep: training mask (pairs with keep == 0 are left out)."""
     yp, x, n, d = _prep(yp, x)
+    k, kp = _keep_ptr(keep, n)
     if rows is None:
         rr = None
         cnt = n
@@ -110,9 +137,10 @@ def gradient(yp, x, sigma, rows=None, nthreads=1, with_abs=False, with_sq=False)
     g = np.zeros((cnt, d))
     a = np.zeros((cnt, d)) if with_abs else None
     q = np.zeros((cnt, d)) if with_sq else None
-    _check(_load().mdso_gradient_rows(n, d, _ptr(yp), _ptr(x), float(sigma),
-                                      None if rr is None else _ptr(rr), cnt, int(nthreads), _ptr(g),
-                                      None if a is None else _ptr(a), None if q is None else _ptr(q)), "gradient")
+    _check(_load().mdso_gradient_rows_kept(n, d, _ptr(yp), kp, _ptr(x), float(sigma),
+                                           None if rr is None else _ptr(rr), cnt, int(nthreads), _ptr(g),
+                                           None if a is None else _ptr(a), None if q is None else _ptr(q)),
+           "gradient")
     out = (g,)
     if with_abs:
         out += (a,)
@@ -121,36 +149,39 @@ def gradient(yp, x, sigma, rows=None, nthreads=1, with_abs=False, with_sq=False)
     return out if len(out) > 1 else g
 
 
-def dsigma(yp, x, sigma, nthreads=1):
-    """d L / d sigma (Eq. 2 differentiated in sigma)."""
+def dsigma(yp, x, sigma, nthreads=1, keep=None):
+    """d L / d sigma (Eq. 2 differentiated in sigma), over the kept pairs."""
     yp, x, n, d = _prep(yp, x)
+    k, kp = _keep_ptr(keep, n)
     out = np.zeros(1)
-    _check(_load().mdso_dsigma(n, d, _ptr(yp), _ptr(x), float(sigma), int(nthreads), _ptr(out)),
+    _check(_load().mdso_dsigma_kept(n, d, _ptr(yp), kp, _ptr(x), float(sigma), int(nthreads), _ptr(out)),
            "dsigma")
     return float(out[0])
 
 
-def leapfrog(yp, x, p, sigma, eps, n_steps, w=1.0, lam=0.0, nthreads=1):
+def leapfrog(yp, x, p, sigma, eps, n_steps, w=1.0, lam=0.0, nthreads=1, keep=None):
     """n_steps leapfrog steps (M = I); returns (x, p, H0, H1)."""
     x = np.array(x, dtype=np.float64, order="C", copy=True)
     p = np.array(p, dtype=np.float64, order="C", copy=True)
     n, d = x.shape
+    k, kp = _keep_ptr(keep, n)
     if yp is None:
         ypp = None
     else:
         ypp = np.ascontiguousarray(yp, dtype=np.float32)
     h = np.zeros(2)
-    _check(_load().mdso_leapfrog(n, d, None if ypp is None else _ptr(ypp), _ptr(x), _ptr(p),
-                                 float(sigma), float(w), float(lam), float(eps), int(n_steps),
-                                 int(nthreads), _ptr(h[0:]), h[1:].ctypes.data_as(_vp)), "leapfrog")
+    _check(_load().mdso_leapfrog_kept(n, d, None if ypp is None else _ptr(ypp), kp, _ptr(x), _ptr(p),
+                                      float(sigma), float(w), float(lam), float(eps), int(n_steps),
+                                      int(nthreads), _ptr(h[0:]), h[1:].ctypes.data_as(_vp)), "leapfrog")
     return x, p, float(h[0]), float(h[1])
 
 
-def hmc(yp, x, sigma, eps, n_steps, p_all, u_all, w=1.0, lam=0.0, nthreads=1):
+def hmc(yp, x, sigma, eps, n_steps, p_all, u_all, w=1.0, lam=0.0, nthreads=1, keep=None):
     """HMC with caller-supplied momenta (n_iter x N x D) and uniforms (n_iter);
     returns (x, accepted[n_iter], dH[n_iter])."""
     x = np.array(x, dtype=np.float64, order="C", copy=True)
     n, d = x.shape
+    k, kp = _keep_ptr(keep, n)
     p_all = np.ascontiguousarray(p_all, dtype=np.float64)
     u_all = np.ascontiguousarray(u_all, dtype=np.float64)
     n_iter = u_all.shape[0]
@@ -159,10 +190,26 @@ def hmc(yp, x, sigma, eps, n_steps, p_all, u_all, w=1.0, lam=0.0, nthreads=1):
     ypp = None if yp is None else np.ascontiguousarray(yp, dtype=np.float32)
     acc = np.zeros(n_iter, dtype=np.int32)
     dh = np.zeros(n_iter)
-    _check(_load().mdso_hmc(n, d, None if ypp is None else _ptr(ypp), _ptr(x), float(sigma),
-                            float(w), float(lam), float(eps), int(n_steps), int(n_iter), _ptr(p_all),
-                            _ptr(u_all), int(nthreads), _ptr(acc), _ptr(dh)), "hmc")
+    _check(_load().mdso_hmc_kept(n, d, None if ypp is None else _ptr(ypp), kp, _ptr(x), float(sigma),
+                                 float(w), float(lam), float(eps), int(n_steps), int(n_iter), _ptr(p_all),
+                                 _ptr(u_all), int(nthreads), _ptr(acc), _ptr(dh)), "hmc")
     return x, acc.astype(bool), dh
+
+
+def lpd(yp, heldout, xs, sigmas):
+    """Log pointwise predictive density estimate (section 2.4) over the
+    held-out pairs (K x 2) from S posterior draws: locations xs (S x N x D)
+    and sigmas (S)."""
+    yp = np.ascontiguousarray(yp, dtype=np.float32)
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    if xs.ndim == 2:
+        xs = xs[None]
+    S, n, d = xs.shape
+    sg = np.ascontiguousarray(np.broadcast_to(np.asarray(sigmas, dtype=np.float64), (S,)))
+    pr = np.ascontiguousarray(heldout, dtype=np.int64).reshape(-1, 2)
+    out = np.zeros(1)
+    _check(_load().mdso_lpd(n, d, _ptr(yp), pr.shape[0], _ptr(pr), S, _ptr(xs), _ptr(sg), _ptr(out)), "lpd")
+    return float(out[0])
 
 
 def philox4x32_10(counter, key):

@@ -39,6 +39,15 @@
  *   - HMC target log pi(X) = w * L(X, sigma) - (lambda / 2) ||X||_F^2 with
  *     w in {0, 1} and lambda >= 0 (lambda = 0 by default; w = 0 gives the
  *     harmonic oscillator used to pin the integrator).
+ *   - Cross-validation (section 2.4): a fold holds out a set of pairs; the
+ *     training likelihood is Eq. (2) over the kept pairs only (M = their
+ *     count), and the Monte Carlo estimate of the log pointwise predictive
+ *     density is, over held-out pairs,
+ *       lpd-hat = sum_ij log( (1/S) sum_s p(y_ij | X_s, sigma_s) ),
+ *     p the truncated-normal density of Eq. (1).  The printed estimator also
+ *     multiplies each term by the posterior density of the draw; with draws
+ *     taken from that posterior the plain average is the standard estimate,
+ *     which is the one computed here.
  */
 #include <math.h>
 #include <stddef.h>
@@ -126,12 +135,27 @@ static double neg_dr_dsigma(double y, double delta, double sigma) {
            std_normal_pdf(z) * delta / (sigma * sigma * std_normal_cdf(z));
 }
 
-/* Sum over i < j of r_ij, with the pairs of row i summed first (per-row
- * Neumaier sums), rows then summed in order.  Rows are independent, so
- * `nthreads` > 1 splits them over OpenMP threads; the result does not depend
- * on the thread count. */
-static int sum_r_rows(int64_t n, int d, const float *yp, const double *x, double sigma,
-                      int nthreads, double *out) {
+/* keep[] (one byte per packed pair, NULL = all pairs): does pair (i, j)
+ * belong to the training data? */
+static int pair_kept(const unsigned char *keep, int64_t n, int64_t i, int64_t j) {
+    if (!keep) return 1;
+    return i < j ? keep[packed_index(n, i, j)] != 0 : keep[packed_index(n, j, i)] != 0;
+}
+
+/* Number of training pairs. */
+static double kept_pairs(const unsigned char *keep, int64_t n) {
+    if (!keep) return 0.5 * (double)n * (double)(n - 1);
+    double m = 0.0;
+    for (int64_t k = 0; k < n * (n - 1) / 2; ++k) m += keep[k] != 0;
+    return m;
+}
+
+/* Sum over kept pairs i < j of r_ij, with the pairs of row i summed first
+ * (per-row Neumaier sums), rows then summed in order.  Rows are independent,
+ * so `nthreads` > 1 splits them over OpenMP threads; the result does not
+ * depend on the thread count. */
+static int sum_r_rows(int64_t n, int d, const float *yp, const unsigned char *keep, const double *x,
+                      double sigma, int nthreads, double *out) {
     double *row = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     if (!row) return MDSO_OOM;
     int64_t i;
@@ -141,7 +165,8 @@ static int sum_r_rows(int64_t n, int d, const float *yp, const double *x, double
     for (i = 0; i < n; ++i) {
         nsum_t s = {0.0, 0.0};
         for (int64_t j = i + 1; j < n; ++j)
-            nsum_add(&s, r_term((double)yp[packed_index(n, i, j)], distance(x, d, i, j), sigma));
+            if (pair_kept(keep, n, i, j))
+                nsum_add(&s, r_term((double)yp[packed_index(n, i, j)], distance(x, d, i, j), sigma));
         row[i] = nsum_get(&s);
     }
     (void)nthreads;
@@ -155,16 +180,21 @@ static int sum_r_rows(int64_t n, int d, const float *yp, const double *x, double
 /* Log-likelihood, Eq. (2) and the last line of Algorithm 1:
  *   log p(Y | X, sigma) = -M log sigma - sum_{i<j} r_ij
  * ((sigma^2)^(N(1-N)/4) = sigma^(-M)).  Also returns sum_{i<j} r_ij. */
-int mdso_loglik(int64_t n, int d, const float *yp, const double *x, double sigma,
-                int nthreads, double *sum_r, double *loglik) {
+int mdso_loglik_kept(int64_t n, int d, const float *yp, const unsigned char *keep, const double *x,
+                     double sigma, int nthreads, double *sum_r, double *loglik) {
     if (n < 2 || d < 1 || !(sigma > 0.0) || !yp || !x) return MDSO_BAD_ARG;
     double sr = 0.0;
-    int st = sum_r_rows(n, d, yp, x, sigma, nthreads, &sr);
+    int st = sum_r_rows(n, d, yp, keep, x, sigma, nthreads, &sr);
     if (st) return st;
-    double m = 0.5 * (double)n * (double)(n - 1);
+    double m = kept_pairs(keep, n);
     if (sum_r) *sum_r = sr;
     if (loglik) *loglik = -m * log(sigma) - sr;
     return MDSO_OK;
+}
+
+int mdso_loglik(int64_t n, int d, const float *yp, const double *x, double sigma,
+                int nthreads, double *sum_r, double *loglik) {
+    return mdso_loglik_kept(n, d, yp, NULL, x, sigma, nthreads, sum_r, loglik);
 }
 
 /* Gradient of the log-likelihood with respect to x_i, Eq. (9):
@@ -174,9 +204,9 @@ int mdso_loglik(int64_t n, int d, const float *yp, const double *x, double sigma
  * S_ik = sum_{j != i} |term_ijk| and sqterm (optional) sqrt(sum_{j != i}
  * term_ijk^2): the scales used to judge cancellation and rounding when a
  * lower-precision result is compared with this one. */
-int mdso_gradient_rows(int64_t n, int d, const float *yp, const double *x, double sigma,
-                       const int64_t *rows, int64_t nrows, int nthreads,
-                       double *grad, double *absterm, double *sqterm) {
+int mdso_gradient_rows_kept(int64_t n, int d, const float *yp, const unsigned char *keep,
+                            const double *x, double sigma, const int64_t *rows, int64_t nrows,
+                            int nthreads, double *grad, double *absterm, double *sqterm) {
     if (n < 2 || d < 1 || d > 16 || !(sigma > 0.0) || !yp || !x || !grad) return MDSO_BAD_ARG;
     int64_t count = rows ? nrows : n;
     int64_t r;
@@ -195,7 +225,7 @@ int mdso_gradient_rows(int64_t n, int d, const float *yp, const double *x, doubl
         }
         if (i >= 0 && i < n) {
             for (int64_t j = 0; j < n; ++j) {
-                if (j == i) continue;
+                if (j == i || !pair_kept(keep, n, i, j)) continue;
                 double delta = distance(x, d, i, j);
                 if (delta == 0.0) continue; /* coincident points add nothing */
                 double w = grad_factor(y_at(yp, n, i, j), delta, sigma);
@@ -217,11 +247,18 @@ int mdso_gradient_rows(int64_t n, int d, const float *yp, const double *x, doubl
     return MDSO_OK;
 }
 
+int mdso_gradient_rows(int64_t n, int d, const float *yp, const double *x, double sigma,
+                       const int64_t *rows, int64_t nrows, int nthreads,
+                       double *grad, double *absterm, double *sqterm) {
+    return mdso_gradient_rows_kept(n, d, yp, NULL, x, sigma, rows, nrows, nthreads, grad, absterm, sqterm);
+}
+
 /* Derivative of the log-likelihood in sigma (not printed in the paper;
  * obtained by differentiating Eq. (2), including its sigma^(-M) factor):
- *   d/dsigma log p = -M / sigma + sum_{i<j} neg_dr_dsigma(y_ij, delta_ij). */
-int mdso_dsigma(int64_t n, int d, const float *yp, const double *x, double sigma,
-                int nthreads, double *dsigma) {
+ *   d/dsigma log p = -M / sigma + sum_{i<j} neg_dr_dsigma(y_ij, delta_ij),
+ * over the kept pairs. */
+int mdso_dsigma_kept(int64_t n, int d, const float *yp, const unsigned char *keep, const double *x,
+                     double sigma, int nthreads, double *dsigma) {
     if (n < 2 || d < 1 || !(sigma > 0.0) || !yp || !x || !dsigma) return MDSO_BAD_ARG;
     double *row = (double *)malloc(sizeof(double) * (size_t)n);
     if (!row) return MDSO_OOM;
@@ -232,16 +269,22 @@ int mdso_dsigma(int64_t n, int d, const float *yp, const double *x, double sigma
     for (i = 0; i < n; ++i) {
         nsum_t s = {0.0, 0.0};
         for (int64_t j = i + 1; j < n; ++j)
-            nsum_add(&s, neg_dr_dsigma((double)yp[packed_index(n, i, j)], distance(x, d, i, j), sigma));
+            if (pair_kept(keep, n, i, j))
+                nsum_add(&s, neg_dr_dsigma((double)yp[packed_index(n, i, j)], distance(x, d, i, j), sigma));
         row[i] = nsum_get(&s);
     }
     (void)nthreads;
     nsum_t tot = {0.0, 0.0};
     for (i = 0; i < n; ++i) nsum_add(&tot, row[i]);
     free(row);
-    double m = 0.5 * (double)n * (double)(n - 1);
+    double m = kept_pairs(keep, n);
     *dsigma = -m / sigma + nsum_get(&tot);
     return MDSO_OK;
+}
+
+int mdso_dsigma(int64_t n, int d, const float *yp, const double *x, double sigma,
+                int nthreads, double *dsigma) {
+    return mdso_dsigma_kept(n, d, yp, NULL, x, sigma, nthreads, dsigma);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -249,15 +292,15 @@ int mdso_dsigma(int64_t n, int d, const float *yp, const double *x, double sigma
 /* ---------------------------------------------------------------------- */
 
 /* log pi(X) = w L(X, sigma) - lambda/2 ||X||^2 and its gradient (N x D). */
-static int target(int64_t n, int d, const float *yp, const double *x, double sigma,
-                  double w, double lambda, int nthreads, double *logpi, double *grad) {
+static int target(int64_t n, int d, const float *yp, const unsigned char *keep, const double *x,
+                  double sigma, double w, double lambda, int nthreads, double *logpi, double *grad) {
     int64_t nd = n * d;
     double ll = 0.0;
     if (w != 0.0) {
-        int st = mdso_loglik(n, d, yp, x, sigma, nthreads, NULL, &ll);
+        int st = mdso_loglik_kept(n, d, yp, keep, x, sigma, nthreads, NULL, &ll);
         if (st) return st;
         if (grad) {
-            st = mdso_gradient_rows(n, d, yp, x, sigma, NULL, 0, nthreads, grad, NULL, NULL);
+            st = mdso_gradient_rows_kept(n, d, yp, keep, x, sigma, NULL, 0, nthreads, grad, NULL, NULL);
             if (st) return st;
             for (int64_t k = 0; k < nd; ++k) grad[k] *= w;
         }
@@ -285,27 +328,73 @@ static double kinetic(int64_t nd, const double *p) {
  *   p <- p + eps/2 grad log pi(x);  x <- x + eps p;  p <- p + eps/2 grad log pi(x).
  * x and p (N x D) are advanced in place.  H0 / H1 receive the energy
  * H = -log pi(x) + p^T p / 2 (Eq. (6)) before and after. */
-int mdso_leapfrog(int64_t n, int d, const float *yp, double *x, double *p, double sigma,
-                  double w, double lambda, double eps, int n_steps, int nthreads,
-                  double *h0, double *h1) {
+int mdso_leapfrog_kept(int64_t n, int d, const float *yp, const unsigned char *keep, double *x,
+                       double *p, double sigma, double w, double lambda, double eps, int n_steps,
+                       int nthreads, double *h0, double *h1) {
     if (n < 2 || d < 1 || n_steps < 0 || !x || !p || (w != 0.0 && (!yp || !(sigma > 0.0))))
         return MDSO_BAD_ARG;
     int64_t nd = n * d;
     double *g = (double *)malloc(sizeof(double) * (size_t)nd);
     if (!g) return MDSO_OOM;
     double lp = 0.0;
-    int st = target(n, d, yp, x, sigma, w, lambda, nthreads, &lp, g);
+    int st = target(n, d, yp, keep, x, sigma, w, lambda, nthreads, &lp, g);
     if (st) { free(g); return st; }
     if (h0) *h0 = -lp + kinetic(nd, p);
     for (int s = 0; s < n_steps; ++s) {
         for (int64_t k = 0; k < nd; ++k) p[k] += 0.5 * eps * g[k];
         for (int64_t k = 0; k < nd; ++k) x[k] += eps * p[k];
-        st = target(n, d, yp, x, sigma, w, lambda, nthreads, &lp, g);
+        st = target(n, d, yp, keep, x, sigma, w, lambda, nthreads, &lp, g);
         if (st) { free(g); return st; }
         for (int64_t k = 0; k < nd; ++k) p[k] += 0.5 * eps * g[k];
     }
     if (h1) *h1 = -lp + kinetic(nd, p);
     free(g);
+    return MDSO_OK;
+}
+
+int mdso_leapfrog(int64_t n, int d, const float *yp, double *x, double *p, double sigma,
+                  double w, double lambda, double eps, int n_steps, int nthreads,
+                  double *h0, double *h1) {
+    return mdso_leapfrog_kept(n, d, yp, NULL, x, p, sigma, w, lambda, eps, n_steps, nthreads, h0, h1);
+}
+
+/* Truncated-normal density of one observation (Eq. (1): y ~ N(delta,
+ * sigma^2) restricted to y > 0), on the log scale:
+ *   log p(y | delta, sigma) = -log(sqrt(2 pi) sigma) - (y - delta)^2 / (2 sigma^2)
+ *                             - log Phi(delta / sigma). */
+static double log_density(double y, double delta, double sigma) {
+    double e = y - delta;
+    return -log(sqrt(2.0 * M_PI) * sigma) - e * e / (2.0 * sigma * sigma) - log_std_normal_cdf(delta / sigma);
+}
+
+/* Log pointwise predictive density estimate of section 2.4 over the held-out
+ * pairs (pairs[2 k], pairs[2 k + 1]), k < npairs, from S posterior draws
+ * (locations xs[s] (N x D) and sigmas[s]):
+ *   lpd-hat = sum_k log( (1/S) sum_s p(y_k | X_s, sigma_s) ),
+ * each log-mean evaluated as m + log(sum_s exp(l_s - m)) - log S with
+ * m = max_s l_s (the same number, without underflow of exp(l_s)). */
+int mdso_lpd(int64_t n, int d, const float *yp, int64_t npairs, const int64_t *pairs, int S,
+             const double *xs, const double *sigmas, double *lpd) {
+    if (n < 2 || d < 1 || npairs < 0 || S < 1 || !yp || !xs || !sigmas || !lpd || (npairs > 0 && !pairs))
+        return MDSO_BAD_ARG;
+    double *l = (double *)malloc(sizeof(double) * (size_t)S);
+    if (!l) return MDSO_OOM;
+    nsum_t tot = {0.0, 0.0};
+    for (int64_t k = 0; k < npairs; ++k) {
+        int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j) { free(l); return MDSO_BAD_ARG; }
+        double m = -INFINITY;
+        for (int s = 0; s < S; ++s) {
+            if (!(sigmas[s] > 0.0)) { free(l); return MDSO_BAD_ARG; }
+            l[s] = log_density(y_at(yp, n, i, j), distance(xs + (int64_t)s * n * d, d, i, j), sigmas[s]);
+            if (l[s] > m) m = l[s];
+        }
+        double e = 0.0;
+        for (int s = 0; s < S; ++s) e += exp(l[s] - m);
+        nsum_add(&tot, m + log(e) - log((double)S));
+    }
+    free(l);
+    *lpd = nsum_get(&tot);
     return MDSO_OK;
 }
 
@@ -316,9 +405,9 @@ int mdso_leapfrog(int64_t n, int d, const float *yp, double *x, double *p, doubl
  * min(1, exp(-H(x*,p*)) / exp(-H(x0,p0))) (Eq. (8)); u_all[t] in (0,1).
  * x (N x D) is updated in place.  accepted[t] (0/1) and dh[t] = H1 - H0 are
  * returned per iteration. */
-int mdso_hmc(int64_t n, int d, const float *yp, double *x, double sigma, double w,
-             double lambda, double eps, int n_steps, int n_iter, const double *p_all,
-             const double *u_all, int nthreads, int *accepted, double *dh) {
+int mdso_hmc_kept(int64_t n, int d, const float *yp, const unsigned char *keep, double *x, double sigma,
+                  double w, double lambda, double eps, int n_steps, int n_iter, const double *p_all,
+                  const double *u_all, int nthreads, int *accepted, double *dh) {
     if (n < 2 || d < 1 || n_iter < 0 || !x || !p_all || !u_all) return MDSO_BAD_ARG;
     int64_t nd = n * d;
     double *x1 = (double *)malloc(sizeof(double) * (size_t)nd);
@@ -328,7 +417,7 @@ int mdso_hmc(int64_t n, int d, const float *yp, double *x, double sigma, double 
         memcpy(x1, x, sizeof(double) * (size_t)nd);
         memcpy(p, p_all + (int64_t)t * nd, sizeof(double) * (size_t)nd);
         double h0 = 0.0, h1 = 0.0;
-        int st = mdso_leapfrog(n, d, yp, x1, p, sigma, w, lambda, eps, n_steps, nthreads, &h0, &h1);
+        int st = mdso_leapfrog_kept(n, d, yp, keep, x1, p, sigma, w, lambda, eps, n_steps, nthreads, &h0, &h1);
         if (st) { free(x1); free(p); return st; }
         int acc = log(u_all[t]) < h0 - h1;
         if (accepted) accepted[t] = acc;
@@ -338,6 +427,13 @@ int mdso_hmc(int64_t n, int d, const float *yp, double *x, double sigma, double 
     free(x1);
     free(p);
     return MDSO_OK;
+}
+
+int mdso_hmc(int64_t n, int d, const float *yp, double *x, double sigma, double w,
+             double lambda, double eps, int n_steps, int n_iter, const double *p_all,
+             const double *u_all, int nthreads, int *accepted, double *dh) {
+    return mdso_hmc_kept(n, d, yp, NULL, x, sigma, w, lambda, eps, n_steps, n_iter, p_all, u_all, nthreads,
+                         accepted, dh);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -39,6 +39,12 @@ MUTANTS = {
                         "for (int64_t k = 0; k < nd; ++k) x[k] += 0.5 * eps * p[k];"),
     "philox_multiplier": ("uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];",
                           "uint64_t p1 = (uint64_t)0xCD9E8D57u * c[1];"),
+    "fold_counts_all_pairs": ("if (!keep) return 0.5 * (double)n * (double)(n - 1);",
+                              "return 0.5 * (double)n * (double)(n - 1);"),
+    "fold_ignored_in_gradient": ("if (j == i || !pair_kept(keep, n, i, j)) continue;", "if (j == i) continue;"),
+    "lpd_drop_log_phi": ("- e * e / (2.0 * sigma * sigma) - log_std_normal_cdf(delta / sigma);",
+                         "- e * e / (2.0 * sigma * sigma);"),
+    "lpd_no_log_S": ("nsum_add(&tot, m + log(e) - log((double)S));", "nsum_add(&tot, m + log(e));"),
 }
 
 _i64, _int, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -56,6 +62,9 @@ def _build(tmp_path, name, src_text):
     lib.mdso_dsigma.argtypes = [_i64, _int, _vp, _vp, _dbl, _int, _vp]
     lib.mdso_leapfrog.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _int, _vp, _vp]
     lib.mdso_philox4x32_10.argtypes = [_vp, _vp, _vp]
+    lib.mdso_loglik_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _int, _vp, _vp]
+    lib.mdso_gradient_rows_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp, _vp]
+    lib.mdso_lpd.argtypes = [_i64, _int, _vp, _i64, _vp, _int, _vp, _vp, _vp]
     return lib
 
 
@@ -92,6 +101,43 @@ def _pins_hold(lib):
     ds = np.zeros(1)
     lib.mdso_dsigma(n, d, _p(y), _p(x), s, 1, _p(ds))
     if not math.isclose(ds[0], (ll(x, s + h) - ll(x, s - h)) / (2 * h), rel_tol=1e-6):
+        return False
+    # a cross-validation fold: training likelihood over the kept pairs, its
+    # gradient, and lpd-hat from two draws against scipy's truncated normal
+    fold = [(0, 3), (2, 7), (5, 8)]
+    keep = np.ones(len(dl), dtype=np.uint8)
+    for i, j in fold:
+        keep[i * n - i * (i + 1) // 2 + (j - i - 1)] = 0
+    kept = keep.astype(bool)
+    lk = np.zeros(1)
+    lib.mdso_loglik_kept(n, d, _p(y), _p(keep), _p(x), s, 1, None, _p(lk))
+    ref = stats.truncnorm.logpdf(y[kept].astype(np.float64), -dl[kept] / s, np.inf, loc=dl[kept], scale=s).sum() \
+        + 0.5 * kept.sum() * math.log(2 * math.pi)
+    if not math.isclose(lk[0], ref, rel_tol=1e-12):
+        return False
+    gk = np.zeros((n, d))
+    lib.mdso_gradient_rows_kept(n, d, _p(y), _p(keep), _p(x), s, None, 0, 1, _p(gk), None, None)
+
+    def llk(xx):
+        out = np.zeros(1)
+        lib.mdso_loglik_kept(n, d, _p(y), _p(keep), _p(np.ascontiguousarray(xx)), s, 1, None, _p(out))
+        return out[0]
+    for i in range(n):
+        xp = x.copy(); xp[i, 0] += h
+        xm = x.copy(); xm[i, 0] -= h
+        if not math.isclose(gk[i, 0], (llk(xp) - llk(xm)) / (2 * h), rel_tol=1e-5, abs_tol=1e-6):
+            return False
+    pr = np.array(fold, dtype=np.int64)
+    xs = np.ascontiguousarray(np.stack([x, x + 0.2]))
+    sg = np.array([s, 1.3 * s])
+    out = np.zeros(1)
+    lib.mdso_lpd(n, d, _p(y), len(fold), _p(pr), 2, _p(xs), _p(sg), _p(out))
+    yy = np.array([y[i * n - i * (i + 1) // 2 + (j - i - 1)] for i, j in fold], dtype=np.float64)
+    dens = np.zeros((2, len(fold)))
+    for t in range(2):
+        dd = np.linalg.norm(xs[t][pr[:, 0]] - xs[t][pr[:, 1]], axis=1)
+        dens[t] = stats.truncnorm.pdf(yy, -dd / sg[t], np.inf, loc=dd, scale=sg[t])
+    if not math.isclose(out[0], np.log(dens.mean(axis=0)).sum(), rel_tol=1e-12):
         return False
     # harmonic oscillator closed form
     lam, eps, steps = 1.0, 0.1, 5
