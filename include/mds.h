@@ -192,6 +192,46 @@ int mds_hmc_enqueue(mds_ctx *ctx, int n_iter, int n_steps, double eps, uint64_t 
 int mds_hmc_collect(mds_ctx *ctx, int64_t cap, int32_t *accepted, double *dh, int64_t *count,
                     mds_hmc_stats *stats);
 
+/* ------------------------------------------------------------------------
+ * Cross-validation (section 2.4 "Model selection" of arXiv:1905.04582).  A
+ * fold holds out a set of observations y_ij; the model is trained on the rest
+ * and scored on the held-out pairs by the log pointwise predictive density,
+ * estimated from S posterior draws (X_s, sigma_s) as
+ *   lpd-hat = sum_{held-out i<j} log( (1/S) sum_s p(y_ij | X_s, sigma_s) ),
+ * p the truncated-normal density of Eq. (1):
+ *   p(y | delta, sigma) = phi((y - delta) / sigma) / (sigma Phi(delta / sigma)), y > 0.
+ * (The paper's formula also multiplies each density by the posterior density
+ * of its draw; with draws taken from that posterior the plain average is the
+ * standard estimate, which is the one computed.)
+ * ------------------------------------------------------------------------ */
+
+/* Hold out the pairs pairs[2k], pairs[2k+1] (k < n_pairs; int64, host; each
+ * pair of distinct items in [0, N), in either order; duplicates count once):
+ * from now on L, dL/dX, dL/dsigma, leapfrog and HMC use the other pairs only,
+ * with M = the number of those (the training likelihood of the fold).  The
+ * held-out y are kept aside for the predictive density; the lpd-hat
+ * accumulators restart.  n_pairs = 0 (pairs may be NULL) restores every
+ * pair.  mds_set_data drops the fold.  Errors: INVALID_ARG (a bad pair),
+ * STATE (no data; queued HMC iterations), OOM, CUDA. */
+int mds_set_heldout(mds_ctx *ctx, const int64_t *pairs, int64_t n_pairs);
+
+/* Number of distinct held-out pairs of the current fold. */
+int mds_heldout_count(const mds_ctx *ctx, int64_t *count);
+
+/* Add the current state (X, sigma) as one posterior draw: the density p of
+ * every held-out pair enters its running average (FP64, per pair a running
+ * log-sum-exp, so no density underflows).  Synchronises.  Errors: STATE (no
+ * fold, locations or sigma; queued HMC iterations), NONFINITE, CUDA. */
+int mds_lpd_accumulate(mds_ctx *ctx);
+
+/* lpd-hat over the draws accumulated so far (fixed-order FP64 sum over the
+ * held-out pairs) into *lpd, and the number of draws S into *draws
+ * (optional).  Errors: STATE (no draw yet), CUDA. */
+int mds_lpd(mds_ctx *ctx, double *lpd, int64_t *draws);
+
+/* Forget the accumulated draws (the fold stays). */
+int mds_lpd_reset(mds_ctx *ctx);
+
 /* Number of pairs M = N(N-1)/2 and the bytes of tile-packed Y resident on
  * the device. */
 int mds_problem_size(const mds_ctx *ctx, int64_t *pairs, int64_t *y_bytes);

@@ -72,6 +72,11 @@ SIGNATURES = {
     "mds_leapfrog": (_int, [_vp, _int, _dbl, _vp, _int, _int, _pdbl]),
     "mds_hmc": (_int, [_vp, _int, _int, _dbl, _u64, _vp, _vp, _vp, _vp, ctypes.POINTER(mds_hmc_stats)]),
     "mds_hmc_enqueue": (_int, [_vp, _int, _int, _dbl, _u64]),
+    "mds_set_heldout": (_int, [_vp, _vp, _i64]),
+    "mds_heldout_count": (_int, [_vp, _pi64]),
+    "mds_lpd_accumulate": (_int, [_vp]),
+    "mds_lpd": (_int, [_vp, _pdbl, _pi64]),
+    "mds_lpd_reset": (_int, [_vp]),
     "mds_hmc_collect": (_int, [_vp, _i64, _vp, _vp, _pi64, ctypes.POINTER(mds_hmc_stats)]),
     "mds_problem_size": (_int, [_vp, _pi64, _pi64]),
     "mds_set_strip": (_int, [_vp, _i32]),

@@ -90,6 +90,16 @@ struct mds_ctx {
     void *host_stage = nullptr;       // pinned host memory for the one read-back of a collect
     size_t host_stage_bytes = 0;
 
+    // cross-validation fold (section 2.4): held-out pairs and the lpd-hat accumulators
+    int64_t ho_count = 0;
+    int64_t *ho_off = nullptr;         // their offsets in the tile-packed Y (marked y = -1 there)
+    int2 *ho_pairs = nullptr;          // (i, j), i < j
+    float *ho_y = nullptr;             // their y, set aside
+    unsigned char *tile_ho = nullptr;  // [tiles] 1 where a tile holds a held-out pair
+    double *lse_m = nullptr, *lse_s = nullptr;  // per pair running log-sum-exp of the densities
+    double *lpd_part = nullptr;        // kLpdParts partials + the result
+    int64_t lpd_draws = 0;
+
     // pair-pass timing (mds_set_profiling)
     bool profiling = false;
     std::vector<cudaEvent_t> prof_a, prof_b;
@@ -294,6 +304,7 @@ PairArgs pair_args(const mds_ctx *c) {
     a.row_part = c->row_part;
     a.col_part = c->col_part;
     a.scal_part = c->scal_part;
+    a.tile_ho = c->ho_count > 0 ? c->tile_ho : nullptr;
     a.err = c->err;
     const double s = c->sigma;
     const double inv_sqrt_2pi = 0.39894228040143267794;
@@ -330,6 +341,7 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.mode = mode;
     r.fp64 = c->fp64;
     r.sigma = c->sigma;
+    r.m_pairs = 0.5 * static_cast<double>(c->n) * static_cast<double>(c->n - 1) - static_cast<double>(c->ho_count);
     r.lambda = c->lambda;
     r.eps = eps;
     r.grad = static_cast<double *>(c->grad);
@@ -731,6 +743,33 @@ int hmc_collect(mds_ctx *c, int64_t cap, int32_t *accepted, double *dh, int64_t 
     return err_status(c, h, what);
 }
 
+// Forget the held-out fold: restore the held-out y into the tile-packed Y
+// (unless Y is about to be replaced) and free the fold's buffers.
+int drop_fold(mds_ctx *c, bool restore) {
+    if (c->ho_count > 0) {
+        if (restore) {
+            cudaError_t e = launch_ho_restore(c->y, c->ho_off, c->ho_count, c->ho_y, c->stream);
+            if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "fold restore: %s", cudaGetErrorString(e));
+        }
+        CU(cudaMemsetAsync(c->tile_ho, 0, static_cast<size_t>(c->tiles), c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    void *bufs[] = {c->ho_off, c->ho_pairs, c->ho_y, c->lse_m, c->lse_s};
+    for (void *b : bufs) dev_free(b);
+    c->ho_off = nullptr;
+    c->ho_pairs = nullptr;
+    c->ho_y = nullptr;
+    c->lse_m = nullptr;
+    c->lse_s = nullptr;
+    if (c->ho_count > 0) {
+        c->gen++;
+        c->grad_valid = false;
+    }
+    c->ho_count = 0;
+    c->lpd_draws = 0;
+    return MDS_OK;
+}
+
 }  // namespace
 
 void mds::set_thread_error(const char *fmt, ...) {
@@ -854,6 +893,8 @@ int mds_destroy(mds_ctx *c) {
                     c->bad,      c->e_start,  c->e_end,     c->stage,    c->p_inj,     c->u_inj,
                     c->acc_out,  c->dh_out};
     for (void *b : bufs) dev_free(b);
+    void *ho_bufs[] = {c->ho_off, c->ho_pairs, c->ho_y, c->tile_ho, c->lse_m, c->lse_s, c->lpd_part};
+    for (void *b : ho_bufs) dev_free(b);
     if (c->host_stage) cudaFreeHost(c->host_stage);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -879,6 +920,7 @@ int mds_set_data(mds_ctx *c, const void *y, int dtype, int layout, int64_t ld, i
     if (layout == MDS_Y_FULL && ld < c->n) return fail(c, MDS_ERR_INVALID_ARG, "ld (%lld) < N", (long long)ld);
     c->have_data = false;
     c->grad_valid = false;
+    CHECK(drop_fold(c, false));  // the new Y replaces the marked values
     const bool f64 = dtype == MDS_F64;
     const size_t eb = f64 ? 8 : 4;
     const unsigned long long none = ~0ull;
@@ -1144,6 +1186,104 @@ int mds_hmc_collect(mds_ctx *c, int64_t cap, int32_t *accepted, double *dh, int6
     int st = hmc_collect(c, cap, accepted, dh, &n, stats, "hmc");
     if (count) *count = n;
     return st;
+}
+
+int mds_set_heldout(mds_ctx *c, const int64_t *pairs, int64_t n_pairs) {
+    CHECK(check_ctx(c));
+    if (n_pairs < 0 || (n_pairs > 0 && !pairs)) return fail(c, MDS_ERR_INVALID_ARG, "need n_pairs >= 0 and pairs");
+    if (n_pairs > 0 && !c->have_data) return fail(c, MDS_ERR_STATE, "no data: call mds_set_data first");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    const int64_t n = c->n;
+    std::vector<int64_t> key(static_cast<size_t>(n_pairs));
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j)
+            return fail(c, MDS_ERR_INVALID_ARG, "held-out pair %lld = (%lld, %lld) is not a pair of distinct items",
+                        (long long)k, (long long)i, (long long)j);
+        if (i > j) std::swap(i, j);
+        key[k] = packed_row_start(i, n) + (j - i - 1);
+    }
+    std::sort(key.begin(), key.end());
+    key.erase(std::unique(key.begin(), key.end()), key.end());
+    CHECK(drop_fold(c, true));
+    const int64_t count = static_cast<int64_t>(key.size());
+    if (count == 0) return MDS_OK;
+    std::vector<int64_t> off(count);
+    std::vector<int2> pr(count);
+    for (int64_t k = 0; k < count; ++k) {
+        // invert the packed index row by row (rows are long; a binary search would do for huge N)
+        int64_t lo = 0, hi = n - 2;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (packed_row_start(mid, n) <= key[k]) lo = mid; else hi = mid - 1;
+        }
+        const int64_t i = lo, j = key[k] - packed_row_start(i, n) + i + 1;
+        const int64_t I = i / kTile, J = j / kTile;
+        off[k] = tile_index(I, J, c->nt) * kTileElems + tile_offset(static_cast<int>(i - I * kTile),
+                                                                    static_cast<int>(j - J * kTile));
+        pr[k] = make_int2(static_cast<int>(i), static_cast<int>(j));
+    }
+    if (!c->tile_ho) {
+        CHECK(dev_alloc_t(c, &c->tile_ho, static_cast<size_t>(c->tiles)));
+        CU(cudaMemsetAsync(c->tile_ho, 0, static_cast<size_t>(c->tiles), c->stream));
+    }
+    if (!c->lpd_part) CHECK(dev_alloc_t(c, &c->lpd_part, (kLpdParts + 1) * sizeof(double)));
+    CHECK(dev_alloc_t(c, &c->ho_off, count * sizeof(int64_t)));
+    CHECK(dev_alloc_t(c, &c->ho_pairs, count * sizeof(int2)));
+    CHECK(dev_alloc_t(c, &c->ho_y, count * sizeof(float)));
+    CHECK(dev_alloc_t(c, &c->lse_m, count * sizeof(double)));
+    CHECK(dev_alloc_t(c, &c->lse_s, count * sizeof(double)));
+    CU(cudaMemcpyAsync(c->ho_off, off.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->ho_pairs, pr.data(), count * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = launch_ho_mark(c->y, c->ho_off, count, c->ho_y, c->tile_ho, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "fold mark: %s", cudaGetErrorString(e));
+    CU(cudaStreamSynchronize(c->stream));  // the host vectors above go out of scope
+    c->ho_count = count;
+    c->lpd_draws = 0;
+    c->gen++;
+    c->grad_valid = false;
+    return MDS_OK;
+}
+
+int mds_heldout_count(const mds_ctx *c, int64_t *count) {
+    if (!c || !count) return MDS_ERR_INVALID_ARG;
+    *count = c->ho_count;
+    return MDS_OK;
+}
+
+int mds_lpd_accumulate(mds_ctx *c) {
+    CHECK(check_ctx(c));
+    if (c->ho_count == 0) return fail(c, MDS_ERR_STATE, "no held-out pairs: call mds_set_heldout first");
+    if (!c->have_x) return fail(c, MDS_ERR_STATE, "no locations: call mds_set_locations first");
+    if (!c->have_sigma) return fail(c, MDS_ERR_STATE, "no sigma: call mds_set_sigma first");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    cudaError_t e = launch_lpd_accumulate(c->x, c->fp64, c->d, c->ho_pairs, c->ho_y, c->ho_count, c->sigma,
+                                          c->lpd_draws == 0, c->lse_m, c->lse_s, c->err, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "lpd: %s", cudaGetErrorString(e));
+    CHECK(check_device_err(c, "lpd"));
+    c->lpd_draws++;
+    return MDS_OK;
+}
+
+int mds_lpd(mds_ctx *c, double *lpd, int64_t *draws) {
+    CHECK(check_ctx(c));
+    if (!lpd) return fail(c, MDS_ERR_INVALID_ARG, "lpd is NULL");
+    if (c->lpd_draws == 0) return fail(c, MDS_ERR_STATE, "no draws accumulated (mds_lpd_accumulate)");
+    cudaError_t e = launch_lpd_sum(c->lse_m, c->lse_s, c->ho_count, static_cast<double>(c->lpd_draws),
+                                   c->lpd_part, c->lpd_part + kLpdParts, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "lpd: %s", cudaGetErrorString(e));
+    CU(cudaMemcpyAsync(lpd, c->lpd_part + kLpdParts, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (draws) *draws = c->lpd_draws;
+    return MDS_OK;
+}
+
+int mds_lpd_reset(mds_ctx *c) {
+    CHECK(check_ctx(c));
+    c->lpd_draws = 0;
+    return MDS_OK;
 }
 
 int mds_problem_size(const mds_ctx *c, int64_t *pairs, int64_t *y_bytes) {

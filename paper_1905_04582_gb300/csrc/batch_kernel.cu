@@ -35,14 +35,11 @@ struct BatchLayout {
     __host__ __device__ int bytes() const { return off_bar() + 3 * 8; }
 };
 
-// Row block of one chain into shared memory as [k][row pair] (the layout
-// tile_f32 reads without bank conflicts).
+// Row block of one chain into shared memory ([k][row pair], as stored).
 template <int D>
 __device__ __forceinline__ void copy_xi(const BatchChain &ch, int I, float4 *dst) {
-    for (int idx = threadIdx.x; idx < 32 * D; idx += kPairThreads) {
-        const int k = idx / 32, rp = idx % 32;
-        dst[idx] = ch.xrow[(static_cast<int64_t>(I) * 32 + rp) * D + k];
-    }
+    const float4 *src = ch.xrow + static_cast<int64_t>(I) * 32 * D;
+    for (int idx = threadIdx.x; idx < 32 * D; idx += kPairThreads) dst[idx] = src[idx];
 }
 
 template <int D>

@@ -80,9 +80,12 @@ enum ScalarPart : int {
 // the squared distance is sum_k Dh^2 + Dl (2 Dh + Dl) with Dl = xl_i - xl_j,
 // a small correction computed in FP32 -- which keeps y - delta accurate where
 // y and delta nearly cancel.
-//   xrow[(rp * D + k)] (float4) = { xh_{2rp,k}, xh_{2rp+1,k}, xl_{2rp,k}, xl_{2rp+1,k} }
+//   xrow[(I * D + k) * 32 + r] (float4) = { xh_{i,k}, xh_{i+1,k}, xl_{i,k}, xl_{i+1,k} },
+//        i = 64 I + 2 r (row block I, row pair r: D x 32 float4, contiguous)
 //   xcol[(j  * D + k)] (float4) = { -xh_{j,k}, -xh_{j,k}, -xl_{j,k}, -xl_{j,k} }
-// A tile's column block J is 64 * D float4, contiguous (bulk-copied per warp).
+// A row block is 32 D float4 in the [k][row pair] order the pair kernel
+// reads (one bulk TMA copy per strip); a tile's column block J is 64 D
+// float4, contiguous (bulk-copied per warp).
 // ---------------------------------------------------------------------------
 struct Split {
     float q;       // quantum
@@ -105,6 +108,7 @@ struct PairArgs {
     void *row_part;          // [row slots][64][D] (float / double)
     void *col_part;          // [tiles][64][D]     (float / double)
     void *scal_part;         // [n_strips][kScalarParts] (float / double)
+    const unsigned char *tile_ho;  // [tiles] 1 where a tile holds a held-out pair (y < 0), or null
     unsigned *err;           // device error word (see ErrBits)
     // FP32C constants (sigma folded in on the host), each duplicated {c, c}
     // so that it is a ready operand of the packed f32x2 instructions
@@ -233,6 +237,7 @@ struct ReduceArgs {
     int32_t d;
     int32_t mode;
     bool fp64;                // context precision (x, p, partial types)
+    double m_pairs;           // pairs in the likelihood (M less the held-out ones)
     double sigma;
     double lambda;            // prior precision
     double eps;               // leapfrog step
@@ -335,6 +340,24 @@ cudaError_t launch_resplit(const XState &xs, int64_t n_pad, int d, cudaStream_t 
 cudaError_t launch_xmax(const void *x, bool fp64, int64_t count, unsigned *out, cudaStream_t s);
 // Copy / convert an array between element types (device to device).
 cudaError_t launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t count, cudaStream_t s);
+
+// Cross-validation folds (section 2.4 of the paper).  Held-out pairs are
+// marked in the tile-packed Y with a negative value (the pass masks them) and
+// their y kept aside; tile_ho[t] = 1 for the tiles that hold one.
+cudaError_t launch_ho_mark(float *y, const int64_t *off, int64_t count, float *ho_y, unsigned char *tile_ho,
+                           cudaStream_t s);
+cudaError_t launch_ho_restore(float *y, const int64_t *off, int64_t count, const float *ho_y, cudaStream_t s);
+// Fold the predictive density of every held-out pair at the current state
+// into per-pair running log-sum-exp accumulators (lse_m, lse_s); first = no
+// earlier draw.
+cudaError_t launch_lpd_accumulate(const void *x, bool fp64, int d, const int2 *pairs, const float *ho_y,
+                                  int64_t count, double sigma, bool first, double *lse_m, double *lse_s,
+                                  unsigned *err, cudaStream_t s);
+// lpd-hat = sum over pairs of lse_m + log(lse_s) - log(draws) into *out
+// (fixed-order reduction; part holds kLpdParts doubles).
+constexpr int kLpdParts = 1024;
+cudaError_t launch_lpd_sum(const double *lse_m, const double *lse_s, int64_t count, double draws, double *part,
+                           double *out, cudaStream_t s);
 
 // Set the message mds_last_error(NULL) returns in the calling thread.
 void set_thread_error(const char *fmt, ...);

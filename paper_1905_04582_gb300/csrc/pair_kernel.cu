@@ -72,7 +72,10 @@ __device__ __forceinline__ void issue_stage(unsigned char *dst, uint64_t *bar, c
     tma_load_1d(dst + kWarpTileElems * 4, xsrc, kXj, bar);
 }
 
-template <int D>
+// HELDOUT: the context has a cross-validation fold (tiles flagged in
+// a.tile_ho take the masked path, which then also skips y < 0); a separate
+// instantiation so that the plain pass carries no extra register pressure.
+template <int D, bool HELDOUT>
 __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) pair_f32_kernel(const __grid_constant__ PairArgs a) {
     using L = F32Layout<D>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -115,11 +118,9 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
         for (int s = 0; s < kStages && s < nst; ++s)
             tma_load_1d(ring + s * L::kStageBytes + kWarpTileElems * 4, xsrc0 + s * kTile * D, kXjBytes, &bars[s]);
     }
-    // x_i of the row block: 32 row pairs x D, stored [k][rp] in shared memory
-    for (int idx = tid; idx < 32 * D; idx += kPairThreads) {
-        const int k = idx / 32, rp = idx % 32;
-        xis[idx] = a.xrow[(static_cast<int64_t>(st.I) * 32 + rp) * D + k];
-    }
+    // x_i of the row block: 32 row pairs x D, [k][rp] as stored
+    const float4 *xsrc_row = a.xrow + static_cast<int64_t>(st.I) * 32 * D;
+    for (int idx = tid; idx < 32 * D; idx += kPairThreads) xis[idx] = xsrc_row[idx];
     __syncthreads();
 
     float2 racc[4][D];
@@ -147,15 +148,15 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
         const float4 *ys = reinterpret_cast<const float4 *>(sbuf);
         const float4 *xjs = reinterpret_cast<const float4 *>(sbuf + kWarpTileElems * 4);
         const int J = st.j0 + jt;
-        const bool masked = (J == st.I) || (ragged && J == nt - 1);
+        const bool masked = (J == st.I) || (ragged && J == nt - 1) || (HELDOUT && a.tile_ho[t0 + jt]);
         float2 e2 = f2(0.f, 0.f), mdv = f2(0.f, 0.f), prod = f2(1.f, 1.f);
         float *colp = colp_base + ((t0 + jt) * kTile + warp * kWarpCols) * D;
         {
             const int row_rel = rowbase - J * kTile;
             const int64_t ncv = n - static_cast<int64_t>(J) * kTile;
             if (masked)
-                tile_f32<D, true, PairArgs>(a, ys, xjs, xis, lane, row_rel, warp * kWarpCols, ncv, racc, colp, e2, mdv,
-                                            prod);
+                tile_f32<D, true, PairArgs, HELDOUT>(a, ys, xjs, xis, lane, row_rel, warp * kWarpCols, ncv, racc, colp,
+                                                     e2, mdv, prod);
             else
                 tile_f32<D, false, PairArgs>(a, ys, xjs, xis, lane, row_rel, warp * kWarpCols, ncv, racc, colp, e2, mdv,
                                              prod);
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
     double *colp_base = reinterpret_cast<double *>(a.col_part);
     for (int jt = 0; jt < nst; ++jt) {
         const int J = st.j0 + jt;
-        const bool masked = (J == st.I) || (ragged && J == nt - 1);
+        const bool masked = (J == st.I) || (ragged && J == nt - 1) || (a.tile_ho && a.tile_ho[t0 + jt]);
         const int row_rel = rowbase - J * kTile;
         const int64_t ncv = n - static_cast<int64_t>(J) * kTile;
         const float4 *ys = reinterpret_cast<const float4 *>(a.y + (t0 + jt) * kTileElems + warp * kWarpTileElems);
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
                 for (int h = 0; h < 2; ++h) {
                     const float yf = (c & 1) ? (h ? yv.w : yv.z) : (h ? yv.y : yv.x);
                     const int r = row_rel + 2 * (la + 8 * q) + h;
-                    const bool valid = !masked || (col > r && col < ncv);
+                    const bool valid = !masked || (col > r && col < ncv && yf >= 0.f);  // y < 0: held out
                     double dl[D];
                     double d2 = 0.0;
 #pragma unroll
@@ -336,14 +337,19 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
 template <int D>
 cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s) {
     using L = F32Layout<D>;
-    static bool attr_set = false;  // per instantiation, set once per process
+    static bool attr_set = false;  // per instantiation pair, set once per process
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pair_f32_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+        cudaError_t e = cudaFuncSetAttribute(pair_f32_kernel<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             L::kBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(pair_f32_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (a.n_strips <= 0) return cudaSuccess;
-    const cudaError_t e = launch_pdl(pair_f32_kernel<D>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a);
+    const cudaError_t e =
+        a.tile_ho ? launch_pdl(pair_f32_kernel<D, true>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a)
+                  : launch_pdl(pair_f32_kernel<D, false>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

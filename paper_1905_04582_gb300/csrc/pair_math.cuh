@@ -239,7 +239,7 @@ __device__ __forceinline__ void pair2_f32(const K &a, const float4 (&xi)[D], con
 
 // One tile for this lane: 8 rows x 4 columns, column pairs one at a time;
 // the column sums of each pair are reduced over the 8 row lanes and written.
-template <int D, bool MASKED, typename K>
+template <int D, bool MASKED, typename K, bool HELDOUT = false>
 __device__ __forceinline__ void tile_f32(const K &a, const float4 *ys, const float4 *xjs, const float4 *xis,
                                          int lane, int row_rel, int col_lo, int64_t ncol_valid,
                                          float2 (&racc)[4][D], float *colp, float2 &e2, float2 &md, float2 &prod) {
@@ -266,16 +266,20 @@ __device__ __forceinline__ void tile_f32(const K &a, const float4 *ys, const flo
             for (int k = 0; k < D; ++k) xi[k] = xis[k * 32 + la + 8 * q];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
+                const float2 y2 = e == 0 ? f2(yv.x, yv.y) : f2(yv.z, yv.w);
                 float2 vm = f2(1.f, 1.f);
                 if (MASKED) {
                     // rows r, r+1 of the row pair, column c (tile-relative,
-                    // rows shifted so that the diagonal test is c > r)
+                    // rows shifted so that the diagonal test is c > r); with
+                    // a cross-validation fold, a held-out pair carries y < 0
                     const int r = row_rel + 2 * (la + 8 * q);
                     const int c = col_lo + 4 * lb + 2 * cp + e;
                     const bool cv = c < ncol_valid;
-                    vm = f2((cv && c > r) ? 1.f : 0.f, (cv && c > r + 1) ? 1.f : 0.f);
+                    if (HELDOUT)
+                        vm = f2((cv && c > r && y2.x >= 0.f) ? 1.f : 0.f, (cv && c > r + 1 && y2.y >= 0.f) ? 1.f : 0.f);
+                    else
+                        vm = f2((cv && c > r) ? 1.f : 0.f, (cv && c > r + 1) ? 1.f : 0.f);
                 }
-                const float2 y2 = e == 0 ? f2(yv.x, yv.y) : f2(yv.z, yv.w);
                 pair2_f32<D, MASKED, K>(a, xi, xj[e], y2, vm, racc[q], cacc[e], e2, md, prod);
             }
         }

@@ -111,7 +111,7 @@ __device__ __forceinline__ void write_split(const XState &xs, int64_t k, int d, 
     const Split sp = *xs.split;
     const float h = __fsub_rn(__fadd_rn(v, sp.magic), sp.magic);  // nearest multiple of q
     const float l = __fsub_rn(v, h);                               // exact
-    float *xr = reinterpret_cast<float *>(xs.xrow + ((k >> 1) * d + kk));
+    float *xr = reinterpret_cast<float *>(xs.xrow + (((k >> 6) * d + kk) * 32 + ((k >> 1) & 31)));
     xr[k & 1] = h;
     xr[2 + (k & 1)] = l;
     xs.xcol[k * d + kk] = make_float4(-h, -h, -l, -l);
@@ -192,7 +192,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         }
         if (tid == 0) {
             const double sg = a.sigma;
-            const double m = 0.5 * static_cast<double>(a.n) * static_cast<double>(a.n - 1);
+            const double m = a.m_pairs;
             const double sum_logphi = kF32 ? -kLn2 * dlp : dlp;      // FP32C: sum log2(1/Phi)
             const double sum_mdelta = kF32 ? dmd / kSqrt2Pi : dmd;   // FP32C: sqrt(2 pi) (phi/Phi) delta
             const double sum_r = de2 / (2.0 * sg * sg) + sum_logphi;

@@ -212,6 +212,35 @@ class MDS:
         return acc.astype(bool), dh, {"iterations": stats.iterations, "accepted": stats.accepted,
                                       "last_dh": stats.last_dh, "last_loglik": stats.last_loglik}
 
+    # -- cross-validation (section 2.4)
+    def set_heldout(self, pairs):
+        """Hold out the pairs (K x 2, any order within a pair); None or an
+        empty list restores every pair."""
+        if pairs is None or len(pairs) == 0:
+            self._check(self._lib.mds_set_heldout(self._h, None, 0))
+            return
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        self._check(self._lib.mds_set_heldout(self._h, pr.ctypes.data_as(ctypes.c_void_p), pr.shape[0]))
+
+    def heldout_count(self):
+        c = ctypes.c_int64()
+        self._check(self._lib.mds_heldout_count(self._h, ctypes.byref(c)))
+        return c.value
+
+    def lpd_accumulate(self):
+        """Score the current (X, sigma) as one posterior draw."""
+        self._check(self._lib.mds_lpd_accumulate(self._h))
+
+    def lpd(self):
+        """(lpd-hat, draws) over the draws accumulated so far."""
+        v = ctypes.c_double()
+        s = ctypes.c_int64()
+        self._check(self._lib.mds_lpd(self._h, ctypes.byref(v), ctypes.byref(s)))
+        return v.value, s.value
+
+    def lpd_reset(self):
+        self._check(self._lib.mds_lpd_reset(self._h))
+
     def hmc_enqueue(self, n_iter, n_steps, eps, seed=0):
         """Queue n_iter HMC iterations on the context's stream; no waiting."""
         self._check(self._lib.mds_hmc_enqueue(self._h, int(n_iter), int(n_steps), float(eps),
