@@ -57,11 +57,16 @@ def _load():
             lib.mdso_hmc_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _int,
                                           _vp, _vp, _int, _vp, _vp]
             lib.mdso_lpd.argtypes = [_i64, _int, _vp, _i64, _vp, _int, _vp, _vp, _vp]
+            lib.mdso_sigma_mh.argtypes = [_i64, _int, _vp, _vp, _vp, _vp, _dbl, _int, _dbl, _dbl, _dbl, _vp,
+                                          _vp, _int, _vp]
+            lib.mdso_sigma_draws.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             _vp, _vp]
+            lib.mdso_sigma_draws.restype = None
             lib.mdso_philox4x32_10.argtypes = [_vp, _vp, _vp]
             lib.mdso_draw_momentum.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.c_uint32, _i64, _vp, _vp]
             for f in ("mdso_loglik_kept", "mdso_gradient_rows_kept", "mdso_dsigma_kept",
-                      "mdso_leapfrog_kept", "mdso_hmc_kept", "mdso_lpd"):
+                      "mdso_leapfrog_kept", "mdso_hmc_kept", "mdso_lpd", "mdso_sigma_mh"):
                 getattr(lib, f).restype = _int
             lib.mdso_philox4x32_10.restype = None
             lib.mdso_draw_momentum.restype = None
@@ -230,3 +235,31 @@ def draw_momentum(seed, chain, it, count):
     _load().mdso_draw_momentum(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, chain, it, count,
                                _ptr(p), _ptr(u))
     return p, float(u[0])
+
+
+def sigma_mh(yp, x, sigma, step, shape, rate, z_all, u_all, w=1.0, keep=None, nthreads=1):
+    """Random-walk Metropolis updates of log sigma given X with the prior
+    sigma^-2 ~ Gamma(shape, rate) (w = 0: prior only).  Returns
+    (sigma, accepted[n_iter])."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, d = x.shape
+    k, kp = _keep_ptr(keep, n)
+    z = np.ascontiguousarray(z_all, dtype=np.float64)
+    u = np.ascontiguousarray(u_all, dtype=np.float64)
+    if z.shape != u.shape or z.ndim != 1:
+        raise ValueError("z_all and u_all must be vectors of the same length")
+    ypp = None if yp is None else np.ascontiguousarray(yp, dtype=np.float32)
+    s = np.array([float(sigma)])
+    acc = np.zeros(len(z), dtype=np.int32)
+    _check(_load().mdso_sigma_mh(n, d, None if ypp is None else _ptr(ypp), kp, _ptr(x), _ptr(s), float(w), len(z),
+                                 float(step), float(shape), float(rate), _ptr(z), _ptr(u), int(nthreads), _ptr(acc)),
+           "sigma_mh")
+    return float(s[0]), acc.astype(bool)
+
+
+def sigma_draws(seed, chain, it):
+    """(z, u) of sigma update `it` from the Philox stream keyed by `seed`."""
+    z = np.zeros(1)
+    u = np.zeros(1)
+    _load().mdso_sigma_draws(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, chain, it, _ptr(z), _ptr(u))
+    return float(z[0]), float(u[0])

@@ -19,6 +19,11 @@
  *   delta_ij = ||x_i - x_j||, sigma > 0, z_ij = delta_ij / sigma,
  *   M = N (N - 1) / 2 pairs.
  *
+ * The cross-validation functions (training likelihood of a fold, lpd-hat)
+ * are pinned in tests/test_oracle_cv_pins.py and the sigma update in
+ * tests/test_oracle_sigma_pins.py; planted mistakes in
+ * tests/test_oracle_mutations.py.
+ *
  * Pinned by (tests/test_oracle_pins.py): the N = 2 closed form at 50 digits,
  * scipy's truncated-normal log density summed over pairs (Eq. 1 model),
  * central finite differences of the oracle's own log-likelihood in X and in
@@ -48,6 +53,10 @@
  *     multiplies each term by the posterior density of the draw; with draws
  *     taken from that posterior the plain average is the standard estimate,
  *     which is the one computed here.
+ *   - sigma update: the paper takes "Gibbs steps" for sigma^2 with the prior
+ *     sigma^-2 ~ Gamma(s0, r0) (shape, rate), but the Phi term of Eq. (2)
+ *     makes that full conditional non-standard, so the update here is a
+ *     random-walk Metropolis step on log sigma (prior and Jacobian included).
  */
 #include <math.h>
 #include <stddef.h>
@@ -500,4 +509,69 @@ void mdso_draw_momentum(uint32_t seed_lo, uint32_t seed_hi, uint32_t chain, uint
         mdso_philox4x32_10(ctr, key, o);
         *u = bits_to_open_unit(o[0]);
     }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Update of sigma given X (the sigma^2 step of the paper's Gibbs scheme,  */
+/* section 3; prior sigma^-2 ~ Gamma(s0, r0), section 2.2).  The Phi term   */
+/* of Eq. (2) makes the full conditional non-standard, so the update is a   */
+/* random-walk Metropolis step on tau = log sigma.                          */
+/* ---------------------------------------------------------------------- */
+
+/* Draws of sigma update `iter`: counter (0, iter, chain, 2); words (0, 1)
+ * give z = sqrt(-2 ln u1) cos(2 pi u2), word 2 gives the uniform. */
+void mdso_sigma_draws(uint32_t seed_lo, uint32_t seed_hi, uint32_t chain, uint32_t iter, double *z, double *u) {
+    uint32_t key[2] = {seed_lo, seed_hi};
+    uint32_t ctr[4] = {0u, iter, chain, 2u};
+    uint32_t o[4];
+    mdso_philox4x32_10(ctr, key, o);
+    double u1 = bits_to_open_unit(o[0]);
+    double u2 = bits_to_open_unit(o[1]);
+    *z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    *u = bits_to_open_unit(o[2]);
+}
+
+/* log density of tau = log sigma under the prior sigma^-2 ~ Gamma(s0, r0)
+ * (shape s0, rate r0): with lambda = sigma^-2 = exp(-2 tau) and
+ * |d lambda / d tau| = 2 lambda,
+ *   log p(tau) = (s0 - 1) log lambda - r0 lambda + log(2 lambda) + const
+ *              = s0 log lambda - r0 lambda + const. */
+static double log_prior_tau(double sigma, double s0, double r0) {
+    double lambda = 1.0 / (sigma * sigma);
+    return s0 * log(lambda) - r0 * lambda;
+}
+
+/* n_iter updates of *sigma: tau' = tau + step z_t, accepted iff
+ *   log u_t < [w L(X, sigma') + log p(tau')] - [w L(X, sigma) + log p(tau)]
+ * (L over the kept pairs; w in {0, 1}, w = 0 samples the prior).  z_all and
+ * u_all hold the draws; accepted[t] (optional) receives the decisions. */
+int mdso_sigma_mh(int64_t n, int d, const float *yp, const unsigned char *keep, const double *x, double *sigma,
+                  double w, int n_iter, double step, double s0, double r0, const double *z_all,
+                  const double *u_all, int nthreads, int *accepted) {
+    if (n < 2 || d < 1 || n_iter < 0 || !x || !sigma || !(*sigma > 0.0) || !z_all || !u_all ||
+        !(s0 > 0.0) || !(r0 > 0.0) || (w != 0.0 && !yp))
+        return MDSO_BAD_ARG;
+    double s = *sigma, ll = 0.0;
+    if (w != 0.0) {
+        int st = mdso_loglik_kept(n, d, yp, keep, x, s, nthreads, NULL, &ll);
+        if (st) return st;
+    }
+    double cur = w * ll + log_prior_tau(s, s0, r0);
+    for (int t = 0; t < n_iter; ++t) {
+        double s1 = exp(log(s) + step * z_all[t]);
+        double ll1 = 0.0;
+        if (w != 0.0) {
+            int st = mdso_loglik_kept(n, d, yp, keep, x, s1, nthreads, NULL, &ll1);
+            if (st) return st;
+        }
+        double prop = w * ll1 + log_prior_tau(s1, s0, r0);
+        int acc = log(u_all[t]) < prop - cur;
+        if (acc) {
+            s = s1;
+            cur = prop;
+        }
+        if (accepted) accepted[t] = acc;
+    }
+    *sigma = s;
+    return MDSO_OK;
 }

@@ -45,6 +45,9 @@ MUTANTS = {
     "lpd_drop_log_phi": ("- e * e / (2.0 * sigma * sigma) - log_std_normal_cdf(delta / sigma);",
                          "- e * e / (2.0 * sigma * sigma);"),
     "lpd_no_log_S": ("nsum_add(&tot, m + log(e) - log((double)S));", "nsum_add(&tot, m + log(e));"),
+    "sigma_prior_no_jacobian": ("return s0 * log(lambda) - r0 * lambda;", "return (s0 - 1.0) * log(lambda) - r0 * lambda;"),
+    "sigma_prior_rate_as_scale": ("return s0 * log(lambda) - r0 * lambda;", "return s0 * log(lambda) - lambda / r0;"),
+    "sigma_step_on_sigma": ("double s1 = exp(log(s) + step * z_all[t]);", "double s1 = s + step * z_all[t];"),
 }
 
 _i64, _int, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -65,6 +68,7 @@ def _build(tmp_path, name, src_text):
     lib.mdso_loglik_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _int, _vp, _vp]
     lib.mdso_gradient_rows_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp, _vp]
     lib.mdso_lpd.argtypes = [_i64, _int, _vp, _i64, _vp, _int, _vp, _vp, _vp]
+    lib.mdso_sigma_mh.argtypes = [_i64, _int, _vp, _vp, _vp, _vp, _dbl, _int, _dbl, _dbl, _dbl, _vp, _vp, _int, _vp]
     return lib
 
 
@@ -138,6 +142,17 @@ def _pins_hold(lib):
         dd = np.linalg.norm(xs[t][pr[:, 0]] - xs[t][pr[:, 1]], axis=1)
         dens[t] = stats.truncnorm.pdf(yy, -dd / sg[t], np.inf, loc=dd, scale=sg[t])
     if not math.isclose(out[0], np.log(dens.mean(axis=0)).sum(), rel_tol=1e-12):
+        return False
+    # the sigma update with the likelihood off samples sigma^-2 ~ Gamma(3, 2)
+    rs = np.random.default_rng(5)
+    zz, uu = rs.standard_normal(60000), rs.random(60000)
+    sg = np.array([0.7])
+    lam = []
+    for b in range(0, 60000, 20):
+        lib.mdso_sigma_mh(2, 1, None, None, _p(np.zeros((2, 1))), _p(sg), 0.0, 20, 0.8, 3.0, 2.0,
+                          _p(zz[b:b + 20]), _p(uu[b:b + 20]), 1, None)
+        lam.append(1.0 / sg[0] ** 2)
+    if stats.kstest(lam[100:], stats.gamma(3.0, scale=0.5).cdf).pvalue < 1e-4:
         return False
     # harmonic oscillator closed form
     lam, eps, steps = 1.0, 0.1, 5
