@@ -192,6 +192,27 @@ int mds_hmc_enqueue(mds_ctx *ctx, int n_iter, int n_steps, double eps, uint64_t 
 int mds_hmc_collect(mds_ctx *ctx, int64_t cap, int32_t *accepted, double *dh, int64_t *count,
                     mds_hmc_stats *stats);
 
+/* The current sigma (set by mds_set_sigma or moved by mds_sigma_mh). */
+int mds_get_sigma(const mds_ctx *ctx, double *sigma);
+
+/* Update sigma given X: the sigma^2 step of the paper's Gibbs scheme
+ * (section 3) with the prior sigma^-2 ~ Gamma(shape, rate) (section 2.2).
+ * The Phi term of Eq. (2) makes that full conditional non-standard, so each
+ * of the n_iter updates is a random-walk Metropolis step on tau = log sigma:
+ *   tau' = tau + step z,  accepted iff  log u < P(tau') - P(tau),
+ *   P(tau) = L(X, sigma) + shape log(sigma^-2) - rate sigma^-2
+ * (L of Eq. (2) over the training pairs; the Jacobian of the log scale is
+ * included).  Each proposal costs one fused pass.  z_all / u_all (host,
+ * n_iter each, u in (0,1)) inject the draws; otherwise update t of the
+ * context uses the Philox4x32-10 block at counter (0, t, 0, 2) keyed by
+ * `seed` (z by Box-Muller from words 0 and 1, u from word 2), t counting
+ * every update drawn so far.  accepted (optional, n_iter int32, host).
+ * Proposals outside the FP32C range of sigma are rejected.  Synchronises.
+ * Errors: INVALID_ARG, STATE (no data/locations/sigma; queued HMC
+ * iterations), NONFINITE, CUDA. */
+int mds_sigma_mh(mds_ctx *ctx, int n_iter, double step, double shape, double rate, uint64_t seed,
+                 const double *z_all, const double *u_all, int32_t *accepted);
+
 /* ------------------------------------------------------------------------
  * Cross-validation (section 2.4 "Model selection" of arXiv:1905.04582).  A
  * fold holds out a set of observations y_ij; the model is trained on the rest

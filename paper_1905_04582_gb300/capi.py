@@ -72,6 +72,8 @@ SIGNATURES = {
     "mds_leapfrog": (_int, [_vp, _int, _dbl, _vp, _int, _int, _pdbl]),
     "mds_hmc": (_int, [_vp, _int, _int, _dbl, _u64, _vp, _vp, _vp, _vp, ctypes.POINTER(mds_hmc_stats)]),
     "mds_hmc_enqueue": (_int, [_vp, _int, _int, _dbl, _u64]),
+    "mds_get_sigma": (_int, [_vp, _pdbl]),
+    "mds_sigma_mh": (_int, [_vp, _int, _dbl, _dbl, _dbl, _u64, _vp, _vp, _vp]),
     "mds_set_heldout": (_int, [_vp, _vp, _i64]),
     "mds_heldout_count": (_int, [_vp, _pi64]),
     "mds_lpd_accumulate": (_int, [_vp]),

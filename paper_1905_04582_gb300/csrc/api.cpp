@@ -100,6 +100,11 @@ struct mds_ctx {
     double *lpd_part = nullptr;        // kLpdParts partials + the result
     int64_t lpd_draws = 0;
 
+    // sigma updates (random walk on log sigma)
+    int64_t sigma_iter = 0;            // updates drawn so far (Philox counter)
+    double *sigma_draws = nullptr;     // device z, u of one call
+    int64_t sigma_draws_cap = 0;
+
     // pair-pass timing (mds_set_profiling)
     bool profiling = false;
     std::vector<cudaEvent_t> prof_a, prof_b;
@@ -659,10 +664,6 @@ int hmc_enqueue(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, 
     // one HMC iteration as a CUDA graph, captured once per configuration
     const auto key = std::make_tuple(c->gen, n_steps, eps, inj ? 2 : 1, c->profiling ? 1 : 0, seed, c->strip);
     if (!c->graph || key != c->graph_key) {
-        if (c->graph) {
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
-        }
         cudaGraph_t g = nullptr;
         CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         c->prof_used = 0;
@@ -675,9 +676,22 @@ int hmc_enqueue(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, 
             return st;
         }
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&c->graph, g, 0);
+        if (c->graph) {
+            // same launches with new arguments (sigma, eps, buffers): update the
+            // instantiated graph in place; otherwise instantiate afresh
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(c->graph, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+            }
+        }
+        if (!c->graph) e = cudaGraphInstantiate(&c->graph, g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            return fail(c, MDS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
         c->graph_key = key;
     }
     for (int t = 0; t < n_iter; ++t) {
@@ -893,7 +907,7 @@ int mds_destroy(mds_ctx *c) {
                     c->bad,      c->e_start,  c->e_end,     c->stage,    c->p_inj,     c->u_inj,
                     c->acc_out,  c->dh_out};
     for (void *b : bufs) dev_free(b);
-    void *ho_bufs[] = {c->ho_off, c->ho_pairs, c->ho_y, c->tile_ho, c->lse_m, c->lse_s, c->lpd_part};
+    void *ho_bufs[] = {c->ho_off, c->ho_pairs, c->ho_y, c->tile_ho, c->lse_m, c->lse_s, c->lpd_part, c->sigma_draws};
     for (void *b : ho_bufs) dev_free(b);
     if (c->host_stage) cudaFreeHost(c->host_stage);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1283,6 +1297,91 @@ int mds_lpd(mds_ctx *c, double *lpd, int64_t *draws) {
 int mds_lpd_reset(mds_ctx *c) {
     CHECK(check_ctx(c));
     c->lpd_draws = 0;
+    return MDS_OK;
+}
+
+int mds_get_sigma(const mds_ctx *c, double *sigma) {
+    if (!c || !sigma) return MDS_ERR_INVALID_ARG;
+    *sigma = c->sigma;
+    return MDS_OK;
+}
+
+int mds_sigma_mh(mds_ctx *c, int n_iter, double step, double shape, double rate, uint64_t seed, const double *z_all,
+                 const double *u_all, int32_t *accepted) {
+    CHECK(check_ctx(c));
+    if (n_iter < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_iter must be >= 0");
+    if (!(step >= 0.0) || !std::isfinite(step) || !(shape > 0.0) || !(rate > 0.0) || !std::isfinite(shape) ||
+        !std::isfinite(rate))
+        return fail(c, MDS_ERR_INVALID_ARG, "need step >= 0 and a Gamma prior with shape > 0 and rate > 0");
+    if ((z_all == nullptr) != (u_all == nullptr))
+        return fail(c, MDS_ERR_INVALID_ARG, "z_all and u_all must be given together");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    CHECK(ready(c));
+    if (n_iter == 0) return MDS_OK;
+    std::vector<double> z(n_iter), u(n_iter);
+    if (z_all) {
+        for (int t = 0; t < n_iter; ++t) {
+            if (!(u_all[t] > 0.0 && u_all[t] < 1.0) || !std::isfinite(z_all[t]))
+                return fail(c, MDS_ERR_INVALID_ARG, "draw %d: need a finite z and u in (0,1)", t);
+            z[t] = z_all[t];
+            u[t] = u_all[t];
+        }
+    } else {
+        if (n_iter > c->sigma_draws_cap) {
+            dev_free(c->sigma_draws);
+            c->sigma_draws = nullptr;
+            CHECK(dev_alloc_t(c, &c->sigma_draws, 2 * static_cast<size_t>(n_iter) * sizeof(double)));
+            c->sigma_draws_cap = n_iter;
+        }
+        cudaError_t e = launch_sigma_draws(seed, 0u, c->sigma_iter, n_iter, c->sigma_draws,
+                                           c->sigma_draws + n_iter, c->stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "sigma draws: %s", cudaGetErrorString(e));
+        CU(cudaMemcpyAsync(z.data(), c->sigma_draws, n_iter * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaMemcpyAsync(u.data(), c->sigma_draws + n_iter, n_iter * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        c->sigma_iter += n_iter;
+    }
+    // log posterior of tau = log sigma: L(X, sigma) + s0 log(sigma^-2) - r0 sigma^-2
+    auto log_post = [&](double ll, double sg) {
+        const double lam = 1.0 / (sg * sg);
+        return ll + shape * std::log(lam) - rate * lam;
+    };
+    auto eval_ll = [&](double *ll) -> int {
+        CHECK(evaluate(c));
+        double s[kScalars];
+        CU(cudaMemcpyAsync(s, c->scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        *ll = s[kLogLik];
+        return MDS_OK;
+    };
+    double ll = 0.0;
+    CHECK(eval_ll(&ll));
+    double cur = log_post(ll, c->sigma);
+    for (int t = 0; t < n_iter; ++t) {
+        const double s0 = c->sigma;
+        const double s1 = std::exp(std::log(s0) + step * z[t]);
+        if (!(s1 > 0.0) || !std::isfinite(s1) || (!c->fp64 && (s1 < 1e-6 || s1 > 1e6))) {
+            if (accepted) accepted[t] = 0;  // outside the supported range: rejected
+            continue;
+        }
+        c->sigma = s1;
+        c->gen++;
+        c->grad_valid = false;
+        double ll1 = 0.0;
+        CHECK(eval_ll(&ll1));
+        const double prop = log_post(ll1, s1);
+        const int acc = std::log(u[t]) < prop - cur;
+        if (acc) {
+            cur = prop;
+        } else {
+            c->sigma = s0;
+            c->gen++;
+            c->grad_valid = false;  // the cached pass is at the rejected sigma
+        }
+        if (accepted) accepted[t] = acc;
+    }
     return MDS_OK;
 }
 

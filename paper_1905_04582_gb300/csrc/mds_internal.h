@@ -304,6 +304,9 @@ struct AcceptArgs {
     unsigned *err;
 };
 cudaError_t launch_traj_end(const AcceptArgs &a, cudaStream_t s);
+// z (standard normal) and u (uniform) of sigma updates iter0 .. iter0 + n - 1.
+cudaError_t launch_sigma_draws(uint64_t seed, uint32_t chain, int64_t iter0, int n, double *z, double *u,
+                               cudaStream_t s);
 
 // Batched launches (one per step for all problems): per-problem argument
 // tables in device memory.  jobs[k] = (problem, column block J or -1).

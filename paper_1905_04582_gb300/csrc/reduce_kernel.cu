@@ -624,6 +624,20 @@ __global__ void __launch_bounds__(kTrajThreads) traj_end_batch_kernel(const Acce
     traj_end_body<float, D>(cfg[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
+// Draws of the sigma update (section 3's sigma^2 step, a random walk on
+// log sigma): update t uses the Philox4x32-10 block at counter
+// (0, t, chain, 2): z from words 0 and 1 (Box-Muller), the uniform from word 2.
+__global__ void sigma_draws_kernel(uint64_t seed, uint32_t chain, int64_t iter0, int n, double *z, double *u) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t c[4] = {0u, static_cast<uint32_t>(iter0 + t), chain, 2u};
+    philox10(c, seed);
+    double z0, z1;
+    box_muller(c[0], c[1], z0, z1);
+    z[t] = z0;
+    u[t] = open_unit(c[2]);
+}
+
 #define MDS_SWITCH_D(KERNEL, T, GRID, BLOCK, STREAM, ARGS)                        \
     switch ((ARGS).d) {                                                          \
         case 1: KERNEL<T, 1><<<GRID, BLOCK, 0, STREAM>>>(ARGS); break;           \
@@ -830,6 +844,13 @@ int traj_start_grid(int64_t n, int d) { return static_cast<int>(((n * d + 3) / 4
 cudaError_t launch_traj_start_batch(const TrajArgs *cfg, int n_chains, int max_grid, int d, cudaStream_t s) {
     const dim3 grid(max_grid, n_chains);
     MDS_SWITCH_DB(traj_start_batch_kernel, grid, kTrajThreads, s, d, cfg)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_draws(uint64_t seed, uint32_t chain, int64_t iter0, int n, double *z, double *u,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    sigma_draws_kernel<<<(n + 127) / 128, 128, 0, s>>>(seed, chain, iter0, n, z, u);
     return cudaGetLastError();
 }
 

@@ -212,6 +212,28 @@ class MDS:
         return acc.astype(bool), dh, {"iterations": stats.iterations, "accepted": stats.accepted,
                                       "last_dh": stats.last_dh, "last_loglik": stats.last_loglik}
 
+    # -- sigma update (random walk on log sigma, Gamma prior on sigma^-2)
+    def get_sigma(self):
+        v = ctypes.c_double()
+        self._check(self._lib.mds_get_sigma(self._h, ctypes.byref(v)))
+        return v.value
+
+    def sigma_mh(self, n_iter, step, shape, rate, seed=0, z_all=None, u_all=None):
+        """n_iter Metropolis updates of sigma given X; returns (accepted, sigma)."""
+        acc = np.zeros(n_iter, dtype=np.int32)
+        zz = uu = None
+        if z_all is not None:
+            zz = np.ascontiguousarray(z_all, dtype=np.float64)
+            uu = np.ascontiguousarray(u_all, dtype=np.float64)
+            if zz.shape != (n_iter,) or uu.shape != (n_iter,):
+                raise ValueError("z_all and u_all must hold n_iter values each")
+        self._check(self._lib.mds_sigma_mh(self._h, int(n_iter), float(step), float(shape), float(rate),
+                                           int(seed) & (2**64 - 1),
+                                           None if zz is None else zz.ctypes.data_as(ctypes.c_void_p),
+                                           None if uu is None else uu.ctypes.data_as(ctypes.c_void_p),
+                                           acc.ctypes.data_as(ctypes.c_void_p)))
+        return acc.astype(bool), self.get_sigma()
+
     # -- cross-validation (section 2.4)
     def set_heldout(self, pairs):
         """Hold out the pairs (K x 2, any order within a pair); None or an
