@@ -177,6 +177,30 @@ def barrier(world):
         dist.barrier()
 
 
+def pass_distribution(model, wl, flush_l2, stream, n_warm=100, n_cold=20):
+    """Pair-kernel launch times (CUDA events around the launch): p10 / p50 /
+    p90 over n_warm back-to-back evaluations (Y L2-resident) and over n_cold
+    evaluations each after an L2 flush (Y from HBM)."""
+    import torch
+    x_dev = torch.from_numpy(wl.x_eval.copy()).to(device=torch.device("cuda", torch.cuda.current_device()))
+
+    def run(n, cold):
+        out = []
+        for _ in range(n):
+            if cold:
+                flush_l2()
+            model.set_profiling(True)  # restarts the launch timer
+            model.set_locations(x_dev)  # invalidates the cached pass (Y untouched)
+            model.log_likelihood()
+            out.append(model.pass_time()[1])
+        model.set_profiling(False)
+        q = np.quantile(np.array(out) * 1e3, [0.1, 0.5, 0.9])
+        return {"p10": float(q[0]), "p50": float(q[1]), "p90": float(q[2]), "n": n}
+
+    torch.cuda.synchronize()
+    return {"warm": run(n_warm, False), "cold": run(n_cold, True)}
+
+
 def cpu_oracle_rate(wl, evals, nthreads=1):
     """Oracle (as it stands) likelihood + gradient on the host: pairs/s."""
     import oracle
@@ -320,6 +344,7 @@ def run_gpu(args):
         m64.set_sigma(wl.sigma)
         ms64 = m64.time_pass(5)
     ms32 = model.time_pass(20)
+    pass_dist = pass_distribution(model, wl, flush_l2, stream)
 
     # end to end through the C ABI with host buffers: X in, one HMC
     # iteration, X and the statistics out
@@ -342,6 +367,10 @@ def run_gpu(args):
         rate, secs = cpu_oracle_rate(wl, args.cpu_evals)
         cpu = {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_evals} serial evaluations of L and dL/dX at N=5392 ({secs:.1f} s)"}
+        ncores = os.cpu_count() or 1
+        rate_mt, secs_mt = cpu_oracle_rate(wl, args.cpu_evals, nthreads=ncores)
+        cpu["all_cores"] = {"value": rate_mt, "unit": "pairs/s", "cores": ncores, "kind": "oracle (OpenMP rows)",
+                            "sample": f"{args.cpu_evals} evaluations of L and dL/dX at N=5392 ({secs_mt:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -358,7 +387,8 @@ def run_gpu(args):
             "accept_rate": acc_total / args.steps,
             "hbm_fraction_of_pairs_rate": value * 4.0 / 1e9 / hbm_peak,
             "pass_alone": {"fp32c_ms": ms32, "fp64_ms": ms64, "fp32c_pairs_per_s": m_pairs / (ms32 / 1e3),
-                           "fp64_pairs_per_s": m_pairs / (ms64 / 1e3), "speedup_vs_fp64": ms64 / ms32},
+                           "fp64_pairs_per_s": m_pairs / (ms64 / 1e3), "speedup_vs_fp64": ms64 / ms32,
+                           "pair_kernel_warm_us": pass_dist["warm"], "pair_kernel_cold_us": pass_dist["cold"]},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFP32-op/s",
                          "frac": alu_achieved / alu_peak, "traffic": traffic,
                          "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
@@ -409,6 +439,89 @@ def run_pass_only(args):
     return 0
 
 
+def _alu_peak_tflops():
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def run_sweep(args):
+    """The scale sweep (N = 20000, 50000; D = 2, 6; FP32C, autotuned strip):
+    one JSON line per size with the pass time and its HBM and ALU fractions,
+    Y (0.8 / 5.0 GB) far larger than L2, so every pass streams it from HBM."""
+    import torch
+    from paper_1905_04582_gb300 import build as B
+    from paper_1905_04582_gb300 import workloads as W
+    from paper_1905_04582_gb300.mds import MDS
+    B.build()
+    torch.cuda.set_device(0)
+    hbm_peak, peak_kind = load_peaks()
+    alu_peak = _alu_peak_tflops()
+    for n, d in ((20000, 2), (20000, 6), (50000, 2), (50000, 6)):
+        wl = W.scale_sweep(n, d)
+        with MDS(wl.n, wl.d, "fp32c") as m:
+            m.set_data(wl.y_packed)
+            m.set_locations(wl.x_eval)
+            m.set_sigma(wl.sigma)
+            ms = m.time_pass(args.reps)
+            strip = m.get_strip()
+        line = {"sweep": True, "workload": wl.name, "n": n, "d": d, "pairs": wl.m, "strip": strip,
+                "ms_per_pass": ms, "pairs_per_s": wl.m / (ms / 1e3),
+                "hbm": {"achieved_gbs": 4.0 * wl.m / (ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                        "frac": 4.0 * wl.m / (ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind},
+                "alu": {"achieved_tflops": wl.m * fp32_ops_per_pair(d) / (ms / 1e3) / 1e12, "peak_tflops": alu_peak,
+                        "frac": wl.m * fp32_ops_per_pair(d) / (ms / 1e3) / 1e12 / alu_peak}}
+        if n == 20000 and d == 2:
+            with MDS(wl.n, wl.d, "fp64") as m64:
+                m64.set_data(wl.y_packed)
+                m64.set_locations(wl.x_eval)
+                m64.set_sigma(wl.sigma)
+                ms64 = m64.time_pass(2)
+            line["fp64_ms_per_pass"] = ms64
+            line["speedup_vs_fp64"] = ms64 / ms
+        print(json.dumps(line), flush=True)
+        del wl
+    return 0
+
+
+def run_batch(args):
+    """Batched datasets x chains (N = 1600, 1500, 1300, 992; 8 chains each):
+    pair evaluations per second of one batched pass for all 32 chains, and
+    HMC leapfrog steps per second over all chains."""
+    import torch
+    from paper_1905_04582_gb300 import build as B
+    from paper_1905_04582_gb300 import workloads as W
+    from paper_1905_04582_gb300.mds import Batch
+    B.build()
+    torch.cuda.set_device(0)
+    ds = W.batch_datasets()
+    chains = 8
+    b = Batch([w.n for w in ds], 2, [chains] * len(ds))
+    for k, w in enumerate(ds):
+        b.set_data(k, w.y_packed)
+        b.set_sigma(k, w.sigma)
+        for j in range(chains):
+            b.set_locations(k, j, w.x_eval)
+    ms = b.time_pass(args.reps)
+    evals = sum(w.m for w in ds) * chains
+    b.hmc(2, N_LEAPFROG, [5e-4] * len(ds), seed=1)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    acc, dh = b.hmc(args.steps, N_LEAPFROG, [5e-4] * len(ds), seed=2)
+    wall = time.perf_counter() - t0
+    alu_peak = _alu_peak_tflops()
+    print(json.dumps({"batch": True, "datasets": [w.n for w in ds], "chains_per_dataset": chains,
+                      "strip": b.get_strip(), "ms_per_pass": ms, "pair_evals_per_pass": evals,
+                      "pair_evals_per_s": evals / (ms / 1e3),
+                      "alu": {"achieved_tflops": evals * fp32_ops_per_pair(2) / (ms / 1e3) / 1e12,
+                              "peak_tflops": alu_peak,
+                              "frac": evals * fp32_ops_per_pair(2) / (ms / 1e3) / 1e12 / alu_peak},
+                      "hmc_iterations": args.steps, "leapfrog_steps_per_s_all_chains":
+                          args.steps * N_LEAPFROG * len(ds) * chains / wall,
+                      "accept_rate": float(np.mean(acc)), "wall_s": wall}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,10 +538,16 @@ def main():
     ap.add_argument("--strip", type=int, default=None)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--kernel-hash", action="store_true", help="print the pair kernel's source hash and exit")
+    ap.add_argument("--sweep", action="store_true", help="the N = 20000 / 50000 scale sweep (pass only)")
+    ap.add_argument("--batch", action="store_true", help="batched datasets x chains")
     args = ap.parse_args()
     if args.kernel_hash:
         print(pair_kernel_sha256())
         return 0
+    if args.sweep:
+        return run_sweep(args)
+    if args.batch:
+        return run_batch(args)
     if args.pass_only:
         return run_pass_only(args)
     if args.warmup < 3:
