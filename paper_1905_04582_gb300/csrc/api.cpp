@@ -562,7 +562,7 @@ AcceptArgs make_accept_args(const mds_ctx *c, int n_steps, int metropolis, int u
     a.n_start_parts = start_grid;
     a.start_part = c->e_start;
     if (n_steps > 0) {
-        a.n_end_parts = static_cast<int32_t>(c->nt);
+        a.n_end_parts = static_cast<int32_t>(c->nt * kReduceQuarters);
         a.end_part = c->e_end;
     } else {
         a.n_end_parts = start_grid;
@@ -861,7 +861,7 @@ int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out
     if ((st = dev_alloc_t(c, &c->bad, sizeof(unsigned long long)))) return cleanup(st);
     const int64_t start_grid_max = (nd_pad + 4 * 256 - 1) / (4 * 256) + 1;
     if ((st = dev_alloc_t(c, &c->e_start, start_grid_max * 2 * sizeof(double)))) return cleanup(st);
-    if ((st = dev_alloc_t(c, &c->e_end, (c->nt + 1) * 2 * sizeof(double)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->e_end, (c->nt * kReduceQuarters + 1) * 2 * sizeof(double)))) return cleanup(st);
     if ((st = dev_alloc(c, &c->stage, nd_pad * sizeof(double)))) return cleanup(st);
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
@@ -1588,7 +1588,7 @@ int batch_tables(mds_batch *b, int strip) {
         ch[g] = BatchChain{c->xrow, c->xcol, static_cast<float *>(c->row_part), static_cast<float *>(c->col_part),
                            static_cast<float *>(c->scal_part)};
         rc[g] = reduce_args(c, kModeEval, 0.0);
-        for (int J = 0; J < c->nt; ++J) jobs.push_back(make_int2(g, J));
+        for (int J = 0; J < c->nt * kReduceQuarters; ++J) jobs.push_back(make_int2(g, J));
         jobs.push_back(make_int2(g, -1));
     }
     if (st.size() > b->strips_cap) {

@@ -245,10 +245,13 @@ struct ReduceArgs {
     double *scal;             // [kScalars]
     XState xs;
     void *p;                  // [N][D]
-    double *energy_part;      // [nt][2] (kModeHalfKick): kinetic, ||x||^2
+    double *energy_part;      // [nt * kReduceQuarters][2] (kModeHalfKick): kinetic, ||x||^2
     unsigned *err;
 };
 
+// The reduction runs kReduceQuarters CTAs per column block (16 items each)
+// plus one CTA for the scalars.
+constexpr int kReduceQuarters = 4;
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t s);
 
 // Trajectory start: (optionally) draw / load p, save x0 and the cached

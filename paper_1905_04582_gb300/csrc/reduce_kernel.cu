@@ -27,8 +27,15 @@
 namespace mds {
 namespace {
 
-constexpr int kRedThreads = 512;  // 64 items x 8 splits
-constexpr int kSplits = kRedThreads / kTile;
+// One CTA reduces a quarter of a column block (16 items) with 16 splits per
+// item: small CTAs become resident beside the pair pass's last CTAs (the
+// reduction is launched as a programmatic dependent), and one round of loads
+// covers the partials of a block at N = 5392.
+constexpr int kRedThreads = 256;
+constexpr int kRedRows = 16;                       // items per CTA
+constexpr int kRedQuarters = kReduceQuarters;      // CTAs per column block
+static_assert(kRedQuarters * kRedRows == kTile, "quarters must cover a block");
+constexpr int kSplits = kRedThreads / kRedRows;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kSqrt2Pi = 2.50662827463100050242;
 
@@ -143,18 +150,18 @@ struct GradT<double> {
 // One CTA of the reduction: column block J of one problem, or its scalar
 // sums when J < 0.  `a` may live in global memory (batched launches).
 template <typename T, int D>
-__device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J) {
+__device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int Jq) {
     constexpr bool kF32 = std::is_same<T, float>::value;
     using Acc = typename std::conditional<kF32, DF, double>::type;
     using G = typename GradT<T>::type;
-    __shared__ Acc sm[kSplits * kTile * D > 64 ? kSplits * kTile * D : 64];
+    __shared__ Acc sm[kSplits * kRedRows > 64 ? kSplits * kRedRows : 64];
     const int tid = threadIdx.x;
     const int nt = a.nt;
     // every input (partials, x, p) comes from the pass just before
     pdl_trigger();
     pdl_wait();
 
-    if (J < 0) {
+    if (Jq < 0) {
         // scalar partials of all strips -> L, sum r, dL/dsigma (fixed order)
         const T *sp = reinterpret_cast<const T *>(a.scal_part);
         Acc e2{}, md{}, lp{};
@@ -228,15 +235,17 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         return;
     }
 
-    const int r = tid & (kTile - 1);
-    const int s = tid / kTile;
+    const int J = Jq / kRedQuarters;
+    const int r = (Jq % kRedQuarters) * kRedRows + (tid % kRedRows);  // row within the block
+    const int s = tid / kRedRows;
     const int64_t k = static_cast<int64_t>(J) * kTile + r;
     Acc acc[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) acc[d] = Acc{};
-    // loads are issued four at a time (independent of the running sums) so
-    // that the latency of the L2 reads overlaps
-    constexpr int kU = 4;
+    // the loads of a round are issued together (independent of the running
+    // sums), so one round costs one L2 latency; at N = 5392 a round covers
+    // every partial of the block
+    constexpr int kU = D <= 2 ? 8 : D <= 4 ? 4 : 2;
     const T *cp = reinterpret_cast<const T *>(a.col_part);
     for (int I0 = s; I0 <= J; I0 += kSplits * kU) {
         T v[kU][D];
@@ -278,9 +287,27 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
                     acc[d] -= v[u][d];
             }
     }
+    // the kSplits partial sums of every (row, coordinate), combined one
+    // coordinate at a time through shared memory, in a fixed order
+    Acc gsum[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) sm[(s * kTile + r) * D + d] = acc[d];
-    __syncthreads();
+    for (int d = 0; d < D; ++d) {
+        const int rq = tid % kRedRows;
+        sm[s * kRedRows + rq] = acc[d];
+        __syncthreads();
+        if (s == 0) {
+            Acc g = sm[rq];
+#pragma unroll
+            for (int q = 1; q < kSplits; ++q) {
+                if constexpr (kF32)
+                    df_add(g, sm[q * kRedRows + rq]);
+                else
+                    g += sm[q * kRedRows + rq];
+            }
+            gsum[d] = g;
+        }
+        __syncthreads();
+    }
 
     Acc ke{}, xx{};
     float xmax = 0.f;
@@ -291,14 +318,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         bool bad = false;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            Acc g = sm[r * D + d];
-#pragma unroll
-            for (int q = 1; q < kSplits; ++q) {
-                if constexpr (kF32)
-                    df_add(g, sm[(q * kTile + r) * D + d]);
-                else
-                    g += sm[(q * kTile + r) * D + d];
-            }
+            const Acc g = gsum[d];
             T gv;
             if constexpr (kF32) {
                 grad[k * D + d] = make_float2(g.hi, g.lo);
@@ -338,15 +358,15 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             const DF tk = block_sum_df<kRedThreads>(ke, sm);
             const DF tx = block_sum_df<kRedThreads>(xx, sm);
             if (tid == 0) {
-                a.energy_part[2 * J] = df_double(tk);
-                a.energy_part[2 * J + 1] = df_double(tx);
+                a.energy_part[2 * Jq] = df_double(tk);
+                a.energy_part[2 * Jq + 1] = df_double(tx);
             }
         } else {
             const double tk = block_sum_d<kRedThreads>(ke, sm);
             const double tx = block_sum_d<kRedThreads>(xx, sm);
             if (tid == 0) {
-                a.energy_part[2 * J] = tk;
-                a.energy_part[2 * J + 1] = tx;
+                a.energy_part[2 * Jq] = tk;
+                a.energy_part[2 * Jq + 1] = tx;
             }
         }
     }
@@ -361,10 +381,12 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_constant__ ReduceArgs a) {
-    reduce_body<T, D>(a, a.mode, blockIdx.x == static_cast<unsigned>(a.nt) ? -1 : static_cast<int>(blockIdx.x));
+    const int last = a.nt * kRedQuarters;
+    reduce_body<T, D>(a, a.mode, blockIdx.x == static_cast<unsigned>(last) ? -1 : static_cast<int>(blockIdx.x));
 }
 
-// Batched: job (problem index, column block or -1) per CTA.
+// Batched: job (problem index, quarter-block index J * kReduceQuarters + q,
+// or -1 for the scalars) per CTA.
 template <int D>
 __global__ void __launch_bounds__(kRedThreads) reduce_batch_kernel(const ReduceArgs *cfg, const int2 *jobs, int mode) {
     const int2 job = jobs[blockIdx.x];
@@ -788,7 +810,7 @@ int grid_for(int64_t work, int threads) {
 }  // namespace
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t s) {
-    const dim3 grid(a.nt + 1);  // one CTA per column block + one for the scalars
+    const dim3 grid(a.nt * kRedQuarters + 1);  // kRedQuarters CTAs per column block + one for the scalars
     cudaError_t e = cudaSuccess;
     if (a.fp64) {
         MDS_SWITCH_D_PDL(reduce_kernel, double, grid, kRedThreads, s, a)
