@@ -122,6 +122,91 @@ def custom(n, d, sigma=0.5, seed=11, noise=None, mixture=None):
                 mixture=mixture)
 
 
+# --- phylogenetic forests (section 2.2's Brownian-diffusion prior) --------
+
+# the paper's four influenza subtypes (section 3): 1370 + 1389 + 1393 + 1240 = 5392
+SUBTYPE_SIZES = (1370, 1389, 1393, 1240)
+
+
+@dataclass
+class Forest:
+    n: int                 # tips (items 0..n-1 are nodes 0..n-1)
+    parent: np.ndarray     # [n_nodes] int64, -1 for roots
+    length: np.ndarray     # [n_nodes] float64 branch length to the parent (0 for roots)
+    sigma_mat: np.ndarray  # D x D diffusion covariance
+    mu: np.ndarray         # D root mean
+    tau0: float            # root variance scalar
+    tau_u: float           # variance scalar of unsequenced items (tips that are roots)
+
+    @property
+    def n_nodes(self):
+        return int(self.parent.shape[0])
+
+
+def random_forest(tree_sizes, n_lone=0, d=2, seed=0, tau0=1.0, tau_u=2.0, rate=1.0):
+    """Random coalescent trees over disjoint groups of items, plus n_lone
+    unsequenced items.  Items are assigned to the groups in a seeded random
+    order; each tree joins two random lineages at a time after an
+    exponential waiting time (rate * k (k - 1) / 2 for k lineages), so branch
+    lengths are > 0.  Sigma is a seeded random SPD matrix, mu seeded."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(sum(tree_sizes)) + int(n_lone)
+    items = rng.permutation(n)
+    parent = [-1] * n
+    length = [0.0] * n
+    time = [0.0] * n
+    pos = 0
+    for size in tree_sizes:
+        lineages = [int(v) for v in items[pos:pos + size]]
+        pos += size
+        t = 0.0
+        while len(lineages) > 1:
+            k = len(lineages)
+            t += rng.exponential(1.0 / (rate * k * (k - 1) / 2.0))
+            a, b = rng.choice(k, size=2, replace=False)
+            u, v = lineages[a], lineages[b]
+            node = len(parent)
+            parent.append(-1)
+            length.append(0.0)
+            time.append(t)
+            for c in (u, v):
+                parent[c] = node
+                length[c] = t - time[c]
+            lineages = [w for j, w in enumerate(lineages) if j != a and j != b] + [node]
+    a = rng.standard_normal((d, d))
+    sigma_mat = a @ a.T / d + 0.5 * np.eye(d)
+    mu = rng.standard_normal(d)
+    return Forest(n, np.array(parent, dtype=np.int64), np.array(length, dtype=np.float64), sigma_mat, mu,
+                  float(tau0), float(tau_u))
+
+
+def brownian_tips(forest, seed=0):
+    """One draw of X (N x D) from the Brownian diffusion down the forest:
+    roots ~ N(mu, tau0 Sigma), children ~ N(parent, length Sigma),
+    unsequenced items ~ N(mu, tau_u Sigma)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = forest.mu.shape[0]
+    chol = np.linalg.cholesky(forest.sigma_mat)
+    n_nodes = forest.n_nodes
+    val = np.full((n_nodes, d), np.nan)
+    children = [[] for _ in range(n_nodes)]
+    for k in range(n_nodes):
+        if forest.parent[k] >= 0:
+            children[forest.parent[k]].append(k)
+    for r in range(n_nodes):
+        if forest.parent[r] >= 0:
+            continue
+        scale = forest.tau_u if r < forest.n else forest.tau0
+        val[r] = forest.mu + np.sqrt(scale) * chol @ rng.standard_normal(d)
+        stack = [r]
+        while stack:
+            u = stack.pop()
+            for c in children[u]:
+                val[c] = val[u] + np.sqrt(forest.length[c]) * chol @ rng.standard_normal(d)
+                stack.append(c)
+    return val[:forest.n].copy()
+
+
 # --- layout helpers (pure data movement) ---------------------------------
 
 def packed_to_full(y_packed, n, diag=0.0, dtype=np.float32):
