@@ -63,6 +63,11 @@ def _load():
                                              _vp, _vp]
             lib.mdso_sigma_draws.restype = None
             lib.mdso_philox4x32_10.argtypes = [_vp, _vp, _vp]
+            lib.mdso_rwmh.argtypes = [_i64, _int, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _vp, _vp, _vp, _vp, _vp]
+            lib.mdso_rwmh.restype = _int
+            lib.mdso_rwmh_draws.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                            _i64, _int, _vp, _vp, _vp]
+            lib.mdso_rwmh_draws.restype = None
             lib.mdso_draw_momentum.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.c_uint32, _i64, _vp, _vp]
             for f in ("mdso_loglik_kept", "mdso_gradient_rows_kept", "mdso_dsigma_kept",
@@ -263,3 +268,31 @@ def sigma_draws(seed, chain, it):
     u = np.zeros(1)
     _load().mdso_sigma_draws(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, chain, it, _ptr(z), _ptr(u))
     return float(z[0]), float(u[0])
+
+
+def rwmh(yp, x, sigma, step, items, z_all, u_all, w=1.0, lam=0.0):
+    """Single-item random-walk Metropolis (section 2.3's prior art):
+    proposal t moves item items[t] by step * z_all[t]; accepted iff
+    log u_t < log pi(X') - log pi(X).  Returns (x, accepted, dlogpi)."""
+    x = np.array(x, dtype=np.float64, order="C")
+    n, d = x.shape
+    yp = np.ascontiguousarray(yp, dtype=np.float32) if w != 0.0 else np.zeros(1, dtype=np.float32)
+    items = np.ascontiguousarray(items, dtype=np.int64)
+    z = np.ascontiguousarray(z_all, dtype=np.float64).reshape(len(items), d)
+    u = np.ascontiguousarray(u_all, dtype=np.float64)
+    acc = np.zeros(len(items), dtype=np.int32)
+    dl = np.zeros(len(items))
+    _check(_load().mdso_rwmh(n, d, _ptr(yp), _ptr(x), sigma, w, lam, step, len(items), _ptr(items), _ptr(z),
+                             _ptr(u), _ptr(acc), _ptr(dl)), "rwmh")
+    return x, acc, dl
+
+
+def rwmh_draws(seed, chain, it, n, d):
+    """(item, z[D], u) of random-walk proposal `it` from Philox4x32-10
+    (counters (it, 0, chain, 3) and (it, 1 + q, chain, 3))."""
+    item = ctypes.c_int64()
+    z = np.zeros(d)
+    u = ctypes.c_double()
+    _load().mdso_rwmh_draws(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, chain, it, n, d, ctypes.byref(item),
+                            _ptr(z), ctypes.byref(u))
+    return int(item.value), z, float(u.value)

@@ -575,3 +575,89 @@ int mdso_sigma_mh(int64_t n, int d, const float *yp, const unsigned char *keep, 
     *sigma = s;
     return MDSO_OK;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Single-item random-walk Metropolis: the prior-art sampler of section    */
+/* 2.3 (a low-dimensional random-walk kernel applied to one x_i at a time). */
+/* Moving x_i changes only the N - 1 terms r_ij, j != i, so a proposal     */
+/* costs O(N D) instead of a full O(N^2 D) evaluation.                      */
+/* ---------------------------------------------------------------------- */
+
+/* sum_{j != i} r_ij with x_i taken as xi (a D-vector), the other rows of X
+ * as they are. */
+static double row_r(int64_t n, int d, const float *yp, const double *x, int64_t i, const double *xi,
+                    double sigma) {
+    nsum_t s = {0.0, 0.0};
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double dd = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double t = xi[k] - x[j * d + k];
+            dd += t * t;
+        }
+        nsum_add(&s, r_term(y_at(yp, n, i, j), sqrt(dd), sigma));
+    }
+    return nsum_get(&s);
+}
+
+/* n_prop proposals; proposal t moves item items[t] to x_i + step z_t
+ * (z_all: n_prop x D) and is accepted iff log u_t < log pi(X') - log pi(X),
+ * log pi = w L(X, sigma) - (lambda/2) ||X||^2, where
+ *   L(X') - L(X) = sum_{j != i} r_ij(x_i) - sum_{j != i} r_ij(x_i')
+ * (the -M log sigma of Eq. (2) cancels).  x is updated in place;
+ * accepted[t] and dlogpi[t] (optional) receive the decision and the
+ * log-target difference. */
+int mdso_rwmh(int64_t n, int d, const float *yp, double *x, double sigma, double w, double lambda, double step,
+              int n_prop, const int64_t *items, const double *z_all, const double *u_all, int *accepted,
+              double *dlogpi) {
+    if (n < 2 || d < 1 || d > 16 || n_prop < 0 || !x || !items || !z_all || !u_all || !(sigma > 0.0) ||
+        (w != 0.0 && !yp))
+        return MDSO_BAD_ARG;
+    for (int t = 0; t < n_prop; ++t) {
+        int64_t i = items[t];
+        if (i < 0 || i >= n) return MDSO_BAD_ARG;
+        double xi[16];
+        double sq0 = 0.0, sq1 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            xi[k] = x[i * d + k] + step * z_all[(int64_t)t * d + k];
+            sq0 += x[i * d + k] * x[i * d + k];
+            sq1 += xi[k] * xi[k];
+        }
+        double dl = 0.0;
+        if (w != 0.0) dl = w * (row_r(n, d, yp, x, i, x + i * d, sigma) - row_r(n, d, yp, x, i, xi, sigma));
+        double a = dl - 0.5 * lambda * (sq1 - sq0);
+        int acc = log(u_all[t]) < a;
+        if (acc)
+            for (int k = 0; k < d; ++k) x[i * d + k] = xi[k];
+        if (accepted) accepted[t] = acc;
+        if (dlogpi) dlogpi[t] = a;
+    }
+    return MDSO_OK;
+}
+
+/* Draws of random-walk proposal `iter` of a chain keyed (seed_lo, seed_hi):
+ * counter (iter, 0, chain, 3): item = floor(word0 * N / 2^32), u from
+ * word 1; counters (iter, 1 + q, chain, 3) give z components 4q..4q+3 by
+ * Box-Muller from words (0, 1) and (2, 3), as the momenta. */
+void mdso_rwmh_draws(uint32_t seed_lo, uint32_t seed_hi, uint32_t chain, uint32_t iter, int64_t n, int d,
+                     int64_t *item, double *z, double *u) {
+    uint32_t key[2] = {seed_lo, seed_hi};
+    uint32_t ctr[4] = {iter, 0u, chain, 3u};
+    uint32_t o[4];
+    mdso_philox4x32_10(ctr, key, o);
+    *item = (int64_t)(((uint64_t)o[0] * (uint64_t)n) >> 32);
+    *u = bits_to_open_unit(o[1]);
+    for (int q = 0; 4 * q < d; ++q) {
+        uint32_t c2[4] = {iter, 1u + (uint32_t)q, chain, 3u};
+        mdso_philox4x32_10(c2, key, o);
+        for (int h = 0; h < 2; ++h) {
+            double u1 = bits_to_open_unit(o[2 * h]);
+            double u2 = bits_to_open_unit(o[2 * h + 1]);
+            double rad = sqrt(-2.0 * log(u1));
+            double th = 2.0 * M_PI * u2;
+            int e0 = 4 * q + 2 * h;
+            if (e0 < d) z[e0] = rad * cos(th);
+            if (e0 + 1 < d) z[e0 + 1] = rad * sin(th);
+        }
+    }
+}

@@ -48,6 +48,11 @@ MUTANTS = {
     "sigma_prior_no_jacobian": ("return s0 * log(lambda) - r0 * lambda;", "return (s0 - 1.0) * log(lambda) - r0 * lambda;"),
     "sigma_prior_rate_as_scale": ("return s0 * log(lambda) - r0 * lambda;", "return s0 * log(lambda) - lambda / r0;"),
     "sigma_step_on_sigma": ("double s1 = exp(log(s) + step * z_all[t]);", "double s1 = s + step * z_all[t];"),
+    "rwmh_difference_reversed": ("dl = w * (row_r(n, d, yp, x, i, x + i * d, sigma) - row_r(n, d, yp, x, i, xi, sigma));",
+                                 "dl = w * (row_r(n, d, yp, x, i, xi, sigma) - row_r(n, d, yp, x, i, x + i * d, sigma));"),
+    "rwmh_row_skips_a_neighbour": ("        if (j == i) continue;\n        double dd = 0.0;",
+                                   "        if (j == i || j == i + 1) continue;\n        double dd = 0.0;"),
+    "rwmh_prior_sign": ("double a = dl - 0.5 * lambda * (sq1 - sq0);", "double a = dl + 0.5 * lambda * (sq1 - sq0);"),
 }
 
 _i64, _int, _dbl, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -69,6 +74,7 @@ def _build(tmp_path, name, src_text):
     lib.mdso_gradient_rows_kept.argtypes = [_i64, _int, _vp, _vp, _vp, _dbl, _vp, _i64, _int, _vp, _vp, _vp]
     lib.mdso_lpd.argtypes = [_i64, _int, _vp, _i64, _vp, _int, _vp, _vp, _vp]
     lib.mdso_sigma_mh.argtypes = [_i64, _int, _vp, _vp, _vp, _vp, _dbl, _int, _dbl, _dbl, _dbl, _vp, _vp, _int, _vp]
+    lib.mdso_rwmh.argtypes = [_i64, _int, _vp, _vp, _dbl, _dbl, _dbl, _dbl, _int, _vp, _vp, _vp, _vp, _vp]
     return lib
 
 
@@ -153,6 +159,36 @@ def _pins_hold(lib):
                           _p(zz[b:b + 20]), _p(uu[b:b + 20]), 1, None)
         lam.append(1.0 / sg[0] ** 2)
     if stats.kstest(lam[100:], stats.gamma(3.0, scale=0.5).cdf).pvalue < 1e-4:
+        return False
+    # single-item random walk: each log-target difference against full
+    # likelihoods; with the likelihood off the chain samples N(0, 1/lambda)
+    items = np.array([0, 4, 8, 2, 2], dtype=np.int64)
+    zr = np.ascontiguousarray(rng.standard_normal((5, d)))
+    ur = np.full(5, 0.5)
+    xr = np.ascontiguousarray(x.copy())
+    acc = np.zeros(5, dtype=np.int32)
+    dlr = np.zeros(5)
+    lib.mdso_rwmh(n, d, _p(y), _p(xr), s, 1.0, 0.4, 0.3, 5, _p(items), _p(zr), _p(ur), _p(acc), _p(dlr))
+    xs = x.copy()
+    for t in range(5):
+        xp = xs.copy()
+        xp[items[t]] += 0.3 * zr[t]
+        ref = ll(xp) - ll(xs) - 0.2 * (np.sum(xp ** 2) - np.sum(xs ** 2))
+        if not math.isclose(dlr[t], ref, rel_tol=1e-10, abs_tol=1e-10):
+            return False
+        if acc[t]:
+            xs = xp
+    rr = np.random.default_rng(6)
+    tot = 60000
+    it = np.ascontiguousarray(rr.integers(0, 2, tot).astype(np.int64))
+    zz, uu = rr.standard_normal(tot), rr.random(tot)
+    xq = np.zeros(2)
+    smp = []
+    for b in range(0, tot, 20):
+        lib.mdso_rwmh(2, 1, None, _p(xq), 1.0, 0.0, 2.0, 1.2, 20, _p(it[b:b + 20]), _p(zz[b:b + 20]),
+                      _p(uu[b:b + 20]), None, None)
+        smp.append(xq[0])
+    if stats.kstest(smp[100:], stats.norm(scale=math.sqrt(0.5)).cdf).pvalue < 1e-4:
         return False
     # harmonic oscillator closed form
     lam, eps, steps = 1.0, 0.1, 5
