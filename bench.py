@@ -40,14 +40,17 @@ WORKLOAD = "paper-scale N=5392 D=2, 6-component Gaussian mixture, sigma=0.3, FP3
 SM_MAX_MHZ = 2070.0
 
 
-def fp32_ops_per_pair(d):
-    """FP32 lane operations per pair in pair2_f32 (pair_math.cuh), an FMA
-    counting once: per coordinate the exact-split differences (3), squares
+def fp32_ops_per_pair(d, far_frac=0.0):
+    """FP32 lane operations per pair, an FMA counting once.  pair2_f32
+    (pair_math.cuh): per coordinate the exact-split differences (3), squares
     (1), cross term (2) and the two gradient accumulations (2); fixed: d^2,
     residual (2), half inverse, corrected e (2), exp argument, Mills ratio
     P and D (3 + 3), D Phi, 1/Phi, phi/Phi, log-product, e^2, m delta, w (2),
-    w/delta."""
-    return 8 * d + 22
+    w/delta: 8 D + 22.  pair2_far (warp blocks whose pairs all lie at
+    z >= 8, Phi terms dropped): the same per coordinate; fixed d^2, residual
+    (2), half inverse, corrected e (2), e^2, w (2): 8 D + 9.  far_frac is the
+    fraction of warp blocks that took pair2_far."""
+    return (1.0 - far_frac) * (8 * d + 22) + far_frac * (8 * d + 9)
 
 
 PAIR_KERNEL_SOURCES = ("pair_kernel.cu", "pair_math.cuh", "mds_internal.h", "mills_ratio_coeffs.h")
@@ -268,6 +271,10 @@ def run_gpu(args):
     model.set_data(wl.y_packed)
     model.set_locations(wl.x_eval)
     model.set_sigma(wl.sigma)
+    if args.order == "locality":
+        model.reorder()  # tile layouts in the locality order of the start point
+    far_blocks, total_blocks = model.far_blocks()
+    far_frac = far_blocks / total_blocks
     eps = args.eps
     seed = 1234 + rank
 
@@ -333,7 +340,7 @@ def run_gpu(args):
     clk = clocks.summary()
     sm_mhz = (clk or {}).get("sm_max_mhz") or SM_MAX_MHZ
     alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12  # TFP32-op/s
-    ops = fp32_ops_per_pair(wl.d)
+    ops = fp32_ops_per_pair(wl.d, far_frac)
     alu_achieved = m_pairs * ops / (pass_avg_ms / 1e3) / 1e12
     traffic = kernel_traffic(wl.n, wl.d)
 
@@ -344,6 +351,13 @@ def run_gpu(args):
         m64.set_sigma(wl.sigma)
         ms64 = m64.time_pass(5)
     ms32 = model.time_pass(20)
+    # the same FP32C pass with the items in the caller's (random) order: no
+    # warp block is all far, every pair evaluates Phi
+    with MDS(wl.n, wl.d, "fp32c", stream=stream) as m_u:
+        m_u.set_data(wl.y_packed)
+        m_u.set_locations(wl.x_eval)
+        m_u.set_sigma(wl.sigma)
+        ms32_unordered = m_u.time_pass(20)
     pass_dist = pass_distribution(model, wl, flush_l2, stream)
 
     # end to end through the C ABI with host buffers: X in, one HMC
@@ -381,18 +395,25 @@ def run_gpu(args):
                        "precision": "FP32 per pair, compensated FP32 partials reduced in FP64",
                        "step": f"one HMC iteration: {N_LEAPFROG} leapfrog steps (fused L+grad pass each) + Metropolis",
                        "eps": eps, "strip": model.get_strip(),
+                       "order": ("locality order of the start point (mds_reorder)" if args.order == "locality"
+                                 else "caller's item order"),
                        "l2": "flushed (512 MB write) between timed steps; Y (58 MB) stays L2-resident within a step",
                        "parallelism": f"replicas x{world}"},
             "leapfrog_steps_per_s": lf_steps,
             "accept_rate": acc_total / args.steps,
             "hbm_fraction_of_pairs_rate": value * 4.0 / 1e9 / hbm_peak,
+            "far_blocks": {"far": far_blocks, "total": total_blocks, "fraction": far_frac,
+                           "note": "warp blocks of 64 x 8 pairs all at z >= 8: Phi terms skipped (start point)"},
             "pass_alone": {"fp32c_ms": ms32, "fp64_ms": ms64, "fp32c_pairs_per_s": m_pairs / (ms32 / 1e3),
+                           "fp32c_caller_order_ms": ms32_unordered,
                            "fp64_pairs_per_s": m_pairs / (ms64 / 1e3), "speedup_vs_fp64": ms64 / ms32,
                            "pair_kernel_warm_us": pass_dist["warm"], "pair_kernel_cold_us": pass_dist["cold"]},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFP32-op/s",
                          "frac": alu_achieved / alu_peak, "traffic": traffic,
                          "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
-                         "ops_per_pair": ops, "kernel": f"pair_f32_kernel<{wl.d}>", "launches_timed": n_pass,
+                         "ops_per_pair": ops, "ops_per_pair_note": "8D+22 (Phi evaluated), 8D+9 (far blocks), "
+                                                                   "weighted by the far-block fraction",
+                         "kernel": f"pair_f32_kernel<{wl.d}>", "launches_timed": n_pass,
                          "avg_launch_ms": pass_avg_ms, "pairs_per_launch": m_pairs,
                          "hbm_view": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                                       "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} hbm_gbs",
@@ -432,8 +453,12 @@ def run_pass_only(args):
         m.set_data(wl.y_packed)
         m.set_locations(wl.x_eval)
         m.set_sigma(wl.sigma)
+        if args.order == "locality":
+            m.reorder()
+        far, total = m.far_blocks()
         ms = m.time_pass(args.reps)
         print(json.dumps({"pass_only": True, "n": wl.n, "d": wl.d, "precision": args.precision,
+                          "order": args.order, "far_fraction": far / total,
                           "strip": m.get_strip(), "ms_per_pass": ms, "pairs_per_s": wl.m / (ms / 1e3),
                           "alg_gb_per_s": 4.0 * wl.m / (ms / 1e3) / 1e9}), flush=True)
     return 0
@@ -463,14 +488,20 @@ def run_sweep(args):
             m.set_data(wl.y_packed)
             m.set_locations(wl.x_eval)
             m.set_sigma(wl.sigma)
+            if args.order == "locality":
+                m.reorder()
+            far, total = m.far_blocks()
             ms = m.time_pass(args.reps)
             strip = m.get_strip()
+        ff = far / total
         line = {"sweep": True, "workload": wl.name, "n": n, "d": d, "pairs": wl.m, "strip": strip,
+                "order": args.order, "far_fraction": ff,
                 "ms_per_pass": ms, "pairs_per_s": wl.m / (ms / 1e3),
                 "hbm": {"achieved_gbs": 4.0 * wl.m / (ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
                         "frac": 4.0 * wl.m / (ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind},
-                "alu": {"achieved_tflops": wl.m * fp32_ops_per_pair(d) / (ms / 1e3) / 1e12, "peak_tflops": alu_peak,
-                        "frac": wl.m * fp32_ops_per_pair(d) / (ms / 1e3) / 1e12 / alu_peak}}
+                "alu": {"achieved_tflops": wl.m * fp32_ops_per_pair(d, ff) / (ms / 1e3) / 1e12,
+                        "peak_tflops": alu_peak,
+                        "frac": wl.m * fp32_ops_per_pair(d, ff) / (ms / 1e3) / 1e12 / alu_peak}}
         if n == 20000 and d == 2:
             with MDS(wl.n, wl.d, "fp64") as m64:
                 m64.set_data(wl.y_packed)
@@ -522,6 +553,168 @@ def run_batch(args):
     return 0
 
 
+def run_tree(args):
+    """HMC at N = 5392 with the phylogenetic prior of section 2.2 in the
+    target (four coalescent trees of the paper's subtype sizes, locations
+    drawn from the Brownian process, Y from those locations): ms per
+    iteration with and without the prior, and the prior's evaluation alone."""
+    import torch
+    from scipy.spatial.distance import pdist
+    from paper_1905_04582_gb300 import build as B
+    from paper_1905_04582_gb300 import workloads as W
+    from paper_1905_04582_gb300.mds import MDS
+    B.build()
+    torch.cuda.set_device(0)
+    f = W.random_forest(W.SUBTYPE_SIZES, n_lone=0, d=2, seed=1, rate=0.05)
+    x_true = W.brownian_tips(f, seed=2)
+    rng = np.random.default_rng(3)
+    sigma = 0.3
+    y = np.abs(pdist(x_true) + sigma * rng.standard_normal(f.n * (f.n - 1) // 2)).astype(np.float32)
+    x_eval = (x_true + 0.02 * rng.standard_normal(x_true.shape)).astype(np.float32)
+    stream = torch.cuda.Stream()
+    out = {"tree": True, "n": f.n, "trees": list(W.SUBTYPE_SIZES), "steps": N_LEAPFROG}
+    for with_tree in (False, True):
+        with MDS(f.n, 2, "fp32c", stream=stream) as m:
+            m.set_data(y)
+            m.set_locations(x_eval)
+            m.set_sigma(sigma)
+            if with_tree:
+                m.set_tree_prior(f.parent, f.length, f.sigma_mat, f.mu, f.tau0, f.tau_u)
+            m.reorder()
+            m.hmc(3, N_LEAPFROG, args.eps, seed=5)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            m.hmc_enqueue(args.steps, N_LEAPFROG, args.eps, seed=6)
+            ev1.record(stream)
+            acc, _, _ = m.hmc_collect()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / args.steps
+            key = "with_tree_prior" if with_tree else "likelihood_only"
+            out[key] = {"ms_per_iteration": ms, "leapfrog_steps_per_s": N_LEAPFROG / (ms / 1e3),
+                        "accept_rate": float(np.mean(acc))}
+            if with_tree:
+                g = torch.empty((f.n, 2), dtype=torch.float64, device="cuda")
+                m.tree_prior(out=g)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                reps = 50
+                for _ in range(reps):
+                    m.tree_prior(out=g)
+                torch.cuda.synchronize()
+                out["tree_prior_call_us"] = 1e6 * (time.perf_counter() - t0) / reps
+    out["tree_prior_cost_per_step_us"] = 1e3 * (out["with_tree_prior"]["ms_per_iteration"] -
+                                               out["likelihood_only"]["ms_per_iteration"]) / N_LEAPFROG
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def ess(chain):
+    """Effective sample size of a scalar chain: n / tau, tau = 1 + 2 sum of
+    autocorrelations over Geyer's initial positive sequence (pairs of lags
+    summed while positive)."""
+    x = np.asarray(chain, dtype=np.float64)
+    n = len(x)
+    x = x - x.mean()
+    v = np.dot(x, x) / n
+    if n < 4 or v == 0.0:
+        return float(n)
+    f = np.fft.rfft(x, 2 * n)
+    acf = np.fft.irfft(f * np.conj(f))[:n] / (n * v)
+    tau = -1.0
+    for k in range(0, n - 1, 2):
+        pair = acf[k] + acf[k + 1]
+        if pair <= 0:
+            break
+        tau += 2 * pair
+    return float(n / max(tau, 1.0))
+
+
+def run_mixing(args):
+    """Mixing of HMC against the single-item random-walk Metropolis sampler
+    (section 2.3's prior art) at N = 5392: effective sample size per second of
+    sampler device time for rotation-invariant statistics (the
+    log-likelihood and distances of fixed item pairs), both from the same
+    HMC-burned-in state, step sizes from short pilots."""
+    import torch
+    from paper_1905_04582_gb300 import build as B
+    from paper_1905_04582_gb300 import workloads as W
+    from paper_1905_04582_gb300.mds import MDS
+    B.build()
+    torch.cuda.set_device(0)
+    wl = W.paper_scale()
+    stream = torch.cuda.Stream()
+    pairs = np.array([[0, 1], [2, 3], [10, 500], [100, 4000], [7, 2500]])
+
+    def stats_of(m):
+        ll, _ = m.log_likelihood()
+        x = m.get_locations()
+        return [ll] + list(np.linalg.norm(x[pairs[:, 0]] - x[pairs[:, 1]], axis=1))
+
+    def timed(stream, fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    with MDS(wl.n, wl.d, "fp32c", stream=stream) as m:
+        m.set_data(wl.y_packed)
+        m.set_locations(wl.x_eval)
+        m.set_sigma(wl.sigma)
+        m.reorder()
+        # burn-in from the jittered start, then the HMC step: the largest of a
+        # few whose pilot acceptance is >= 0.6
+        m.hmc(200, N_LEAPFROG, 2e-4, seed=11)
+        x0 = m.get_locations()
+        eps = 2e-4
+        for cand in (4e-4, 8e-4, 1.6e-3):
+            acc, _, _ = m.hmc(30, N_LEAPFROG, cand, seed=12)
+            m.set_locations(x0)
+            if np.mean(acc) >= 0.6:
+                eps = cand
+        m.reorder()  # the burned-in configuration
+        x0 = m.get_locations()
+        # random-walk step: pilot acceptance closest to 0.35
+        best, step = None, 1e-3
+        for cand in (1e-3, 2e-3, 4e-3, 8e-3, 1.6e-2):
+            acc, _ = m.rwmh(2000, cand, seed=13)
+            m.set_locations(x0)
+            if best is None or abs(np.mean(acc) - 0.35) < best:
+                best, step = abs(np.mean(acc) - 0.35), cand
+        # HMC chain
+        n_hmc = args.steps if args.steps > 20 else 300
+        hmc_stats, hmc_s, hmc_acc = [], 0.0, []
+        for _ in range(n_hmc):
+            (acc, _, _), dt = timed(stream, lambda: m.hmc(1, N_LEAPFROG, eps, seed=14))
+            hmc_s += dt
+            hmc_acc.append(acc[0])
+            hmc_stats.append(stats_of(m))
+        # random-walk chain from the same state: one record per sweep of N proposals
+        m.set_locations(x0)
+        n_sweeps = 60
+        rw_stats, rw_s, rw_acc = [], 0.0, []
+        for _ in range(n_sweeps):
+            (acc, _), dt = timed(stream, lambda: m.rwmh(wl.n, step, seed=15))
+            rw_s += dt
+            rw_acc.append(float(np.mean(acc)))
+            rw_stats.append(stats_of(m))
+    hs, rs = np.array(hmc_stats), np.array(rw_stats)
+    names = ["loglik"] + [f"dist({a},{b})" for a, b in pairs]
+    out = {"mixing": True, "n": wl.n, "workload": WORKLOAD,
+           "hmc": {"eps": eps, "leapfrog_steps": N_LEAPFROG, "iterations": n_hmc, "device_s": hmc_s,
+                   "accept_rate": float(np.mean(hmc_acc)),
+                   "ess": {k: ess(hs[:, c]) for c, k in enumerate(names)}},
+           "rwmh": {"step": step, "proposals_per_sweep": wl.n, "sweeps": n_sweeps, "device_s": rw_s,
+                    "proposals_per_s": n_sweeps * wl.n / rw_s, "accept_rate": float(np.mean(rw_acc)),
+                    "ess": {k: ess(rs[:, c]) for c, k in enumerate(names)}}}
+    out["ess_per_s_ratio_hmc_over_rwmh"] = {
+        k: (out["hmc"]["ess"][k] / hmc_s) / max(out["rwmh"]["ess"][k] / rw_s, 1e-300) for k in names}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,6 +733,10 @@ def main():
     ap.add_argument("--kernel-hash", action="store_true", help="print the pair kernel's source hash and exit")
     ap.add_argument("--sweep", action="store_true", help="the N = 20000 / 50000 scale sweep (pass only)")
     ap.add_argument("--batch", action="store_true", help="batched datasets x chains")
+    ap.add_argument("--tree", action="store_true", help="HMC with the phylogenetic prior (section 2.2)")
+    ap.add_argument("--mixing", action="store_true", help="ESS/s of HMC against single-item random-walk MH")
+    ap.add_argument("--order", default="locality", choices=["locality", "caller"],
+                    help="tile layouts in the locality order (mds_reorder) or the caller's item order")
     args = ap.parse_args()
     if args.kernel_hash:
         print(pair_kernel_sha256())
@@ -548,6 +745,10 @@ def main():
         return run_sweep(args)
     if args.batch:
         return run_batch(args)
+    if args.tree:
+        return run_tree(args)
+    if args.mixing:
+        return run_mixing(args)
     if args.pass_only:
         return run_pass_only(args)
     if args.warmup < 3:

@@ -253,6 +253,105 @@ int mds_lpd(mds_ctx *ctx, double *lpd, int64_t *draws);
 /* Forget the accumulated draws (the fold stays). */
 int mds_lpd_reset(mds_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Locality order and the Phi-term cut-off.  The paper's pass (section 2.5)
+ * evaluates Phi for every pair, and calls it the rate-limiting cost of the
+ * likelihood and gradient (sections 2.3 and 4, where dropping the truncation
+ * term speeds the evaluation up several-fold).  For z = delta/sigma >= 8,
+ * log(1/Phi(z)) < 6.3e-16 and phi(z)/Phi(z) < 5.1e-15: far below the FP32
+ * rounding of the other terms.  The FP32C pass therefore skips the Phi terms
+ * for a warp's block of 64 x 8 pairs when a bounding-box test shows every
+ * pair of the block at z >= z_c.  Such blocks exist only when items that lie
+ * close in the latent space also sit close in the item order; mds_reorder
+ * arranges that inside the library.  Results stay within the FP32C tolerances
+ * either way; only the speed changes.
+ * ------------------------------------------------------------------------ */
+
+/* Host-only (no GPU needed): a locality-preserving order of N points x
+ * (N x D row-major, FP64, finite): recursive bisection of the widest
+ * coordinate, cut at multiples of 64 items, so that each run of 64
+ * consecutive items of the order is one compact cell.  perm[s] receives the
+ * item placed at position s (a permutation of 0..N-1).  Deterministic.
+ * Errors: INVALID_ARG (sizes, NULL pointers, non-finite x). */
+int mds_locality_order(int64_t n, int32_t d, const double *x, int32_t *perm);
+
+/* Re-arrange the context's tile layouts (Y, split locations, partial sums)
+ * in the locality order of the current locations (mds_locality_order).  Every
+ * API array keeps the caller's item order: locations, gradients, momenta,
+ * injected draws, held-out pairs and the Philox draws of item k are those of
+ * the unordered context; sums are taken in another order, so results agree
+ * within rounding, not bitwise.  It can be called again later (e.g. after a
+ * burn-in moved the points).  Needs data and locations; call it before
+ * mds_set_heldout (STATE otherwise) and with no HMC iterations queued.
+ * Re-packs Y on the device (a second copy of Y exists briefly).  Errors:
+ * STATE, OOM, CUDA. */
+int mds_reorder(mds_ctx *ctx);
+
+/* Diagnostics: run one evaluation pass and report how many warp blocks
+ * (64 x 8 pairs; total = 8 per 64 x 64 tile) skipped the Phi terms.
+ * Synchronises.  Errors: STATE (as mds_gradient). */
+int mds_far_blocks(mds_ctx *ctx, int64_t *far, int64_t *total);
+
+/* The current order: perm[s] = item at slot s (N entries; identity before
+ * mds_reorder). */
+int mds_get_order(const mds_ctx *ctx, int32_t *perm);
+
+/* Cut-off z_c of the Phi-term skip of the FP32C pass: 0 turns it off, else
+ * z_c >= 8 (default 8).  The FP64 path evaluates Phi for every pair.
+ * Errors: INVALID_ARG for 0 < z < 8 or a non-finite z. */
+int mds_set_tail_cutoff(mds_ctx *ctx, double z);
+
+/* ------------------------------------------------------------------------
+ * Phylogenetic Brownian-diffusion prior (section 2.2).  The items are the
+ * tips of a forest: nodes 0..N-1 are the tips (item i is node i), nodes
+ * N..n_nodes-1 internal, each with exactly two children; parent[k] = -1
+ * marks a root, and a tip that is a root is an unsequenced item.  A tree's
+ * root value is N(mu, tau0 Sigma), each child N(parent value,
+ * length[k] Sigma); an unsequenced item is N(mu, tau_u Sigma).  Then X is
+ * matrix normal with row covariance V (V_ij = tau0 + root-to-MRCA time within
+ * a tree, V_ii = tau0 + root-to-tip time, tau_u for an unsequenced item, 0
+ * across trees) and column covariance Sigma (D x D):
+ *   log p(X) = -1/2 tr[Sigma^-1 (X - 1 mu^T)^T V^-1 (X - 1 mu^T)]
+ *              - (N D/2) log 2 pi - (N/2) log|Sigma| - (D/2) log|V|.
+ * ------------------------------------------------------------------------ */
+
+/* Set the forest and its parameters (all host arrays, copied): parent and
+ * length [n_nodes] (length > 0 off the roots), sigma_mat D x D symmetric
+ * positive definite, mu [D], tau0 > 0, tau_u > 0.  N <= n_nodes <= 2N - 1.
+ * The message variances of the traversals depend on the forest alone and are
+ * computed here, once.  n_nodes = 0 (or parent NULL) removes the prior.
+ * Errors: INVALID_ARG (not a binary forest over the N tips, a length <= 0,
+ * Sigma not SPD, ...), STATE (HMC iterations queued), OOM, CUDA. */
+int mds_set_tree_prior(mds_ctx *ctx, int64_t n_nodes, const int64_t *parent, const double *length,
+                       const double *sigma_mat, const double *mu, double tau0, double tau_u);
+
+/* log p(X) of the prior at the current locations (optional) and its
+ * gradient d log p / dX = -V^-1 (X - 1 mu^T) Sigma^-1 into `grad` (N x D,
+ * optional, dtype and where as in mds_gradient), by two level-synchronous
+ * traversals of each tree on the device (O(N D^2), FP64; section 2.3 cites
+ * the linear-time post-order evaluation).  Synchronises when an output is
+ * on the host.  Errors: STATE (no prior or no locations). */
+int mds_tree_prior(mds_ctx *ctx, double *logp, void *grad, int dtype, int where);
+
+/* Single-item random-walk Metropolis, the prior-art sampler of section 2.3
+ * (a random-walk kernel applied to one x_i at a time; moving x_i changes only
+ * its N - 1 terms r_ij).  Proposal t moves item i_t to x_i + step z_t and is
+ * accepted iff log u_t < log pi(X') - log pi(X), log pi = L(X, sigma) -
+ * (lambda/2) ||X||^2 (mds_set_prior; no tree prior), with
+ * L(X') - L(X) = sum_{j != i} [r_ij(x_i) - r_ij(x_i')].  Proposals run in
+ * order in one CTA (each depends on the decisions before it): O(N D) work
+ * each.  Draws: items [n_prop] (0..N-1), z_all [n_prop x D] and u_all
+ * [n_prop] in (0,1), host arrays, all three given or all NULL; NULL draws
+ * from Philox4x32-10 keyed by seed: proposal t (a per-context counter)
+ * uses counter (t, 0, 0, 3) for the item floor(word0 N / 2^32) and u from
+ * word 1, and (t, 1 + q, 0, 3) for z components 4q..4q+3 (Box-Muller).
+ * accepted [n_prop] and dlogpi [n_prop] (host, optional) receive the
+ * decisions and the log-target differences.  Synchronises.  Errors:
+ * INVALID_ARG, STATE (no data / locations / sigma, a tree prior, HMC
+ * iterations queued). */
+int mds_rwmh(mds_ctx *ctx, int n_prop, double step, uint64_t seed, const int64_t *items, const double *z_all,
+             const double *u_all, int32_t *accepted, double *dlogpi);
+
 /* Number of pairs M = N(N-1)/2 and the bytes of tile-packed Y resident on
  * the device. */
 int mds_problem_size(const mds_ctx *ctx, int64_t *pairs, int64_t *y_bytes);

@@ -81,6 +81,14 @@ SIGNATURES = {
     "mds_lpd_reset": (_int, [_vp]),
     "mds_hmc_collect": (_int, [_vp, _i64, _vp, _vp, _pi64, ctypes.POINTER(mds_hmc_stats)]),
     "mds_problem_size": (_int, [_vp, _pi64, _pi64]),
+    "mds_locality_order": (_int, [_i64, _i32, _vp, _vp]),
+    "mds_reorder": (_int, [_vp]),
+    "mds_get_order": (_int, [_vp, _vp]),
+    "mds_set_tail_cutoff": (_int, [_vp, _dbl]),
+    "mds_far_blocks": (_int, [_vp, _pi64, _pi64]),
+    "mds_set_tree_prior": (_int, [_vp, _i64, _vp, _vp, _vp, _vp, _dbl, _dbl]),
+    "mds_tree_prior": (_int, [_vp, _pdbl, _vp, _int, _int]),
+    "mds_rwmh": (_int, [_vp, _int, _dbl, _u64, _vp, _vp, _vp, _vp, _vp]),
     "mds_set_strip": (_int, [_vp, _i32]),
     "mds_get_strip": (_int, [_vp, _pi32]),
     "mds_time_pass": (_int, [_vp, _int, _pdbl]),

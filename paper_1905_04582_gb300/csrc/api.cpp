@@ -120,6 +120,26 @@ struct mds_ctx {
     bool y_owned = true;              // false for the chain contexts of a batch that share Y
     std::vector<Strip> strips_host;   // the strip list as uploaded (batched launches reuse it)
 
+    // locality order (mds_reorder): slot s of the tile layouts (Y, split
+    // locations, partial sums) holds item perm[s]; the state and every API
+    // array stay in the caller's item order
+    bool reordered = false;
+    std::vector<int32_t> perm_h, inv_h;   // [n_pad], pads map to themselves
+    int32_t *perm_d = nullptr, *inv_d = nullptr;
+    double tail_z = 8.0;                  // Phi-term cut-off z_c (0: off)
+    int32_t *far_part = nullptr;          // [strips][4 warps] far warp blocks of the last pass
+    size_t far_part_bytes = 0;
+
+    // phylogenetic Brownian-diffusion prior (mds_set_tree_prior)
+    bool tree_on = false;
+    TreeArgs tree{};                      // device pointers and constants (x set per launch)
+    double *tree_grad0 = nullptr;         // its gradient at the trajectory start (restored on reject)
+    cudaStream_t tree_stream = nullptr;   // the traversal runs here, beside the pair pass
+    cudaEvent_t tree_fork = nullptr, tree_join = nullptr;
+    int64_t rw_iter = 0;                  // random-walk proposals drawn so far (Philox counter)
+    std::vector<void *> tree_bufs;        // its device allocations
+
+
     std::string last_error = "no error";
 };
 
@@ -184,6 +204,7 @@ XState xstate(const mds_ctx *c) {
     xs.xcol = c->xcol;
     xs.split = c->split;
     xs.xmax_bits = c->xmax_bits;
+    xs.inv = c->reordered ? c->inv_d : nullptr;
     return xs;
 }
 
@@ -253,6 +274,13 @@ int build_strips(mds_ctx *c, int strip) {
         CHECK(dev_alloc_t(c, &c->row_part, rb));
         c->row_part_bytes = rb;
     }
+    const size_t fpb = v.size() * kPairWarps * sizeof(int32_t);
+    if (fpb > c->far_part_bytes) {
+        dev_free(c->far_part);
+        c->far_part = nullptr;
+        CHECK(dev_alloc_t(c, &c->far_part, fpb));
+        c->far_part_bytes = fpb;
+    }
     const size_t spb = v.size() * kScalarParts * elem(c);
     if (spb > c->scal_part_bytes) {
         dev_free(c->scal_part);
@@ -310,8 +338,13 @@ PairArgs pair_args(const mds_ctx *c) {
     a.col_part = c->col_part;
     a.scal_part = c->scal_part;
     a.tile_ho = c->ho_count > 0 ? c->tile_ho : nullptr;
+    a.perm = c->reordered ? c->perm_d : nullptr;
+    a.far_part = c->far_part;
     a.err = c->err;
     const double s = c->sigma;
+    // far warp blocks: every pair at z >= z_c (the squared-distance bound in
+    // FP32; an overflow to +inf only turns the shortcut off)
+    a.far_d2 = c->tail_z > 0.0 ? static_cast<float>((c->tail_z * s) * (c->tail_z * s)) : INFINITY;
     const double inv_sqrt_2pi = 0.39894228040143267794;
     double sk = 1.0;
     for (int k = 0; k < 4; ++k) {
@@ -339,6 +372,7 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.col_part = c->col_part;
     r.scal_part = c->scal_part;
     r.row_first_slot = c->row_first;
+    r.perm = c->reordered ? c->perm_d : nullptr;
     r.n_strips = c->n_strips;
     r.nt = static_cast<int32_t>(c->nt);
     r.n = c->n;
@@ -354,6 +388,7 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.xs = xstate(c);
     r.p = c->p;
     r.energy_part = c->e_end;
+    r.prior_grad = c->tree_on ? c->tree.grad : nullptr;
     r.err = c->err;
     return r;
 }
@@ -394,8 +429,27 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s) {
         }
         CHECK(record_prof(c, c->prof_a[pk], s));
     }
-    cudaError_t e = c->fp64 ? launch_pair_pass_f64(a, c->d, s) : launch_pair_pass_f32(a, c->d, s);
+    cudaError_t e = cudaSuccess;
+    if (c->tree_on) {
+        // the tree prior at the same x (for the kicks and the energies of
+        // HMC) on its own stream, concurrent with the pair pass; the reduction
+        // waits for both (a fork and a join, also inside captured graphs)
+        TreeArgs ta = c->tree;
+        ta.x = c->x;
+        ta.x_f64 = c->fp64;
+        ta.out = c->scal + kPriorLogp;
+        e = cudaEventRecord(c->tree_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->tree_stream, c->tree_fork, 0);
+        if (e == cudaSuccess) e = launch_tree_prior(ta, c->d, c->tree_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->tree_join, c->tree_stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior launch: %s", cudaGetErrorString(e));
+    }
+    e = c->fp64 ? launch_pair_pass_f64(a, c->d, s) : launch_pair_pass_f32(a, c->d, s);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
+    if (c->tree_on) {
+        e = cudaStreamWaitEvent(s, c->tree_join, 0);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior join: %s", cudaGetErrorString(e));
+    }
     if (c->profiling) {
         CHECK(record_prof(c, c->prof_b[pk], s));
         c->prof_used = pk + 1;
@@ -549,6 +603,8 @@ TrajArgs make_traj_args(const mds_ctx *c, int n_steps, double eps, int momentum_
     t.counters = c->counters;
     t.energy_part = c->e_start;
     t.drift = n_steps > 0 ? 1 : 0;
+    t.prior_grad = c->tree_on ? c->tree.grad : nullptr;
+    t.prior_grad0 = c->tree_on ? c->tree_grad0 : nullptr;
     return t;
 }
 
@@ -579,6 +635,8 @@ AcceptArgs make_accept_args(const mds_ctx *c, int n_steps, int metropolis, int u
     a.grad0 = static_cast<double *>(c->grad0);
     a.scal = c->scal;
     a.counters = c->counters;
+    a.prior_grad = c->tree_on ? c->tree.grad : nullptr;
+    a.prior_grad0 = c->tree_on ? c->tree_grad0 : nullptr;
     // per-iteration outputs only for Metropolis runs (their index is the
     // iteration within the current HMC call, below the output capacity)
     a.acc_out = metropolis ? acc_out : nullptr;
@@ -784,7 +842,91 @@ int drop_fold(mds_ctx *c, bool restore) {
     return MDS_OK;
 }
 
+// Re-pack Y from the current slot order into `order` (new slot -> item, over
+// n_pad slots, pads fixed) and make it the context's slot order.  `from_identity`:
+// Y is in the caller's item order (just ingested) rather than the current order.
+int repack_to(mds_ctx *c, const std::vector<int32_t> &order, bool from_identity) {
+    const int64_t np = c->n_pad;
+    std::vector<int32_t> map(np), inv(np);
+    for (int64_t s = 0; s < np; ++s) {
+        map[s] = (c->reordered && !from_identity) ? c->inv_h[order[s]] : order[s];
+        inv[order[s]] = static_cast<int32_t>(s);
+    }
+    int32_t *map_d = nullptr;
+    float *ny = nullptr;
+    CHECK(dev_alloc_t(c, &map_d, np * sizeof(int32_t)));
+    int st = dev_alloc_t(c, &ny, static_cast<size_t>(c->tiles) * kTileElems * sizeof(float));
+    if (st != MDS_OK) {
+        dev_free(map_d);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(map_d, map.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_repack(c->y, ny, map_d, c->n, static_cast<int32_t>(c->nt), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(map_d);
+    if (e != cudaSuccess) {
+        dev_free(ny);
+        return fail(c, MDS_ERR_CUDA, "reorder: %s", cudaGetErrorString(e));
+    }
+    dev_free(c->y);
+    c->y = ny;
+    if (!c->perm_d) {
+        CHECK(dev_alloc_t(c, &c->perm_d, np * sizeof(int32_t)));
+        CHECK(dev_alloc_t(c, &c->inv_d, np * sizeof(int32_t)));
+    }
+    CU(cudaMemcpyAsync(c->perm_d, order.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->inv_d, inv.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->perm_h = order;
+    c->inv_h = inv;
+    c->reordered = true;
+    c->gen++;  // the captured graph holds the old Y pointer
+    c->grad_valid = false;
+    return MDS_OK;
+}
+
+// Y was just ingested in the caller's order: bring it to the context's slot order.
+int apply_order(mds_ctx *c, const std::vector<int32_t> &order) { return repack_to(c, order, true); }
+
 }  // namespace
+
+// Recursive bisection: split the range along its widest coordinate (ties
+// broken by item index, so the order is the same on every host), at a
+// multiple of 64 items while the range is longer than one tile block, so
+// that every block of 64 slots is one spatially compact cell.
+namespace {
+void bisect(const double *x, int d, int32_t *idx, int64_t len) {
+    while (len > 2) {
+        int best = 0;
+        double width = -1.0;
+        for (int k = 0; k < d; ++k) {
+            double lo = x[static_cast<int64_t>(idx[0]) * d + k], hi = lo;
+            for (int64_t t = 1; t < len; ++t) {
+                const double v = x[static_cast<int64_t>(idx[t]) * d + k];
+                lo = std::min(lo, v);
+                hi = std::max(hi, v);
+            }
+            if (hi - lo > width) {
+                width = hi - lo;
+                best = k;
+            }
+        }
+        const int64_t h = len > kTile ? std::min<int64_t>(len - 1, (len / 2 + kTile - 1) / kTile * kTile) : len / 2;
+        std::nth_element(idx, idx + h, idx + len, [x, d, best](int32_t a, int32_t b) {
+            const double va = x[static_cast<int64_t>(a) * d + best], vb = x[static_cast<int64_t>(b) * d + best];
+            return va < vb || (va == vb && a < b);
+        });
+        bisect(x, d, idx, h);
+        idx += h;
+        len -= h;
+    }
+}
+}  // namespace
+
+void mds::locality_order(int64_t n, int d, const double *x, int32_t *perm) {
+    for (int64_t s = 0; s < n; ++s) perm[s] = static_cast<int32_t>(s);
+    bisect(x, d, perm, n);
+}
 
 void mds::set_thread_error(const char *fmt, ...) {
     char buf[512];
@@ -905,12 +1047,19 @@ int mds_destroy(mds_ctx *c) {
                     c->split,    c->xmax_bits, c->grad,     c->grad0,    c->col_part,  c->row_part,
                     c->scal_part, c->strips,  c->row_first, c->scal,     c->counters,  c->err,
                     c->bad,      c->e_start,  c->e_end,     c->stage,    c->p_inj,     c->u_inj,
-                    c->acc_out,  c->dh_out};
+                    c->acc_out,  c->dh_out,    c->perm_d,    c->inv_d,     c->far_part};
     for (void *b : bufs) dev_free(b);
     void *ho_bufs[] = {c->ho_off, c->ho_pairs, c->ho_y, c->tile_ho, c->lse_m, c->lse_s, c->lpd_part, c->sigma_draws};
     for (void *b : ho_bufs) dev_free(b);
+    for (void *b : c->tree_bufs) dev_free(b);
     if (c->host_stage) cudaFreeHost(c->host_stage);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->tree_stream) {
+        cudaStreamSynchronize(c->tree_stream);
+        cudaStreamDestroy(c->tree_stream);
+    }
+    if (c->tree_fork) cudaEventDestroy(c->tree_fork);
+    if (c->tree_join) cudaEventDestroy(c->tree_join);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (cudaEvent_t e : c->prof_a) cudaEventDestroy(e);
@@ -1007,6 +1156,7 @@ int mds_set_data(mds_ctx *c, const void *y, int dtype, int layout, int64_t ld, i
                     bad / static_cast<unsigned long long>(n), bad % static_cast<unsigned long long>(n));
     }
     if (h) return check_device_err(c, "set_data");
+    if (c->reordered) CHECK(apply_order(c, c->perm_h));  // ingest wrote the caller's order
     c->have_data = true;
     return MDS_OK;
 }
@@ -1233,9 +1383,12 @@ int mds_set_heldout(mds_ctx *c, const int64_t *pairs, int64_t n_pairs) {
             if (packed_row_start(mid, n) <= key[k]) lo = mid; else hi = mid - 1;
         }
         const int64_t i = lo, j = key[k] - packed_row_start(i, n) + i + 1;
-        const int64_t I = i / kTile, J = j / kTile;
-        off[k] = tile_index(I, J, c->nt) * kTileElems + tile_offset(static_cast<int>(i - I * kTile),
-                                                                    static_cast<int>(j - J * kTile));
+        // the pair's place in the tile layout: by slot (upper triangle in slot order)
+        int64_t si = c->reordered ? c->inv_h[i] : i, sj = c->reordered ? c->inv_h[j] : j;
+        if (si > sj) std::swap(si, sj);
+        const int64_t I = si / kTile, J = sj / kTile;
+        off[k] = tile_index(I, J, c->nt) * kTileElems + tile_offset(static_cast<int>(si - I * kTile),
+                                                                    static_cast<int>(sj - J * kTile));
         pr[k] = make_int2(static_cast<int>(i), static_cast<int>(j));
     }
     if (!c->tile_ho) {
@@ -1382,6 +1535,482 @@ int mds_sigma_mh(mds_ctx *c, int n_iter, double step, double shape, double rate,
         }
         if (accepted) accepted[t] = acc;
     }
+    return MDS_OK;
+}
+
+int mds_locality_order(int64_t n, int32_t d, const double *x, int32_t *perm) {
+    if (n < 1 || n > INT32_MAX || d < 1 || d > 8 || !x || !perm) {
+        mds::set_thread_error("mds_locality_order: need 1 <= n < 2^31, 1 <= d <= 8, x and perm");
+        return MDS_ERR_INVALID_ARG;
+    }
+    for (int64_t e = 0; e < n * d; ++e)
+        if (!std::isfinite(x[e])) {
+            mds::set_thread_error("mds_locality_order: x[%lld] is not finite", (long long)e);
+            return MDS_ERR_INVALID_ARG;
+        }
+    mds::locality_order(n, d, x, perm);
+    return MDS_OK;
+}
+
+int mds_reorder(mds_ctx *c) {
+    CHECK(check_ctx(c));
+    if (!c->y_owned) return fail(c, MDS_ERR_STATE, "the chains of a batch share Y and cannot be reordered");
+    if (!c->have_data || !c->have_x) return fail(c, MDS_ERR_STATE, "mds_reorder needs data and locations");
+    if (c->ho_count > 0)
+        return fail(c, MDS_ERR_STATE, "a cross-validation fold is set: call mds_reorder before mds_set_heldout");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    const int64_t n = c->n, np = c->n_pad;
+    std::vector<double> xh(static_cast<size_t>(n * c->d));
+    CHECK(copy_out(c, c->x, c->fp64 ? 1 : 0, xh.data(), MDS_F64, MDS_HOST, n * c->d));
+    std::vector<int32_t> order(static_cast<size_t>(np));
+    locality_order(n, c->d, xh.data(), order.data());
+    for (int64_t s = n; s < np; ++s) order[s] = static_cast<int32_t>(s);
+    CHECK(repack_to(c, order, false));
+    if (!c->fp64) {
+        // split locations at their new slots
+        cudaError_t e = launch_resplit(xstate(c), np, c->d, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "reorder: %s", cudaGetErrorString(e));
+    }
+    return MDS_OK;
+}
+
+int mds_far_blocks(mds_ctx *c, int64_t *far, int64_t *total) {
+    CHECK(check_ctx(c));
+    if (!far || !total) return fail(c, MDS_ERR_INVALID_ARG, "far and total must not be NULL");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    CHECK(ready(c));
+    CHECK(autotune(c));  // so that the counted pass is the only one
+    CHECK(evaluate(c));
+    int64_t v = 0;
+    if (!c->fp64) {
+        std::vector<int32_t> parts(static_cast<size_t>(c->n_strips) * kPairWarps);
+        CU(cudaMemcpyAsync(parts.data(), c->far_part, parts.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        for (int32_t p : parts) v += p;
+    }
+    *far = v;
+    *total = c->tiles * kPairWarps * 2;  // column pairs of the 4 warps per tile
+    return MDS_OK;
+}
+
+int mds_get_order(const mds_ctx *c, int32_t *perm) {
+    if (!c || !perm) return MDS_ERR_INVALID_ARG;
+    for (int64_t s = 0; s < c->n; ++s) perm[s] = c->reordered ? c->perm_h[s] : static_cast<int32_t>(s);
+    return MDS_OK;
+}
+
+int mds_set_tail_cutoff(mds_ctx *c, double z) {
+    CHECK(check_ctx(c));
+    if (!(z == 0.0 || z >= 8.0) || !std::isfinite(z))
+        return fail(c, MDS_ERR_INVALID_ARG, "the Phi cut-off must be 0 (off) or a finite z >= 8, got %g", z);
+    if (z != c->tail_z) {
+        c->tail_z = z;
+        c->gen++;
+    }
+    return MDS_OK;
+}
+
+int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const double *length,
+                       const double *sigma_mat, const double *mu, double tau0, double tau_u) {
+    CHECK(check_ctx(c));
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    const int64_t n = c->n;
+    const int d = c->d;
+    auto drop = [c]() {
+        for (void *b : c->tree_bufs) dev_free(b);
+        c->tree_bufs.clear();
+        c->tree = TreeArgs{};
+        c->tree_grad0 = nullptr;
+        const double zero[2] = {0.0, 0.0};
+        cudaMemcpyAsync(c->scal + kPriorLogp, zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        if (c->tree_on) c->gen++;
+        c->tree_on = false;
+        c->grad_valid = false;
+    };
+    if (n_nodes == 0 || !parent) {
+        drop();
+        return MDS_OK;
+    }
+    if (!length || !sigma_mat || !mu) return fail(c, MDS_ERR_INVALID_ARG, "length, Sigma and mu are required");
+    if (n_nodes < n || n_nodes > 2 * n - 1)
+        return fail(c, MDS_ERR_INVALID_ARG, "a binary forest over N = %lld tips has N to 2N-1 nodes, got %lld",
+                    (long long)n, (long long)n_nodes);
+    if (!(tau0 > 0.0) || !std::isfinite(tau0) || !(tau_u > 0.0) || !std::isfinite(tau_u))
+        return fail(c, MDS_ERR_INVALID_ARG, "tau0 and tau_u must be finite and > 0");
+    // ---- the forest
+    std::vector<int32_t> c0(n_nodes, -1), c1(n_nodes, -1);
+    for (int64_t k = 0; k < n_nodes; ++k) {
+        const int64_t p = parent[k];
+        if (p == -1) continue;
+        if (p < n || p >= n_nodes)
+            return fail(c, MDS_ERR_INVALID_ARG, "node %lld: parent %lld is not an internal node", (long long)k,
+                        (long long)p);
+        if (!(length[k] > 0.0) || !std::isfinite(length[k]))
+            return fail(c, MDS_ERR_INVALID_ARG, "node %lld: branch length must be finite and > 0", (long long)k);
+        if (c0[p] < 0) c0[p] = static_cast<int32_t>(k);
+        else if (c1[p] < 0) c1[p] = static_cast<int32_t>(k);
+        else return fail(c, MDS_ERR_INVALID_ARG, "node %lld has more than two children", (long long)p);
+    }
+    for (int64_t k = n; k < n_nodes; ++k)
+        if (c1[k] < 0) return fail(c, MDS_ERR_INVALID_ARG, "internal node %lld needs two children", (long long)k);
+    // heights in post-order from every root (an iterative DFS); a node seen
+    // twice or never means a cycle
+    std::vector<int32_t> height(n_nodes, -1), roots, lone;
+    std::vector<int32_t> order;  // internal nodes, children before parents
+    for (int64_t r = 0; r < n_nodes; ++r) {
+        if (parent[r] != -1) continue;
+        if (r < n) {
+            lone.push_back(static_cast<int32_t>(r));
+            height[r] = 0;
+            continue;
+        }
+        roots.push_back(static_cast<int32_t>(r));
+        std::vector<std::pair<int32_t, int>> st{{static_cast<int32_t>(r), 0}};
+        while (!st.empty()) {
+            auto &top = st.back();
+            const int32_t u = top.first;
+            if (u < n) {
+                height[u] = 0;
+                st.pop_back();
+                continue;
+            }
+            if (top.second < 2) {
+                const int32_t ch = top.second == 0 ? c0[u] : c1[u];
+                top.second++;
+                if (height[ch] != -1 || static_cast<int64_t>(st.size()) > n_nodes)
+                    return fail(c, MDS_ERR_INVALID_ARG, "the parent links do not form a forest");
+                st.push_back({ch, 0});
+                continue;
+            }
+            height[u] = 1 + std::max(height[c0[u]], height[c1[u]]);
+            order.push_back(u);
+            st.pop_back();
+        }
+    }
+    for (int64_t k = 0; k < n_nodes; ++k)
+        if (height[k] < 0) return fail(c, MDS_ERR_INVALID_ARG, "node %lld is not connected to a root", (long long)k);
+    // ---- Sigma: symmetric positive definite; its inverse and log-determinant
+    std::vector<double> L(d * d, 0.0), sinv(d * d, 0.0);
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            const double a = sigma_mat[i * d + j], b = sigma_mat[j * d + i];
+            if (!std::isfinite(a) || std::fabs(a - b) > 1e-12 * (std::fabs(a) + std::fabs(b)))
+                return fail(c, MDS_ERR_INVALID_ARG, "Sigma must be finite and symmetric");
+        }
+    double logdet = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double s = sigma_mat[j * d + j];
+        for (int k = 0; k < j; ++k) s -= L[j * d + k] * L[j * d + k];
+        if (!(s > 0.0)) return fail(c, MDS_ERR_INVALID_ARG, "Sigma is not positive definite");
+        L[j * d + j] = std::sqrt(s);
+        logdet += std::log(s);
+        for (int i = j + 1; i < d; ++i) {
+            double t = sigma_mat[i * d + j];
+            for (int k = 0; k < j; ++k) t -= L[i * d + k] * L[j * d + k];
+            L[i * d + j] = t / L[j * d + j];
+        }
+    }
+    for (int col = 0; col < d; ++col) {  // Sigma^-1 = L^-T L^-1, column by column
+        std::vector<double> y(d, 0.0), z(d, 0.0);
+        for (int i = 0; i < d; ++i) {
+            double t = i == col ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= L[i * d + k] * y[k];
+            y[i] = t / L[i * d + i];
+        }
+        for (int i = d - 1; i >= 0; --i) {
+            double t = y[i];
+            for (int k = i + 1; k < d; ++k) t -= L[k * d + i] * z[k];
+            z[i] = t / L[i * d + i];
+        }
+        for (int i = 0; i < d; ++i) sinv[i * d + col] = z[i];
+    }
+    for (int k = 0; k < d; ++k)
+        if (!std::isfinite(mu[k])) return fail(c, MDS_ERR_INVALID_ARG, "mu must be finite");
+    // ---- message variances (they depend on the tree alone) and the weights
+    const double log2pi = 1.8378770664093454836;
+    const double hd = 0.5 * d;
+    std::vector<double> up_v(n_nodes, 0.0), dn_v(n_nodes, 0.0);
+    // per node: weights (up: children before parents; down: parents first)
+    struct W {
+        double alpha = 0, cinv = 0, beta0 = 0, beta1 = 0, g0 = 0, g1 = 0;
+    };
+    std::vector<W> wt(n_nodes);
+    double cst = -0.5 * static_cast<double>(n) * logdet;
+    for (int32_t k : order) {
+        const double va = up_v[c0[k]] + length[c0[k]], vb = up_v[c1[k]] + length[c1[k]], sv = va + vb;
+        wt[k].alpha = vb / sv;
+        wt[k].cinv = 1.0 / sv;
+        up_v[k] = va * vb / sv;
+        cst -= hd * (log2pi + std::log(sv));
+    }
+    std::vector<double> root_cinv;
+    for (int32_t r : roots) {
+        const double sv = up_v[r] + tau0;
+        root_cinv.push_back(1.0 / sv);
+        cst -= hd * (log2pi + std::log(sv));
+        dn_v[r] = tau0;
+    }
+    cst -= hd * (log2pi + std::log(tau_u)) * static_cast<double>(lone.size());
+    for (auto it = order.rbegin(); it != order.rend(); ++it) {  // parents before children
+        const int32_t k = *it;
+        const double vk = dn_v[k];
+        for (int side = 0; side < 2; ++side) {
+            const int32_t ch = side == 0 ? c0[k] : c1[k], sib = side == 0 ? c1[k] : c0[k];
+            const double vs = up_v[sib] + length[sib];
+            const double beta = vs / (vk + vs);
+            const double vc = vk * vs / (vk + vs) + length[ch];
+            const double g = ch < n ? 1.0 / vc : 0.0;
+            if (side == 0) {
+                wt[k].beta0 = beta;
+                wt[k].g0 = g;
+            } else {
+                wt[k].beta1 = beta;
+                wt[k].g1 = g;
+            }
+            if (ch >= n) dn_v[ch] = vc;
+        }
+    }
+    // ---- level schedule: tree by tree (roots in id order), internal nodes by
+    // (height, id), the root last; children referenced by their index within
+    // the tree (internal) or in the tree's tip list (tips)
+    std::vector<int32_t> tree_of(n_nodes, -1);
+    for (size_t t = 0; t < roots.size(); ++t) tree_of[roots[t]] = static_cast<int32_t>(t);
+    std::vector<std::vector<int32_t>> members(roots.size());
+    for (auto it = order.rbegin(); it != order.rend(); ++it) {  // parents first: a child inherits its tree
+        const int32_t k = *it;
+        if (tree_of[k] < 0) tree_of[k] = tree_of[parent[k]];
+        members[tree_of[k]].push_back(k);
+    }
+    std::vector<TreeNode> nodes;
+    std::vector<int32_t> node_off{0}, tip_items, tip_off{0}, lv_start, tree_lv;
+    std::vector<int32_t> local(n_nodes, -1);
+    int64_t max_fp = 0, scr_total = 0;
+    std::vector<int64_t> scr_off;
+    for (size_t t = 0; t < roots.size(); ++t) {
+        auto &mem = members[t];
+        std::sort(mem.begin(), mem.end(), [&](int32_t a, int32_t b) {
+            return height[a] < height[b] || (height[a] == height[b] && a < b);
+        });
+        for (size_t q = 0; q < mem.size(); ++q) local[mem[q]] = static_cast<int32_t>(q);
+        tree_lv.push_back(static_cast<int32_t>(lv_start.size()));
+        const int32_t tip0 = static_cast<int32_t>(tip_items.size());
+        int prev = -1;
+        for (size_t q = 0; q < mem.size(); ++q) {
+            const int32_t k = mem[q];
+            if (height[k] != prev) {
+                lv_start.push_back(static_cast<int32_t>(q));
+                prev = height[k];
+            }
+            TreeNode r{};
+            int32_t ref[2];
+            for (int side = 0; side < 2; ++side) {
+                const int32_t ch = side == 0 ? c0[k] : c1[k];
+                if (ch >= n) {
+                    ref[side] = local[ch];
+                } else {
+                    ref[side] = -(static_cast<int32_t>(tip_items.size()) - tip0 + 1);
+                    tip_items.push_back(ch);
+                }
+            }
+            r.c0 = ref[0];
+            r.c1 = ref[1];
+            r.alpha = wt[k].alpha;
+            r.cinv = wt[k].cinv;
+            r.beta0 = wt[k].beta0;
+            r.beta1 = wt[k].beta1;
+            r.g0 = wt[k].g0;
+            r.g1 = wt[k].g1;
+            nodes.push_back(r);
+        }
+        node_off.push_back(static_cast<int32_t>(nodes.size()));
+        tip_off.push_back(static_cast<int32_t>(tip_items.size()));
+        const int64_t m = static_cast<int64_t>(mem.size()), kt = static_cast<int64_t>(tip_items.size()) - tip0;
+        const int64_t fp = m * static_cast<int64_t>(sizeof(TreeNode)) + (2 * m + kt) * d * 8;
+        max_fp = std::max(max_fp, fp);
+        scr_off.push_back(scr_total);
+        scr_total += (2 * m + kt) * d;
+    }
+    tree_lv.push_back(static_cast<int32_t>(lv_start.size()));
+    // ---- device copies
+    drop();
+    if (!c->tree_stream) {
+        CU(cudaStreamCreateWithFlags(&c->tree_stream, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&c->tree_fork, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&c->tree_join, cudaEventDisableTiming));
+    }
+    TreeArgs ta{};
+    auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+        void *p = nullptr;
+        int st = dev_alloc(c, &p, std::max<size_t>(bytes, 16));
+        if (st != MDS_OK) return st;
+        c->tree_bufs.push_back(p);
+        if (src && bytes) {
+            cudaError_t e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior upload: %s", cudaGetErrorString(e));
+        }
+        *dst = p;
+        return MDS_OK;
+    };
+    void *p = nullptr;
+    CHECK(up(&p, nodes.data(), nodes.size() * sizeof(TreeNode)));
+    ta.nodes = static_cast<const TreeNode *>(p);
+    CHECK(up(&p, lv_start.data(), lv_start.size() * sizeof(int32_t)));
+    ta.lv_start = static_cast<const int32_t *>(p);
+    CHECK(up(&p, tree_lv.data(), tree_lv.size() * sizeof(int32_t)));
+    ta.tree_lv = static_cast<const int32_t *>(p);
+    CHECK(up(&p, root_cinv.data(), root_cinv.size() * sizeof(double)));
+    ta.root_cinv = static_cast<const double *>(p);
+    CHECK(up(&p, lone.data(), lone.size() * sizeof(int32_t)));
+    ta.lone = static_cast<const int32_t *>(p);
+    CHECK(up(&p, sinv.data(), sinv.size() * sizeof(double)));
+    ta.sigma_inv = static_cast<const double *>(p);
+    CHECK(up(&p, mu, d * sizeof(double)));
+    ta.mu = static_cast<const double *>(p);
+    CHECK(up(&p, node_off.data(), node_off.size() * sizeof(int32_t)));
+    ta.node_off = static_cast<const int32_t *>(p);
+    CHECK(up(&p, tip_items.data(), tip_items.size() * sizeof(int32_t)));
+    ta.tip_items = static_cast<const int32_t *>(p);
+    CHECK(up(&p, tip_off.data(), tip_off.size() * sizeof(int32_t)));
+    ta.tip_off = static_cast<const int32_t *>(p);
+    // messages and tip locations: in shared memory when the largest tree fits
+    // (kTreeSmemMax bytes per CTA), else in global scratch
+    constexpr int64_t kTreeSmemMax = 200 * 1024;
+    if (max_fp > 0 && max_fp <= kTreeSmemMax) {
+        ta.smem_bytes = static_cast<int32_t>((max_fp + 15) / 16 * 16);
+    } else {
+        ta.smem_bytes = 0;
+        CHECK(up(&p, nullptr, static_cast<size_t>(std::max<int64_t>(scr_total, 1)) * sizeof(double)));
+        ta.scratch = static_cast<double *>(p);
+        CHECK(up(&p, scr_off.data(), scr_off.size() * sizeof(int64_t)));
+        ta.scr_off = static_cast<const int64_t *>(p);
+    }
+    CHECK(up(&p, nullptr, static_cast<size_t>(c->n_pad) * d * sizeof(double)));
+    ta.grad = static_cast<double *>(p);
+    CHECK(up(&p, nullptr, static_cast<size_t>(c->n_pad) * d * sizeof(double)));
+    c->tree_grad0 = static_cast<double *>(p);
+    CHECK(up(&p, nullptr, (roots.size() + 2) * sizeof(double)));
+    ta.part = static_cast<double *>(p);
+    ta.out = ta.part + roots.size() + 1;
+    CU(cudaMemsetAsync(ta.grad, 0, static_cast<size_t>(c->n_pad) * d * sizeof(double), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    ta.n = n;
+    ta.n_trees = static_cast<int32_t>(roots.size());
+    ta.n_lone = static_cast<int32_t>(lone.size());
+    ta.tau_u = tau_u;
+    ta.const_term = cst;
+    c->tree = ta;
+    c->tree_on = true;
+    c->gen++;
+    c->grad_valid = false;
+    return MDS_OK;
+}
+
+int mds_tree_prior(mds_ctx *c, double *logp, void *grad, int dtype, int where) {
+    CHECK(check_ctx(c));
+    if (!c->tree_on) return fail(c, MDS_ERR_STATE, "no tree prior: call mds_set_tree_prior first");
+    if (!c->have_x) return fail(c, MDS_ERR_STATE, "no locations set");
+    if (grad) CHECK(valid_enums(c, dtype, where));
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    TreeArgs ta = c->tree;
+    ta.x = c->x;
+    ta.x_f64 = c->fp64;
+    cudaError_t e = launch_tree_prior(ta, c->d, c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior: %s", cudaGetErrorString(e));
+    if (grad) CHECK(copy_out(c, ta.grad, 1, grad, dtype, where, c->n * c->d));
+    if (logp) {
+        CU(cudaMemcpyAsync(logp, ta.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return MDS_OK;
+}
+
+int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *items, const double *z_all,
+             const double *u_all, int32_t *accepted, double *dlogpi) {
+    CHECK(check_ctx(c));
+    if (n_prop < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_prop must be >= 0");
+    if (!(step > 0.0) || !std::isfinite(step)) return fail(c, MDS_ERR_INVALID_ARG, "step must be finite and > 0");
+    const bool inj = items || z_all || u_all;
+    if (inj && !(items && z_all && u_all))
+        return fail(c, MDS_ERR_INVALID_ARG, "inject all of items, z and u, or none");
+    CHECK(ready(c));
+    if (c->tree_on)
+        return fail(c, MDS_ERR_STATE, "the random-walk sampler supports the isotropic prior only (no tree prior)");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    if (n_prop == 0) return MDS_OK;
+    const int d = c->d;
+    if (inj)
+        for (int t = 0; t < n_prop; ++t)
+            if (items[t] < 0 || items[t] >= c->n)
+                return fail(c, MDS_ERR_INVALID_ARG, "items[%d] = %lld is not an item", t, (long long)items[t]);
+    // device copies of the draws and the outputs (freed below)
+    std::vector<void *> tmp;
+    auto alloc = [&](void **p, size_t bytes) -> int {
+        int st = dev_alloc(c, p, std::max<size_t>(bytes, 16));
+        if (st == MDS_OK) tmp.push_back(*p);
+        return st;
+    };
+    auto cleanup = [&](int st) {
+        for (void *p : tmp) dev_free(p);
+        return st;
+    };
+    RwmhArgs a{};
+    void *p = nullptr;
+    if (inj) {
+        int st;
+        if ((st = alloc(&p, n_prop * sizeof(int64_t)))) return cleanup(st);
+        a.items = static_cast<const int64_t *>(p);
+        cudaMemcpyAsync(p, items, n_prop * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+        if ((st = alloc(&p, static_cast<size_t>(n_prop) * d * sizeof(double)))) return cleanup(st);
+        a.z = static_cast<const double *>(p);
+        cudaMemcpyAsync(p, z_all, static_cast<size_t>(n_prop) * d * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if ((st = alloc(&p, n_prop * sizeof(double)))) return cleanup(st);
+        a.u = static_cast<const double *>(p);
+        cudaMemcpyAsync(p, u_all, n_prop * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    }
+    int st;
+    if ((st = alloc(&p, n_prop * sizeof(int32_t)))) return cleanup(st);
+    a.acc_out = static_cast<int32_t *>(p);
+    if ((st = alloc(&p, n_prop * sizeof(double)))) return cleanup(st);
+    a.dl_out = static_cast<double *>(p);
+    a.n = c->n;
+    a.y = c->y;
+    a.nt = static_cast<int32_t>(c->nt);
+    a.inv = c->reordered ? c->inv_d : nullptr;
+    a.x = c->x;
+    a.fp64 = c->fp64;
+    a.sigma = c->sigma;
+    a.lambda = c->lambda;
+    a.step = step;
+    a.n_prop = n_prop;
+    a.seed = seed;
+    a.chain = 0;
+    a.iter0 = c->rw_iter;
+    a.xmax_bits = c->fp64 ? nullptr : c->xmax_bits;
+    a.err = c->err;
+    cudaError_t e = launch_rwmh(a, d, c->stream);
+    if (e != cudaSuccess) return cleanup(fail(c, MDS_ERR_CUDA, "rwmh: %s", cudaGetErrorString(e)));
+    std::vector<int32_t> acc(n_prop);
+    std::vector<double> dl(n_prop);
+    e = cudaMemcpyAsync(acc.data(), a.acc_out, n_prop * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dl.data(), a.dl_out, n_prop * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup(MDS_OK);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "rwmh: %s", cudaGetErrorString(e));
+    if (!inj) c->rw_iter += n_prop;
+    c->grad_valid = false;
+    CHECK(check_device_err(c, "rwmh"));
+    if (!c->fp64) CHECK(set_split_from_xmax(c));  // the split layouts follow the moved items
+    if (accepted) std::memcpy(accepted, acc.data(), n_prop * sizeof(int32_t));
+    if (dlogpi) std::memcpy(dlogpi, dl.data(), n_prop * sizeof(double));
     return MDS_OK;
 }
 

@@ -109,7 +109,12 @@ struct PairArgs {
     void *col_part;          // [tiles][64][D]     (float / double)
     void *scal_part;         // [n_strips][kScalarParts] (float / double)
     const unsigned char *tile_ho;  // [tiles] 1 where a tile holds a held-out pair (y < 0), or null
+    const int32_t *perm;     // FP64: item at slot s (locality order, mds_reorder), or null (identity)
+    int32_t *far_part;       // FP32C: per strip and warp, the warp blocks (64 x 8 pairs) of the last
+                             // pass that skipped the Phi terms (diagnostics), or null
     unsigned *err;           // device error word (see ErrBits)
+    float far_d2;            // FP32C: (z_c sigma)^2; warp blocks at least this far apart skip the Phi
+                             // terms (+inf: never)
     // FP32C constants (sigma folded in on the host), each duplicated {c, c}
     // so that it is a ready operand of the packed f32x2 instructions
     float2 mp[4];            // -P(delta/sigma)/sqrt(2 pi) coefficients in powers of delta
@@ -195,6 +200,8 @@ enum Scalar : int {
     kDSigma0,
     kLogLikEnd,     // L at the end of the pass just reduced (read by the end kernel)
     kLastDH,        // H(end) - H(start) of the last trajectory
+    kPriorLogp,     // log p(X) of the tree prior at the current x (0 without one)
+    kPriorLogp0,    // the same at the trajectory start
     kScalars
 };
 
@@ -219,7 +226,8 @@ enum ReduceMode : int {
 
 // Location state shared by the update kernels.
 struct XState {
-    void *x;                  // [n_pad][D] (float / double): the state
+    void *x;                  // [n_pad][D] (float / double): the state, in the caller's item order
+    const int32_t *inv;       // slot of item k in the tile layouts (locality order), or null (identity)
     float4 *xrow;             // FP32C split layouts (null on the FP64 path)
     float4 *xcol;
     Split *split;             // FP32C quantum (device; grown by the end-of-trajectory reduction)
@@ -231,6 +239,7 @@ struct ReduceArgs {
     const void *col_part;
     const void *scal_part;
     const int32_t *row_first_slot;  // [nt + 1]
+    const int32_t *perm;      // item at slot s of the tile layouts, or null (identity)
     int32_t n_strips;
     int32_t nt;
     int64_t n;
@@ -246,6 +255,7 @@ struct ReduceArgs {
     XState xs;
     void *p;                  // [N][D]
     double *energy_part;      // [nt * kReduceQuarters][2] (kModeHalfKick): kinetic, ||x||^2
+    const double *prior_grad; // [N][D] d log p / dX of the tree prior at x (added to the kicks), or null
     unsigned *err;
 };
 
@@ -275,6 +285,8 @@ struct TrajArgs {
     int64_t *counters;
     double *energy_part;      // [gridDim][2]: kinetic energy, ||x||^2 at the start
     int32_t drift;            // 1: take the first half kick + drift (n_steps > 0)
+    const double *prior_grad; // tree prior gradient at x (or null); saved into prior_grad0
+    double *prior_grad0;
 };
 cudaError_t launch_traj_start(const TrajArgs &a, int *grid_out, cudaStream_t s);
 
@@ -301,6 +313,8 @@ struct AcceptArgs {
     const double *grad0;
     double *scal;
     int64_t *counters;
+    double *prior_grad;       // tree prior gradient (restored from prior_grad0 on reject), or null
+    const double *prior_grad0;
     int32_t *acc_out;         // [out_cap] per-iteration decision (optional)
     double *dh_out;           // [out_cap] per-iteration H1 - H0 (optional)
     int64_t out_cap;          // entries of acc_out / dh_out
@@ -317,6 +331,75 @@ cudaError_t launch_reduce_batch(const ReduceArgs *cfg, const int2 *jobs, int n_j
 int traj_start_grid(int64_t n, int d);
 cudaError_t launch_traj_start_batch(const TrajArgs *cfg, int n_chains, int max_grid, int d, cudaStream_t s);
 cudaError_t launch_traj_end_batch(const AcceptArgs *cfg, int n_chains, int64_t max_nd, int d, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Phylogenetic Brownian-diffusion prior (tree_prior.cu).  Internal node
+// records, per tree in post-order level order (leaves' parents first, the
+// root last); the weights come from the message variances, which depend on
+// the tree alone and are computed on the host.
+// ---------------------------------------------------------------------------
+struct TreeNode {
+    int32_t c0, c1;          // children: >= 0 an internal node (its record index within the tree),
+                             // < 0 the tree's tip -(c + 1) (index into the tree's tip list)
+    double alpha;            // upward mean: m_k = m_c1 + alpha (m_c0 - m_c1)
+    double cinv;             // 1 / (variance of the contrast m_c0 - m_c1)
+    double beta0, beta1;     // downward mean of child i: m_s + beta_i (m_k - m_s), s its sibling
+    double g0, g1;           // 1 / (downward variance) of a tip child (gradient scale)
+};
+
+struct TreeArgs {
+    int64_t n;               // tips (items)
+    const void *x;           // locations [N][D] (float or double, item order)
+    bool x_f64;
+    int32_t n_trees;
+    const TreeNode *nodes;   // tree t's internal nodes at [node_off[t], node_off[t+1]), by level, root last
+    const int32_t *node_off; // [n_trees + 1]
+    const int32_t *tip_items;// tree t's tips (their items) at [tip_off[t], tip_off[t+1])
+    const int32_t *tip_off;  // [n_trees + 1]
+    const int32_t *lv_start; // each level's first record, relative to its tree (a tree's last level
+                             // ends at its node count)
+    const int32_t *tree_lv;  // first level of each tree (+ end)
+    const double *root_cinv; // per tree: 1 / (v_root + tau0)
+    int32_t n_lone;
+    const int32_t *lone;     // unsequenced items (tips that are roots)
+    double tau_u;
+    const double *sigma_inv; // D x D
+    const double *mu;        // D
+    double const_term;       // sum of the log-determinant and 2 pi terms
+    int32_t smem_bytes;      // > 0: a tree's CTA keeps its records, messages and tips in shared memory
+    double *scratch;         // otherwise: per tree (2 m_t + k_t) x D doubles at scr_off[t]
+    const int64_t *scr_off;
+    double *grad;            // [N][D] d log p / dX (out)
+    double *part;            // [n_trees + 1] per-CTA sums (scratch)
+    double *out;             // log p (out, device scalar)
+};
+cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Single-item random-walk Metropolis (rwmh.cu): one CTA runs the proposals
+// in order.
+// ---------------------------------------------------------------------------
+struct RwmhArgs {
+    int64_t n;
+    const float *y;           // tile-packed Y
+    int32_t nt;
+    const int32_t *inv;       // slot of each item (locality order), or null
+    void *x;                  // [N][D] state (float or double), updated in place
+    bool fp64;
+    double sigma, lambda, step;
+    int32_t n_prop;
+    const int64_t *items;     // injected draws (device) or null: Philox
+    const double *z;          // [n_prop][D]
+    const double *u;          // [n_prop]
+    uint64_t seed;
+    uint32_t chain;
+    int64_t iter0;            // Philox counter of the first proposal
+    int32_t *acc_out;         // [n_prop] decisions (optional)
+    double *dl_out;           // [n_prop] log-target differences (optional)
+    unsigned *xmax_bits;      // FP32C running max |x| (atomicMax), or null
+    unsigned *err;
+};
+cudaError_t launch_rwmh(const RwmhArgs &a, int d, cudaStream_t s);
 
 // Y ingest: rows [r0, r1) of the caller's Y (full or packed layout; the
 // pointer addresses row r0) into the tile-packed FP32 layout.  Entries read
@@ -342,6 +425,14 @@ cudaError_t launch_set_x(const void *src, bool src_f64, int64_t n, int64_t n_pad
                          unsigned *err, cudaStream_t s);
 // Recompute the split layouts of the FP32C path from x (after a quantum change).
 cudaError_t launch_resplit(const XState &xs, int64_t n_pad, int d, cudaStream_t s);
+// Re-pack the tile-packed Y for a new slot order: the pair at new slots
+// (s, t) comes from old slots (map[s], map[t]) of old_y (only s < t < n is
+// stored; every other element is written 0).
+cudaError_t launch_repack(const float *old_y, float *new_y, const int32_t *map, int64_t n, int32_t nt, cudaStream_t s);
+// Host: locality order of N points in D dimensions (recursive bisection of
+// the widest coordinate, halves cut at multiples of 64 items): perm[s] is the
+// item placed at slot s.
+void locality_order(int64_t n, int d, const double *x, int32_t *perm);
 // max |x| over the state (float bits into *out via atomicMax; *out must be 0).
 cudaError_t launch_xmax(const void *x, bool fp64, int64_t count, unsigned *out, cudaStream_t s);
 // Copy / convert an array between element types (device to device).

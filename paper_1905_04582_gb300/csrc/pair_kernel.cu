@@ -55,11 +55,13 @@ struct F32Layout {
     static constexpr int kStageBytes = (kWarpTileElems * 4 + kXjBytes + 127) / 128 * 128;
     static constexpr int kRingOffset = (kXiBytes + 127) / 128 * 128;
     static constexpr int kBarOffset = kRingOffset + kPairWarps * kStages * kStageBytes;
+    // each warp's copy of the row box (2 D floats) after the barriers
+    static constexpr int kBoxOffset = kBarOffset + kPairWarps * kStages * 8;
     // the strip epilogue reuses the (then idle) rings for its reduction scratch
     static constexpr int kRedOffset = kRingOffset;
     static constexpr int kRedBytes = kPairWarps * kTile * D * 4 + kPairWarps * 4 * 4;
     static_assert(kRedBytes <= kPairWarps * kStages * kStageBytes, "scratch must fit in the rings");
-    static constexpr int kBytes = kBarOffset + kPairWarps * kStages * 8;
+    static constexpr int kBytes = kBoxOffset + kPairWarps * 2 * D * 4;
 };
 
 // Refill one stage of a warp's ring: its 4 KB quarter of a Y tile and the
@@ -122,6 +124,16 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
     const float4 *xsrc_row = a.xrow + static_cast<int64_t>(st.I) * 32 * D;
     for (int idx = tid; idx < 32 * D; idx += kPairThreads) xis[idx] = xsrc_row[idx];
     __syncthreads();
+    // the row box of the block (each warp its own copy: no further CTA barrier)
+    float *box = reinterpret_cast<float *>(smem + L::kBoxOffset) + warp * 2 * D;
+    {
+        float b[2 * D];
+        row_box<D>(xis, lane, b);
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < 2 * D; ++i) box[i] = b[i];
+        __syncwarp();
+    }
 
     float2 racc[4][D];
 #pragma unroll
@@ -135,6 +147,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
     const int rowbase = st.I * kTile;
     float *colp_base = reinterpret_cast<float *>(a.col_part);
     bool ok = true;
+    int n_far = 0;  // warp blocks of this warp that took the far path
     int jt = 0;
     for (; jt < nst; ++jt) {
         const int stage = jt % kStages;
@@ -158,8 +171,8 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
                 tile_f32<D, true, PairArgs, HELDOUT>(a, ys, xjs, xis, lane, row_rel, warp * kWarpCols, ncv, racc, colp,
                                                      e2, mdv, prod);
             else
-                tile_f32<D, false, PairArgs>(a, ys, xjs, xis, lane, row_rel, warp * kWarpCols, ncv, racc, colp, e2, mdv,
-                                             prod);
+                n_far += tile_f32<D, false, PairArgs, false, true>(a, ys, xjs, xis, lane, row_rel, warp * kWarpCols, ncv,
+                                                                   racc, colp, e2, mdv, prod, box, a.far_d2);
         }
         // all lanes are done reading this stage: refill it (async proxy after
         // the generic reads)
@@ -179,6 +192,8 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
         if (lane == 0)
             for (int j = jt; j < nst && j < jt + kStages; ++j) mbar_wait_bounded(&bars[j % kStages], (j / kStages) & 1, a.err);
     }
+
+    if (lane == 0 && a.far_part) a.far_part[blockIdx.x * kPairWarps + warp] = n_far;
 
     // ---- strip epilogue
     float *red = reinterpret_cast<float *>(smem + L::kRedOffset);
@@ -220,7 +235,11 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int k = 0; k < D; ++k) xi[2 * q + h][k] = a.x64[(rowbase + 2 * (la + 8 * q) + h) * D + k];
+            for (int k = 0; k < D; ++k) {
+                const int slot = rowbase + 2 * (la + 8 * q) + h;
+                const int64_t item = a.perm ? a.perm[slot] : slot;
+                xi[2 * q + h][k] = a.x64[item * D + k];
+            }
     double racc[8][D];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -241,8 +260,10 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
         for (int c = 0; c < 4; ++c) {
             const int col = warp * kWarpCols + 4 * lb + c;
             double xj[D];
+            const int64_t cslot = static_cast<int64_t>(J) * kTile + col;
+            const int64_t citem = a.perm ? a.perm[cslot] : cslot;
 #pragma unroll
-            for (int k = 0; k < D; ++k) xj[k] = a.x64[(static_cast<int64_t>(J) * kTile + col) * D + k];
+            for (int k = 0; k < D; ++k) xj[k] = a.x64[citem * D + k];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float4 yv = ys[(2 * q + (c >> 1)) * 32 + lane];

@@ -237,15 +237,102 @@ __device__ __forceinline__ void pair2_f32(const K &a, const float4 (&xi)[D], con
     }
 }
 
+// The same two pairs where every pair of the warp's block lies at
+// z = delta / sigma >= z_c (z_c = 8 by default): the Phi terms are dropped.
+// For z >= 8, log(1/Phi(z)) <= 1.0000001 Q(z) < 6.3e-16 and
+// phi(z)/Phi(z) < 5.1e-15, far below the FP32 rounding (2^-24 = 6e-8,
+// relative) of the kept terms e^2/(2 sigma^2) and (delta - y)/sigma^2, so
+// the result is the same to FP32 precision.  Geometry, residual-corrected e
+// and the gradient accumulation are those of pair2_f32.
+template <int D, typename K>
+__device__ __forceinline__ void pair2_far(const K &a, const float4 (&xi)[D], const float4 (&xj)[D], float2 y2,
+                                          float2 (&racc)[D], float2 (&cacc)[D], float2 &e2) {
+    float2 s[D];
+    float2 d2h, cr;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const float2 dh = add2(f2(xi[k].x, xi[k].y), f2(xj[k].x, xj[k].y));
+        const float2 dl = add2(f2(xi[k].z, xi[k].w), f2(xj[k].z, xj[k].w));
+        s[k] = add2(dh, dl);
+        if (k == 0) {
+            d2h = mul2(dh, dh);
+            cr = fma2(dl, add2(s[k], dh), f2(FLT_MIN, FLT_MIN));
+        } else {
+            d2h = fma2(dh, dh, d2h);
+            cr = fma2(dl, add2(s[k], dh), cr);
+        }
+    }
+    const float2 d2 = add2(d2h, cr);
+    const float2 inv = f2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
+    const float2 del = f2(sqrt_approx(d2.x), sqrt_approx(d2.y));
+    const float2 res = add2(fma2(neg2(del), del, d2h), cr);
+    const float2 hinv = mul2(inv, f2(0.5f, 0.5f));
+    const float2 e = fma2(neg2(res), hinv, add2(y2, neg2(del)));
+    e2 = fma2(e, e, e2);
+    // w / delta = -(y - delta) / (sigma^2 delta)
+    const float2 wi = mul2(mul2(e, a.neg_inv_s2), inv);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        racc[k] = fma2(wi, s[k], racc[k]);
+        cacc[k] = fma2(wi, s[k], cacc[k]);
+    }
+}
+
+// Row box of a row block: per coordinate the smallest and largest x_i of its
+// 64 rows, from the row-pair split layout in shared memory ([k][row pair]
+// float4 {xh_i, xh_i+1, xl_i, xl_i+1}; xh + xl is x exactly).  Every lane of
+// the calling warp gets box[0..D) = minima, box[D..2D) = maxima.
+template <int D>
+__device__ __forceinline__ void row_box(const float4 *xis, int lane, float (&box)[2 * D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const float4 v = xis[k * 32 + lane];
+        const float a0 = v.x + v.z, a1 = v.y + v.w;
+        float lo = fminf(a0, a1), hi = fmaxf(a0, a1);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        box[k] = lo;
+        box[D + k] = hi;
+    }
+}
+
+// Whether every pair of the warp's 64 rows x 8 columns lies at squared
+// distance >= far_d2: each lane bounds the distance of its two columns
+// (split layout {-xh, -xh, -xl, -xl}) from the row box from below; the
+// decision is warp-uniform.
+template <int D>
+__device__ __forceinline__ bool block_far(const float *box, const float4 (&xj)[2][D], float far_d2) {
+    float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const float lo = box[k], hi = box[D + k];
+        const float c0 = -(xj[0][k].x + xj[0][k].z), c1 = -(xj[1][k].x + xj[1][k].z);
+        const float d0 = fmaxf(fmaxf(lo - c0, c0 - hi), 0.f);
+        const float d1 = fmaxf(fmaxf(lo - c1, c1 - hi), 0.f);
+        g0 = fmaf(d0, d0, g0);
+        g1 = fmaf(d1, d1, g1);
+    }
+    return __all_sync(0xffffffffu, fminf(g0, g1) >= far_d2);
+}
+
 // One tile for this lane: 8 rows x 4 columns, column pairs one at a time;
 // the column sums of each pair are reduced over the 8 row lanes and written.
-template <int D, bool MASKED, typename K, bool HELDOUT = false>
-__device__ __forceinline__ void tile_f32(const K &a, const float4 *ys, const float4 *xjs, const float4 *xis,
+// FAR (unmasked tiles only): a column pair whose whole 64 x 8 block of the
+// warp lies beyond the cut-off (block_far against the row box `box`) takes
+// pair2_far; far_d2 = +inf turns that off.  Returns the number of column
+// pairs that took pair2_far (0..2).
+template <int D, bool MASKED, typename K, bool HELDOUT = false, bool FAR = false>
+__device__ __forceinline__ int tile_f32(const K &a, const float4 *ys, const float4 *xjs, const float4 *xis,
                                          int lane, int row_rel, int col_lo, int64_t ncol_valid,
-                                         float2 (&racc)[4][D], float *colp, float2 &e2, float2 &md, float2 &prod) {
+                                         float2 (&racc)[4][D], float *colp, float2 &e2, float2 &md, float2 &prod,
+                                         const float *box = nullptr, float far_d2 = 0.f) {
     constexpr int V = 2 * D;  // column values of one column pair
     constexpr int P = Pow2<V>::value;
     const int la = lane & 7, lb = lane >> 3;
+    int n_far = 0;
 #pragma unroll 1
     for (int cp = 0; cp < 2; ++cp) {
         float4 xj[2][D];
@@ -258,29 +345,45 @@ __device__ __forceinline__ void tile_f32(const K &a, const float4 *ys, const flo
         for (int e = 0; e < 2; ++e)
 #pragma unroll
             for (int k = 0; k < D; ++k) cacc[e][k] = f2(0.f, 0.f);
+        bool far = false;
+        if constexpr (FAR && !MASKED) far = block_far<D>(box, xj, far_d2);
+        if (far) {
+            ++n_far;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 yv = ys[(2 * q + cp) * 32 + lane];
-            float4 xi[D];
+            for (int q = 0; q < 4; ++q) {
+                const float4 yv = ys[(2 * q + cp) * 32 + lane];
+                float4 xi[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) xi[k] = xis[k * 32 + la + 8 * q];
+                for (int k = 0; k < D; ++k) xi[k] = xis[k * 32 + la + 8 * q];
+                pair2_far<D, K>(a, xi, xj[0], f2(yv.x, yv.y), racc[q], cacc[0], e2);
+                pair2_far<D, K>(a, xi, xj[1], f2(yv.z, yv.w), racc[q], cacc[1], e2);
+            }
+        } else {
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const float2 y2 = e == 0 ? f2(yv.x, yv.y) : f2(yv.z, yv.w);
-                float2 vm = f2(1.f, 1.f);
-                if (MASKED) {
-                    // rows r, r+1 of the row pair, column c (tile-relative,
-                    // rows shifted so that the diagonal test is c > r); with
-                    // a cross-validation fold, a held-out pair carries y < 0
-                    const int r = row_rel + 2 * (la + 8 * q);
-                    const int c = col_lo + 4 * lb + 2 * cp + e;
-                    const bool cv = c < ncol_valid;
-                    if (HELDOUT)
-                        vm = f2((cv && c > r && y2.x >= 0.f) ? 1.f : 0.f, (cv && c > r + 1 && y2.y >= 0.f) ? 1.f : 0.f);
-                    else
-                        vm = f2((cv && c > r) ? 1.f : 0.f, (cv && c > r + 1) ? 1.f : 0.f);
+            for (int q = 0; q < 4; ++q) {
+                const float4 yv = ys[(2 * q + cp) * 32 + lane];
+                float4 xi[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) xi[k] = xis[k * 32 + la + 8 * q];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float2 y2 = e == 0 ? f2(yv.x, yv.y) : f2(yv.z, yv.w);
+                    float2 vm = f2(1.f, 1.f);
+                    if (MASKED) {
+                        // rows r, r+1 of the row pair, column c (tile-relative,
+                        // rows shifted so that the diagonal test is c > r); with
+                        // a cross-validation fold, a held-out pair carries y < 0
+                        const int r = row_rel + 2 * (la + 8 * q);
+                        const int c = col_lo + 4 * lb + 2 * cp + e;
+                        const bool cv = c < ncol_valid;
+                        if (HELDOUT)
+                            vm = f2((cv && c > r && y2.x >= 0.f) ? 1.f : 0.f,
+                                    (cv && c > r + 1 && y2.y >= 0.f) ? 1.f : 0.f);
+                        else
+                            vm = f2((cv && c > r) ? 1.f : 0.f, (cv && c > r + 1) ? 1.f : 0.f);
+                    }
+                    pair2_f32<D, MASKED, K>(a, xi, xj[e], y2, vm, racc[q], cacc[e], e2, md, prod);
                 }
-                pair2_f32<D, MASKED, K>(a, xi, xj[e], y2, vm, racc[q], cacc[e], e2, md, prod);
             }
         }
         // column sums over the tile's 64 rows: 3-level transpose over the row lanes
@@ -301,6 +404,7 @@ __device__ __forceinline__ void tile_f32(const K &a, const float4 *ys, const flo
                 if (base + i < V) colp[(4 * lb + 2 * cp) * D + base + i] = colv[i];
         }
     }
+    return n_far;
 }
 
 // End of a strip for one problem: the row sums over the lane's 4 column

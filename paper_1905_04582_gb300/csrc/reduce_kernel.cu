@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "mds_internal.h"
+#include "philox.cuh"
 
 namespace mds {
 namespace {
@@ -113,8 +114,8 @@ __device__ __forceinline__ float block_max(float v, float *sm) {
 
 // ------------------------------------------------------------ locations
 
-// Rewrite item k, coordinate kk of the FP32C split layouts from value v.
-__device__ __forceinline__ void write_split(const XState &xs, int64_t k, int d, int kk, float v) {
+// Rewrite slot k, coordinate kk of the FP32C split layouts from value v.
+__device__ __forceinline__ void write_split_slot(const XState &xs, int64_t k, int d, int kk, float v) {
     const Split sp = *xs.split;
     const float h = __fsub_rn(__fadd_rn(v, sp.magic), sp.magic);  // nearest multiple of q
     const float l = __fsub_rn(v, h);                               // exact
@@ -124,11 +125,23 @@ __device__ __forceinline__ void write_split(const XState &xs, int64_t k, int d, 
     xs.xcol[k * d + kk] = make_float4(-h, -h, -l, -l);
 }
 
+// The same for item `item` (at its slot of the tile layouts).
+__device__ __forceinline__ void write_split(const XState &xs, int64_t item, int d, int kk, float v) {
+    write_split_slot(xs, xs.inv ? xs.inv[item] : item, d, kk, v);
+}
+
 // Store a coordinate of the state (and the split layouts on the FP32C path).
 template <typename T>
 __device__ __forceinline__ void store_x(const XState &xs, int64_t k, int d, int kk, T v) {
     reinterpret_cast<T *>(xs.x)[k * d + kk] = v;
     if constexpr (std::is_same<T, float>::value) write_split(xs, k, d, kk, v);
+}
+
+// The same, for item k whose slot is known.
+template <typename T>
+__device__ __forceinline__ void store_x_at(const XState &xs, int64_t k, int64_t slot, int d, int kk, T v) {
+    reinterpret_cast<T *>(xs.x)[k * d + kk] = v;
+    if constexpr (std::is_same<T, float>::value) write_split_slot(xs, slot, d, kk, v);
 }
 
 // Gradient storage: FP32C keeps (hi, lo) float pairs, FP64 doubles.
@@ -157,6 +170,14 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     __shared__ Acc sm[kSplits * kRedRows > 64 ? kSplits * kRedRows : 64];
     const int tid = threadIdx.x;
     const int nt = a.nt;
+    // the item at this thread's slot (the order is constant between passes,
+    // so it is read before the wait)
+    int64_t item_of_slot = -1;
+    if (Jq >= 0) {
+        const int64_t ks = static_cast<int64_t>(Jq / kRedQuarters) * kTile + (Jq % kRedQuarters) * kRedRows +
+                           (tid % kRedRows);
+        item_of_slot = (a.perm && ks < a.n) ? a.perm[ks] : ks;
+    }
     // every input (partials, x, p) comes from the pass just before
     pdl_trigger();
     pdl_wait();
@@ -312,6 +333,8 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     Acc ke{}, xx{};
     float xmax = 0.f;
     if (s == 0 && k < a.n) {
+        // slot k of the tile layouts holds item `it` of the state
+        const int64_t it = item_of_slot;
         T *x = reinterpret_cast<T *>(a.xs.x);
         T *p = reinterpret_cast<T *>(a.p);
         G *grad = reinterpret_cast<G *>(a.grad);
@@ -321,25 +344,26 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             const Acc g = gsum[d];
             T gv;
             if constexpr (kF32) {
-                grad[k * D + d] = make_float2(g.hi, g.lo);
+                grad[it * D + d] = make_float2(g.hi, g.lo);
                 gv = df_float(g);
             } else {
-                grad[k * D + d] = g;
+                grad[it * D + d] = g;
                 gv = g;
             }
             bad |= !isfinite(gv);
             if (mode != kModeEval) {
-                const T xv = x[k * D + d];
-                const T tg = gv - static_cast<T>(a.lambda) * xv;  // gradient of log pi
+                const T xv = x[it * D + d];
+                T tg = gv - static_cast<T>(a.lambda) * xv;  // gradient of log pi
+                if (a.prior_grad) tg += static_cast<T>(a.prior_grad[it * D + d]);
                 if (mode == kModeKickDrift) {
-                    const T pn = p[k * D + d] + static_cast<T>(a.eps) * tg;
+                    const T pn = p[it * D + d] + static_cast<T>(a.eps) * tg;
                     const T xn = xv + static_cast<T>(a.eps) * pn;
-                    p[k * D + d] = pn;
-                    store_x<T>(a.xs, k, D, d, xn);
+                    p[it * D + d] = pn;
+                    store_x_at<T>(a.xs, it, k, D, d, xn);
                     xmax = fmaxf(xmax, fabsf(static_cast<float>(xn)));
                 } else {  // kModeHalfKick
-                    const T pn = p[k * D + d] + static_cast<T>(0.5 * a.eps) * tg;
-                    p[k * D + d] = pn;
+                    const T pn = p[it * D + d] + static_cast<T>(0.5 * a.eps) * tg;
+                    p[it * D + d] = pn;
                     if constexpr (kF32) {
                         df_add(ke, 0.5f * pn * pn);
                         df_add(xx, xv * xv);
@@ -393,61 +417,6 @@ __global__ void __launch_bounds__(kRedThreads) reduce_batch_kernel(const ReduceA
     reduce_body<float, D>(cfg[job.x], mode, job.y);
 }
 
-// ------------------------------------------------------------ Philox / RNG
-
-__device__ __forceinline__ void philox_round(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
-    const uint32_t lo0 = 0xD2511F53u * c[0];
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]);
-    const uint32_t lo1 = 0xCD9E8D57u * c[2];
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]);
-    const uint32_t n0 = hi1 ^ c[1] ^ k0;
-    const uint32_t n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-}
-
-// Philox4x32-10 (Salmon et al., SC'11): 10 rounds, Weyl key schedule.
-__device__ __forceinline__ void philox10(uint32_t (&c)[4], uint64_t key) {
-    uint32_t k0 = static_cast<uint32_t>(key), k1 = static_cast<uint32_t>(key >> 32);
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        philox_round(c, k0, k1);
-    }
-}
-
-__device__ __forceinline__ double open_unit(uint32_t b) { return (static_cast<double>(b) + 0.5) * (1.0 / 4294967296.0); }
-
-// Box-Muller pair from two 32-bit words, u = (b + 1/2) / 2^32.
-__device__ __forceinline__ void box_muller(uint32_t b1, uint32_t b2, double &z0, double &z1) {
-    const double u1 = open_unit(b1), u2 = open_unit(b2);
-    const double rad = sqrt(-2.0 * log(u1));
-    double sn, cs;
-    sincospi(2.0 * u2, &sn, &cs);
-    z0 = rad * cs;
-    z1 = rad * sn;
-}
-
-// FP32 version: -log(u1) through log1p for u1 >= 1/2 (1 - u1 exact from the
-// integer), so the radius keeps full relative precision near u1 = 1.
-__device__ __forceinline__ void box_muller(uint32_t b1, uint32_t b2, float &z0, float &z1) {
-    float nl;
-    if (b1 < 0x80000000u)
-        nl = -logf((static_cast<float>(b1) + 0.5f) * 2.3283064365386963e-10f);
-    else
-        nl = -log1pf(-(static_cast<float>(0xFFFFFFFFu - b1) + 0.5f) * 2.3283064365386963e-10f);
-    const float rad = sqrtf(2.0f * nl);
-    float sn, cs;
-    sincospif(2.0f * ((static_cast<float>(b2) + 0.5f) * 2.3283064365386963e-10f), &sn, &cs);
-    z0 = rad * cs;
-    z1 = rad * sn;
-}
-
 // ----------------------------------------------------------- traj start
 
 constexpr int kTrajThreads = 128;
@@ -490,6 +459,11 @@ __device__ __forceinline__ void traj_start_body(const TrajArgs &a, int bx) {
         const T xv = x[e];
         x0[e] = xv;
         grad0[e] = grad[e];
+        double pg = 0.0;
+        if (a.prior_grad) {
+            pg = a.prior_grad[e];
+            a.prior_grad0[e] = pg;
+        }
         if constexpr (kF32) {
             df_add(ke, 0.5f * pv * pv);
             df_add(xx, xv * xv);
@@ -498,7 +472,7 @@ __device__ __forceinline__ void traj_start_body(const TrajArgs &a, int bx) {
             xx += xv * xv;
         }
         if (a.drift) {
-            const T tg = GradT<T>::value(grad[e]) - static_cast<T>(a.lambda) * xv;
+            const T tg = GradT<T>::value(grad[e]) - static_cast<T>(a.lambda) * xv + static_cast<T>(pg);
             pv = pv + static_cast<T>(0.5 * a.eps) * tg;
             const T xn = xv + static_cast<T>(a.eps) * pv;
             store_x<T>(a.xs, e / D, D, static_cast<int>(e % D), xn);
@@ -525,6 +499,7 @@ __device__ __forceinline__ void traj_start_body(const TrajArgs &a, int bx) {
             a.scal[kLogLik0] = a.scal[kLogLik];
             a.scal[kSumR0] = a.scal[kSumR];
             a.scal[kDSigma0] = a.scal[kDSigma];
+            a.scal[kPriorLogp0] = a.scal[kPriorLogp];
             a.counters[kIterCur] = iter;
             a.counters[kIterLocalCur] = iter_local;
         }
@@ -572,8 +547,8 @@ __device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int n
             xx1 += __shfl_xor_sync(0xffffffffu, xx1, o);
         }
         if (lane == 0) {
-            const double h0 = -(a.scal[kLogLik0] - 0.5 * a.lambda * xx0) + ke0;
-            const double h1 = -(a.scal[kLogLikEnd] - 0.5 * a.lambda * xx1) + ke1;
+            const double h0 = -(a.scal[kLogLik0] - 0.5 * a.lambda * xx0 + a.scal[kPriorLogp0]) + ke0;
+            const double h1 = -(a.scal[kLogLikEnd] - 0.5 * a.lambda * xx1 + a.scal[kPriorLogp]) + ke1;
             const double dh = h1 - h0;
             int keep = 1;
             if (a.metropolis) {
@@ -605,6 +580,7 @@ __device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int n
              e += static_cast<int64_t>(nbx) * kTrajThreads) {
             store_x<T>(a.xs, e / D, D, static_cast<int>(e % D), x0[e]);
             grad[e] = grad0[e];
+            if (a.prior_grad) a.prior_grad[e] = a.prior_grad0[e];
         }
     } else if (resplit) {
         const T *x = reinterpret_cast<const T *>(a.xs.x);
@@ -620,6 +596,7 @@ __device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int n
             a.scal[kLogLik] = a.scal[kLogLik0];
             a.scal[kSumR] = a.scal[kSumR0];
             a.scal[kDSigma] = a.scal[kDSigma0];
+            a.scal[kPriorLogp] = a.scal[kPriorLogp0];
         }
         const int64_t il = a.counters[kIterLocalCur];
         if (il >= 0 && il < a.out_cap) {
@@ -745,6 +722,44 @@ __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
             v = static_cast<float>(y);
         }
         if (in_rows || i >= a.n) a.y[t * kTileElems + off] = v;  // rows past N: padding of the last block
+    }
+}
+
+// One thread per element of the new layout; the old element is found by
+// the old slots of the two items (upper triangle: the smaller slot is the row).
+__global__ void repack_kernel(const float *old_y, float *new_y, const int32_t *map, int64_t n, int32_t nt_) {
+    const int64_t nt = nt_;
+    const int64_t total = tile_count(nt) * kTileElems;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t t = g / kTileElems;
+        const int off = static_cast<int>(g % kTileElems);
+        int64_t lo = 0, hi = nt - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (tile_index(mid, mid, nt) <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int64_t I = lo;
+        const int64_t J = I + (t - tile_index(I, I, nt));
+        int rr, cc;
+        tile_rc(off, rr, cc);
+        const int64_t sr = I * kTile + rr, sc = J * kTile + cc;
+        float v = 0.0f;
+        if (sr < sc && sc < n) {
+            int64_t a = map[sr], b = map[sc];
+            if (a > b) {
+                const int64_t tmp = a;
+                a = b;
+                b = tmp;
+            }
+            const int64_t I2 = a / kTile, J2 = b / kTile;
+            v = old_y[tile_index(I2, J2, nt) * kTileElems +
+                      tile_offset(static_cast<int>(a - I2 * kTile), static_cast<int>(b - J2 * kTile))];
+        }
+        new_y[g] = v;
     }
 }
 
@@ -903,6 +918,11 @@ cudaError_t launch_set_x(const void *src, bool src_f64, int64_t n, int64_t n_pad
         else
             set_x_kernel<float, float><<<g, 256, 0, s>>>(static_cast<const float *>(src), n, n_pad, d, xs, err);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repack(const float *old_y, float *new_y, const int32_t *map, int64_t n, int32_t nt, cudaStream_t s) {
+    repack_kernel<<<grid_for(tile_count(nt) * kTileElems, 256), 256, 0, s>>>(old_y, new_y, map, n, nt);
     return cudaGetLastError();
 }
 

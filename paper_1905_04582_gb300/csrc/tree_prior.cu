@@ -1,0 +1,255 @@
+// Phylogenetic Brownian-diffusion prior on the latent locations
+// (arXiv:1905.04582, section 2.2: the matrix-normal density of X with the
+// tree covariance V and the diffusion covariance Sigma), its log density and
+// its gradient in X, by message passing on the forest: O(N D^2) work.
+//
+// Section 2.3 notes that the density is computable in time linear in N by
+// post-order traversals of the trees instead of factorising V (O(N^3)).
+// Gaussian messages on a tree carry a mean and a variance scalar; the
+// variances depend on the tree alone (branch lengths, tau0), not on X, so
+// the host computes them once per tree (mds_set_tree_prior) and folds them
+// into per-node weights.  Per evaluation the device moves only means:
+//  - post-order, level by level (height = 1 + the children's largest): node
+//    k with children a, b sends up m_k = alpha_k m_a + (1 - alpha_k) m_b and
+//    adds the contrast term -1/2 (m_a - m_b)^T Sigma^-1 (m_a - m_b) c_k,
+//    c_k = 1 / (v_a + t_a + v_b + t_b); a tip sends its location.  The root
+//    adds -1/2 (m_root - mu)^T Sigma^-1 (m_root - mu) / (v_root + tau0).
+//    With the constant log-determinant terms (host) these N contrasts sum to
+//    the log density (each contrast carries -1/2 log|Sigma|, and their
+//    variances multiply to |V|).
+//  - pre-order, level by level from the roots (downward mean of a root: mu):
+//    child c of node k with sibling s receives
+//    m_c = beta_c m_k + (1 - beta_c) m_s (precision weights of k's downward
+//    message and s's upward message through its branch).  At a tip the
+//    downward message is the law of x_c given every other item,
+//    N(m_c, v_c Sigma), so d log p / d x_c = -Sigma^-1 (x_c - m_c) / v_c.
+// One CTA per tree keeps the tree's node records, messages and tip
+// locations in shared memory (global scratch when a tree is too large);
+// unsequenced items (tips that are roots, variance tau_u) get one more CTA.
+// FP64 throughout; every sum has a fixed order, so results are
+// deterministic.
+#include <cstdint>
+
+#include "mds_internal.h"
+
+namespace mds {
+namespace {
+
+constexpr int kTreeThreads = 512;
+
+template <int D>
+__device__ __forceinline__ double quad_form(const double *sinv, const double (&v)[D]) {
+    double q = 0.0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        double t = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) t = fma(sinv[r * D + c], v[c], t);
+        q = fma(v[r], t, q);
+    }
+    return q;
+}
+
+// Upward mean of child reference c: an internal node's message (c >= 0) or
+// a tip's location (c < 0).
+template <int D>
+__device__ __forceinline__ void mean_of(const double *up, const double *tx, int c, double (&m)[D]) {
+    const double *src = c >= 0 ? up + static_cast<int64_t>(c) * D : tx + static_cast<int64_t>(-c - 1) * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) m[k] = src[k];
+}
+
+// -Sigma^-1 (x - m) g into grad[item]
+template <int D>
+__device__ __forceinline__ void tip_gradient(const TreeArgs &a, int64_t item, const double *xv, const double (&m)[D],
+                                             double g) {
+    double e[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) e[q] = xv[q] - m[q];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < D; ++q) s = fma(a.sigma_inv[r * D + q], e[q], s);
+        a.grad[item * D + r] = -s * g;
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kTreeThreads / 32; ++w) t += sm[w];
+    return t;  // valid in thread 0
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_constant__ TreeArgs a) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    __shared__ double sm[kTreeThreads / 32];
+    const T *x = static_cast<const T *>(a.x);
+    const int tid = threadIdx.x;
+    double acc = 0.0;  // this thread's quadratic terms (fixed node assignment)
+    const int t = blockIdx.x;
+    if (t < a.n_trees) {
+        const int m = a.node_off[t + 1] - a.node_off[t];
+        const int k = a.tip_off[t + 1] - a.tip_off[t];
+        const int32_t *tips = a.tip_items + a.tip_off[t];
+        const TreeNode *rec;
+        double *up;
+        if (a.smem_bytes > 0) {
+            // stage the tree's records in shared memory (as 8-byte words)
+            TreeNode *srec = reinterpret_cast<TreeNode *>(tsm);
+            const uint64_t *src = reinterpret_cast<const uint64_t *>(a.nodes + a.node_off[t]);
+            uint64_t *dst = reinterpret_cast<uint64_t *>(srec);
+            constexpr int kWords = sizeof(TreeNode) / 8;
+            for (int i = tid; i < m * kWords; i += kTreeThreads) dst[i] = src[i];
+            rec = srec;
+            up = reinterpret_cast<double *>(srec + m);
+        } else {
+            rec = a.nodes + a.node_off[t];
+            up = a.scratch + a.scr_off[t];
+        }
+        double *dn = up + static_cast<int64_t>(m) * D;
+        double *tx = dn + static_cast<int64_t>(m) * D;
+        for (int i = tid; i < k * D; i += kTreeThreads)
+            tx[i] = static_cast<double>(x[static_cast<int64_t>(tips[i / D]) * D + i % D]);
+        __syncthreads();
+        // ---- post-order: levels [lv0, lv1) of this tree
+        const int lv0 = a.tree_lv[t], lv1 = a.tree_lv[t + 1];
+        for (int lv = lv0; lv < lv1; ++lv) {
+            const int end = lv + 1 < lv1 ? a.lv_start[lv + 1] : m;
+            for (int idx = a.lv_start[lv] + tid; idx < end; idx += kTreeThreads) {
+                const TreeNode nd = rec[idx];
+                double ma[D], mb[D], dv[D];
+                mean_of<D>(up, tx, nd.c0, ma);
+                mean_of<D>(up, tx, nd.c1, mb);
+#pragma unroll
+                for (int c = 0; c < D; ++c) dv[c] = ma[c] - mb[c];
+                acc = fma(-0.5 * nd.cinv, quad_form<D>(a.sigma_inv, dv), acc);
+#pragma unroll
+                for (int c = 0; c < D; ++c) up[static_cast<int64_t>(idx) * D + c] = fma(nd.alpha, dv[c], mb[c]);
+            }
+            __syncthreads();
+        }
+        // the root (the last record): m_root - mu ~ N(0, (v_root + tau0) Sigma);
+        // its downward mean is mu
+        if (tid == 0) {
+            double dv[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) dv[c] = up[static_cast<int64_t>(m - 1) * D + c] - a.mu[c];
+            acc = fma(-0.5 * a.root_cinv[t], quad_form<D>(a.sigma_inv, dv), acc);
+#pragma unroll
+            for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(m - 1) * D + c] = a.mu[c];
+        }
+        __syncthreads();
+        // ---- pre-order: the same levels from the root down
+        for (int lv = lv1 - 1; lv >= lv0; --lv) {
+            const int end = lv + 1 < lv1 ? a.lv_start[lv + 1] : m;
+            for (int idx = a.lv_start[lv] + tid; idx < end; idx += kTreeThreads) {
+                const TreeNode nd = rec[idx];
+                double mk[D], m0[D], m1[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) mk[c] = dn[static_cast<int64_t>(idx) * D + c];
+                mean_of<D>(up, tx, nd.c0, m0);
+                mean_of<D>(up, tx, nd.c1, m1);
+                double d0[D], d1[D];  // downward means of child 0 (sibling 1) and child 1
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    d0[c] = fma(nd.beta0, mk[c] - m1[c], m1[c]);
+                    d1[c] = fma(nd.beta1, mk[c] - m0[c], m0[c]);
+                }
+                if (nd.c0 < 0) {
+                    const int tp = -nd.c0 - 1;
+                    tip_gradient<D>(a, tips[tp], tx + static_cast<int64_t>(tp) * D, d0, nd.g0);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(nd.c0) * D + c] = d0[c];
+                }
+                if (nd.c1 < 0) {
+                    const int tp = -nd.c1 - 1;
+                    tip_gradient<D>(a, tips[tp], tx + static_cast<int64_t>(tp) * D, d1, nd.g1);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(nd.c1) * D + c] = d1[c];
+                }
+            }
+            __syncthreads();
+        }
+    } else {
+        // unsequenced items: x_i ~ N(mu, tau_u Sigma) on their own
+        const double g = 1.0 / a.tau_u;
+        for (int idx = tid; idx < a.n_lone; idx += kTreeThreads) {
+            const int64_t i = a.lone[idx];
+            double m[D], e[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                m[q] = a.mu[q];
+                e[q] = static_cast<double>(x[i * D + q]);
+            }
+            double dv[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) dv[q] = e[q] - m[q];
+            acc = fma(-0.5 * g, quad_form<D>(a.sigma_inv, dv), acc);
+            tip_gradient<D>(a, i, e, m, g);
+        }
+    }
+    const double tot = block_sum(acc, sm);
+    if (tid == 0) a.part[t] = tot;
+}
+
+// Fixed-order sum of the per-CTA parts plus the constant (log-determinant)
+// terms.
+__global__ void tree_prior_final_kernel(const double *part, int n_parts, double const_term, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = const_term;
+        for (int i = 0; i < n_parts; ++i) s += part[i];
+        *out = s;
+    }
+}
+
+template <int D, typename T>
+cudaError_t launch_t(const TreeArgs &a, int grid, cudaStream_t s) {
+    static int attr_bytes = 0;  // per instantiation, raised once as needed
+    if (a.smem_bytes > attr_bytes) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(tree_prior_kernel<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_bytes = a.smem_bytes;
+    }
+    tree_prior_kernel<D, T><<<grid, kTreeThreads, a.smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_d(const TreeArgs &a, cudaStream_t s) {
+    const int grid = a.n_trees + (a.n_lone > 0 ? 1 : 0);
+    if (grid > 0) {
+        const cudaError_t e = a.x_f64 ? launch_t<D, double>(a, grid, s) : launch_t<D, float>(a, grid, s);
+        if (e != cudaSuccess) return e;
+    }
+    tree_prior_final_kernel<<<1, 32, 0, s>>>(a.part, grid, a.const_term, a.out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s) {
+    switch (d) {
+        case 1: return launch_d<1>(a, s);
+        case 2: return launch_d<2>(a, s);
+        case 3: return launch_d<3>(a, s);
+        case 4: return launch_d<4>(a, s);
+        case 5: return launch_d<5>(a, s);
+        case 6: return launch_d<6>(a, s);
+        case 7: return launch_d<7>(a, s);
+        case 8: return launch_d<8>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mds

@@ -129,6 +129,70 @@ class MDS:
         self._check(self._lib.mds_get_strip(self._h, ctypes.byref(s)))
         return s.value
 
+    def reorder(self):
+        """Arrange the tile layouts in the locality order of the current
+        locations (mds_reorder); every array of the API keeps the item order."""
+        self._check(self._lib.mds_reorder(self._h))
+
+    def get_order(self):
+        perm = np.empty(self.n, dtype=np.int32)
+        self._check(self._lib.mds_get_order(self._h, perm.ctypes.data_as(ctypes.c_void_p)))
+        return perm
+
+    # -- single-item random-walk Metropolis (section 2.3's prior art)
+    def rwmh(self, n_prop, step, seed=0, items=None, z_all=None, u_all=None):
+        """n_prop single-item random-walk proposals (injected draws or
+        Philox); returns (accepted[n_prop], dlogpi[n_prop])."""
+        acc = np.zeros(int(n_prop), dtype=np.int32)
+        dl = np.zeros(int(n_prop))
+        vp = ctypes.c_void_p
+        if items is not None:
+            it = np.ascontiguousarray(items, dtype=np.int64)
+            z = np.ascontiguousarray(z_all, dtype=np.float64)
+            u = np.ascontiguousarray(u_all, dtype=np.float64)
+            args = (it.ctypes.data_as(vp), z.ctypes.data_as(vp), u.ctypes.data_as(vp))
+        else:
+            args = (None, None, None)
+        self._check(self._lib.mds_rwmh(self._h, int(n_prop), float(step), int(seed) & (2 ** 64 - 1), *args,
+                                       acc.ctypes.data_as(vp), dl.ctypes.data_as(vp)))
+        return acc, dl
+
+    # -- phylogenetic Brownian-diffusion prior (section 2.2)
+    def set_tree_prior(self, parent, length, sigma_mat, mu, tau0, tau_u):
+        """Forest over the items (parent / length per node, -1 for roots) and
+        the diffusion parameters; parent=None removes the prior."""
+        if parent is None:
+            self._check(self._lib.mds_set_tree_prior(self._h, 0, None, None, None, None, 1.0, 1.0))
+            return
+        par = np.ascontiguousarray(parent, dtype=np.int64)
+        ln = np.ascontiguousarray(length, dtype=np.float64)
+        sm = np.ascontiguousarray(sigma_mat, dtype=np.float64)
+        mu_ = np.ascontiguousarray(mu, dtype=np.float64)
+        vp = ctypes.c_void_p
+        self._check(self._lib.mds_set_tree_prior(self._h, par.shape[0], par.ctypes.data_as(vp),
+                                                 ln.ctypes.data_as(vp), sm.ctypes.data_as(vp),
+                                                 mu_.ctypes.data_as(vp), float(tau0), float(tau_u)))
+
+    def tree_prior(self, out=None, dtype=np.float64):
+        """(log p(X), d log p / dX) of the tree prior at the current locations."""
+        lp = ctypes.c_double()
+        if out is None:
+            out = np.empty((self.n, self.d), dtype=dtype)
+        ptr, dt, where, keep = _buf(out, writable=True)
+        self._check(self._lib.mds_tree_prior(self._h, ctypes.byref(lp), ptr, dt, where))
+        return lp.value, out
+
+    def far_blocks(self):
+        """(far, total) warp blocks of one evaluation pass (far: Phi terms skipped)."""
+        f = ctypes.c_int64()
+        t = ctypes.c_int64()
+        self._check(self._lib.mds_far_blocks(self._h, ctypes.byref(f), ctypes.byref(t)))
+        return f.value, t.value
+
+    def set_tail_cutoff(self, z):
+        """Phi-term cut-off z_c of the FP32C pass (0: off; else >= 8)."""
+        self._check(self._lib.mds_set_tail_cutoff(self._h, float(z)))
+
     def problem_size(self):
         m = ctypes.c_int64()
         b = ctypes.c_int64()
@@ -281,6 +345,17 @@ class MDS:
         k = min(cnt.value, cap)
         return acc[:k].astype(bool), dh[:k], {"iterations": stats.iterations, "accepted": stats.accepted,
                                               "last_dh": stats.last_dh, "last_loglik": stats.last_loglik}
+
+
+def locality_order(x):
+    """Locality-preserving order of the rows of x (N x D): perm[s] is the item
+    at position s (mds_locality_order; host only)."""
+    xa = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    n, d = xa.shape
+    perm = np.empty(n, dtype=np.int32)
+    capi.check(capi.lib().mds_locality_order(n, d, xa.ctypes.data_as(ctypes.c_void_p),
+                                             perm.ctypes.data_as(ctypes.c_void_p)))
+    return perm
 
 
 class Batch:

@@ -82,3 +82,32 @@ def test_package_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
                 assert "mds_oracle" not in text, f
+
+
+def test_locality_order_tiles_a_grid_into_squares(lib):
+    """On a 64 x 64 grid the bisection order makes every run of 64 items an
+    8 x 8 square (each cut halves the wider side at a multiple of 64 items)."""
+    from paper_1905_04582_gb300.mds import locality_order
+    import numpy as np
+    g = np.stack(np.meshgrid(np.arange(64.0), np.arange(64.0), indexing="ij"), -1).reshape(-1, 2)
+    g = g[np.random.default_rng(0).permutation(len(g))]  # any input order
+    perm = locality_order(g)
+    assert sorted(perm.tolist()) == list(range(len(g)))
+    blocks = g[perm].reshape(64, 64, 2)
+    span = blocks.max(axis=1) - blocks.min(axis=1)
+    assert np.all(span == 7.0)
+    assert np.array_equal(perm, locality_order(g))  # deterministic
+
+
+def test_locality_order_ragged_and_rejects_bad_input(lib):
+    from paper_1905_04582_gb300.mds import locality_order
+    import numpy as np
+    x = np.random.default_rng(1).standard_normal((333, 3))
+    perm = locality_order(x)
+    assert sorted(perm.tolist()) == list(range(333))
+    assert len(locality_order(x[:1])) == 1
+    bad = x.copy()
+    bad[5, 1] = np.nan
+    with pytest.raises(capi.MDSError) as e:
+        locality_order(bad)
+    assert e.value.status == capi.MDS_ERR_INVALID_ARG

@@ -1,0 +1,141 @@
+"""The phylogenetic Brownian-diffusion prior (section 2.2) on the GPU against
+the dense FP64 oracle (oracle/tree_prior.py), through the C ABI: log p(X)
+and d log p / dX by the device's two tree traversals, for forests with
+several trees and unsequenced items, D = 1..6, both location precisions, up
+to the paper's four subtype trees (N = 5392).
+
+Tolerance.  Both sides are FP64, but the oracle factorises the dense V,
+whose condition number kappa(V) grows with N (coalescent trees have very
+short branches near the tips), while the device passes messages along the
+tree.  A gradient coordinate passes when its error is within
+tol * (|g| + 1e-3 max|g|) with tol = 1e-10 for N <= 64 and 1e-7 otherwise
+(kappa(V) u with kappa up to ~1e8); log p within 1e-10 relative."""
+import numpy as np
+import pytest
+
+from oracle import tree_prior as TP
+from paper_1905_04582_gb300 import workloads as W
+from paper_1905_04582_gb300.capi import MDSError, MDS_ERR_INVALID_ARG, MDS_ERR_STATE
+
+pytestmark = pytest.mark.gpu
+
+
+def model_with_tree(f, x, prec):
+    from paper_1905_04582_gb300.mds import MDS
+    m = MDS(f.n, x.shape[1], prec)
+    m.set_locations(x)
+    m.set_tree_prior(f.parent, f.length, f.sigma_mat, f.mu, f.tau0, f.tau_u)
+    return m
+
+
+def check(f, x, prec, tol):
+    with model_with_tree(f, x, prec) as m:
+        lp, g = m.tree_prior()
+        lp2, g2 = m.tree_prior()
+        xs = m.get_locations()  # the state as stored (FP32 on the FP32C path)
+    assert lp == lp2 and np.array_equal(g, g2)  # deterministic
+    ref = TP.logp(xs, f.parent, f.length, f.sigma_mat, f.mu, f.tau0, f.tau_u)
+    g_ref = TP.gradient(xs, f.parent, f.length, f.sigma_mat, f.mu, f.tau0, f.tau_u)
+    assert abs(lp - ref) <= 1e-10 * abs(ref) + 1e-9, (lp, ref)
+    err = np.abs(g - g_ref)
+    lim = tol * (np.abs(g_ref) + 1e-3 * np.abs(g_ref).max())
+    assert np.all(err <= lim), (float((err / lim).max()), float(err.max()))
+    return float(np.max(err / (np.abs(g_ref) + 1e-3 * np.abs(g_ref).max())))
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+@pytest.mark.parametrize("sizes,lone,d", [((7, 5), 2, 2), ((3, 2), 0, 1), ((20, 9, 4), 5, 3), ((30,), 1, 6)])
+def test_small_forests_match_oracle(prec, sizes, lone, d):
+    f = W.random_forest(sizes, n_lone=lone, d=d, seed=sum(sizes) + d, tau0=0.8, tau_u=1.5)
+    x = W.brownian_tips(f, seed=3)
+    print(prec, sizes, lone, d, check(f, x, prec, 1e-10))
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_medium_forest_matches_oracle(prec):
+    f = W.random_forest((300, 200, 90), n_lone=10, d=2, seed=21)
+    x = W.brownian_tips(f, seed=4)
+    print(prec, check(f, x, prec, 1e-7))
+
+
+def test_paper_scale_forest_matches_oracle():
+    f = W.random_forest(W.SUBTYPE_SIZES, n_lone=0, d=2, seed=1)
+    x = W.brownian_tips(f, seed=5)
+    print("N=5392", check(f, x, "fp64", 1e-7))
+
+
+def test_only_unsequenced_items():
+    f = W.random_forest((), n_lone=40, d=3, seed=9, tau_u=0.7)
+    x = W.brownian_tips(f, seed=6)
+    check(f, x, "fp64", 1e-12)
+
+
+def test_invalid_forests_are_rejected():
+    from paper_1905_04582_gb300.mds import MDS
+    f = W.random_forest((6, 4), n_lone=1, d=2, seed=2)
+    x = W.brownian_tips(f, seed=1)
+    with MDS(f.n, 2, "fp64") as m:
+        m.set_locations(x)
+        with pytest.raises(MDSError) as e:
+            m.tree_prior()
+        assert e.value.status == MDS_ERR_STATE
+        bad = [(f.parent.copy(), f.length.copy(), f.sigma_mat) for _ in range(4)]
+        bad[0][1][0] = 0.0                                # zero branch length
+        bad[1][0][f.n - 1] = bad[1][0][0]                 # an internal node with three children
+        bad[2] = (f.parent[:-1], f.length[:-1], f.sigma_mat)  # a child pointing past the last node
+        bad[3] = (f.parent, f.length, np.array([[1.0, 2.0], [2.0, 1.0]]))  # Sigma not positive definite
+        for par, ln, sm in bad:
+            with pytest.raises(MDSError) as e:
+                m.set_tree_prior(par, ln, sm, f.mu, f.tau0, f.tau_u)
+            assert e.value.status == MDS_ERR_INVALID_ARG
+        m.set_tree_prior(f.parent, f.length, f.sigma_mat, f.mu, f.tau0, f.tau_u)
+        m.tree_prior()
+        m.set_tree_prior(None, None, None, None, 1.0, 1.0)
+        with pytest.raises(MDSError) as e:
+            m.tree_prior()
+        assert e.value.status == MDS_ERR_STATE
+
+
+def _tree_workload(n_sizes, lone, seed):
+    """Items from the Brownian process on a forest; y from those locations
+    (Eq. (1) model, noise = sigma); evaluation point jittered."""
+    f = W.random_forest(n_sizes, n_lone=lone, d=2, seed=seed, tau0=1.0, tau_u=2.0, rate=0.05)
+    x_true = W.brownian_tips(f, seed=seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    from scipy.spatial.distance import pdist
+    sigma = 0.4
+    y = np.abs(pdist(x_true) + sigma * rng.standard_normal(f.n * (f.n - 1) // 2)).astype(np.float32)
+    x_eval = (x_true + 0.05 * rng.standard_normal(x_true.shape)).astype(np.float32)
+    return f, y, x_eval, sigma
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+@pytest.mark.parametrize("reorder", [False, True])
+def test_hmc_with_tree_prior_matches_oracle(prec, reorder):
+    """HMC on log pi = L + log p(X | tree) with injected momenta and uniforms:
+    the same decisions, energy differences and end point as the oracle."""
+    import math
+    from paper_1905_04582_gb300.mds import MDS
+    f, y, x_eval, sigma = _tree_workload((70, 50), 6, 41)
+    tree = (f.parent, f.length, f.sigma_mat, f.mu, f.tau0, f.tau_u)
+    n_iter, n_steps, eps = 5, 8, 2e-3
+    p_all, u_all = W.momenta(42, n_iter, f.n, 2)
+    xr, acc_r, dh_r = TP.hmc(y, x_eval.astype(np.float64), sigma, eps, n_steps, p_all, u_all, tree)
+    with MDS(f.n, 2, prec) as m:
+        m.set_data(y)
+        m.set_locations(x_eval)
+        m.set_sigma(sigma)
+        m.set_tree_prior(*tree)
+        if reorder:
+            m.reorder()
+        acc, dh, _ = m.hmc(n_iter, n_steps, eps, p_all=p_all, u_all=u_all)
+        x = m.get_locations()
+        ll, _ = m.log_likelihood()
+    tol = (2e-6 if prec == "fp32c" else 2e-12) * abs(ll) + (1e-5 if prec == "fp32c" else 1e-9)
+    for t in range(n_iter):
+        if abs(math.log(u_all[t]) + dh_r[t]) <= 2 * tol:
+            pytest.skip("tie zone")
+        assert abs(dh[t] - dh_r[t]) <= tol, (t, dh[t], dh_r[t])
+        assert acc[t] == acc_r[t]
+    assert 0 < acc_r.sum()
+    np.testing.assert_allclose(x, xr, rtol=0, atol=(2e-5 if prec == "fp32c" else 1e-10) * (1 + np.abs(xr).max()))
