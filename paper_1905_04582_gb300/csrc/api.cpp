@@ -256,9 +256,12 @@ int build_strips(mds_ctx *c, int strip) {
     }
     first[nt] = slot;
     // largest strips first: blocks are dispatched roughly in index order, so
-    // this approximates longest-processing-time-first scheduling
+    // this approximates longest-processing-time-first scheduling; among
+    // strips of one length, those that hold a diagonal tile (masked tiles and
+    // the nearest pairs, which evaluate Phi) go first
     std::stable_sort(v.begin(), v.end(), [](const Strip &a, const Strip &b) {
-        return (a.j1 - a.j0) > (b.j1 - b.j0);
+        if (a.j1 - a.j0 != b.j1 - b.j0) return (a.j1 - a.j0) > (b.j1 - b.j0);
+        return (a.j0 == a.I) && (b.j0 != b.I);
     });
     const size_t sb = v.size() * sizeof(Strip);
     if (sb > c->strips_bytes) {
@@ -744,7 +747,7 @@ int hmc_enqueue(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, 
                 c->graph = nullptr;
             }
         }
-        if (!c->graph) e = cudaGraphInstantiate(&c->graph, g, 0);
+        if (!c->graph) e = cudaGraphInstantiate(&c->graph, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             c->graph = nullptr;
@@ -1831,7 +1834,8 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
         node_off.push_back(static_cast<int32_t>(nodes.size()));
         tip_off.push_back(static_cast<int32_t>(tip_items.size()));
         const int64_t m = static_cast<int64_t>(mem.size()), kt = static_cast<int64_t>(tip_items.size()) - tip0;
-        const int64_t fp = m * static_cast<int64_t>(sizeof(TreeNode)) + (2 * m + kt) * d * 8;
+        const int64_t n_lv = static_cast<int64_t>(lv_start.size()) - tree_lv.back();
+        const int64_t fp = m * static_cast<int64_t>(sizeof(TreeNode)) + (2 * m + kt) * d * 8 + 4 * n_lv;
         max_fp = std::max(max_fp, fp);
         scr_off.push_back(scr_total);
         scr_total += (2 * m + kt) * d;
@@ -1840,7 +1844,9 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
     // ---- device copies
     drop();
     if (!c->tree_stream) {
-        CU(cudaStreamCreateWithFlags(&c->tree_stream, cudaStreamNonBlocking));
+        int lo = 0, hi = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CU(cudaStreamCreateWithPriority(&c->tree_stream, cudaStreamNonBlocking, hi));
         CU(cudaEventCreateWithFlags(&c->tree_fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&c->tree_join, cudaEventDisableTiming));
     }
@@ -1963,17 +1969,28 @@ int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *
     };
     RwmhArgs a{};
     void *p = nullptr;
-    if (inj) {
+    {
         int st;
         if ((st = alloc(&p, n_prop * sizeof(int64_t)))) return cleanup(st);
         a.items = static_cast<const int64_t *>(p);
-        cudaMemcpyAsync(p, items, n_prop * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
         if ((st = alloc(&p, static_cast<size_t>(n_prop) * d * sizeof(double)))) return cleanup(st);
         a.z = static_cast<const double *>(p);
-        cudaMemcpyAsync(p, z_all, static_cast<size_t>(n_prop) * d * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if ((st = alloc(&p, n_prop * sizeof(double)))) return cleanup(st);
-        a.u = static_cast<const double *>(p);
-        cudaMemcpyAsync(p, u_all, n_prop * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        a.logu = static_cast<const double *>(p);
+    }
+    if (inj) {
+        std::vector<double> lu(n_prop);
+        for (int t = 0; t < n_prop; ++t) lu[t] = std::log(u_all[t]);
+        cudaError_t e = cudaMemcpyAsync(const_cast<int64_t *>(a.items), items, n_prop * sizeof(int64_t),
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(const_cast<double *>(a.z), z_all, static_cast<size_t>(n_prop) * d * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(const_cast<double *>(a.logu), lu.data(), n_prop * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // lu goes out of scope
+        if (e != cudaSuccess) return cleanup(fail(c, MDS_ERR_CUDA, "rwmh: %s", cudaGetErrorString(e)));
     }
     int st;
     if ((st = alloc(&p, n_prop * sizeof(int32_t)))) return cleanup(st);
@@ -1984,6 +2001,7 @@ int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *
     a.y = c->y;
     a.nt = static_cast<int32_t>(c->nt);
     a.inv = c->reordered ? c->inv_d : nullptr;
+    a.perm = c->reordered ? c->perm_d : nullptr;
     a.x = c->x;
     a.fp64 = c->fp64;
     a.sigma = c->sigma;
@@ -1995,7 +2013,13 @@ int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *
     a.iter0 = c->rw_iter;
     a.xmax_bits = c->fp64 ? nullptr : c->xmax_bits;
     a.err = c->err;
-    cudaError_t e = launch_rwmh(a, d, c->stream);
+    // X in shared memory when it fits (160 KB)
+    a.x_in_smem = static_cast<int64_t>(c->n) * d * static_cast<int64_t>(elem(c)) <= 160 * 1024;
+    cudaError_t e = cudaSuccess;
+    if (!inj)
+        e = launch_rwmh_draws(a, d, const_cast<int64_t *>(a.items), const_cast<double *>(a.z),
+                              const_cast<double *>(a.logu), c->stream);
+    if (e == cudaSuccess) e = launch_rwmh(a, d, c->stream);
     if (e != cudaSuccess) return cleanup(fail(c, MDS_ERR_CUDA, "rwmh: %s", cudaGetErrorString(e)));
     std::vector<int32_t> acc(n_prop);
     std::vector<double> dl(n_prop);

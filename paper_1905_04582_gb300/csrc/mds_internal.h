@@ -384,13 +384,15 @@ struct RwmhArgs {
     const float *y;           // tile-packed Y
     int32_t nt;
     const int32_t *inv;       // slot of each item (locality order), or null
+    const int32_t *perm;      // item at each slot, or null
     void *x;                  // [N][D] state (float or double), updated in place
     bool fp64;
     double sigma, lambda, step;
     int32_t n_prop;
-    const int64_t *items;     // injected draws (device) or null: Philox
+    const int64_t *items;     // the draws (device; injected, or from rwmh_draws_kernel)
     const double *z;          // [n_prop][D]
-    const double *u;          // [n_prop]
+    const double *logu;       // [n_prop] log of the uniforms
+    bool x_in_smem;           // keep X in shared memory (N D values fit)
     uint64_t seed;
     uint32_t chain;
     int64_t iter0;            // Philox counter of the first proposal
@@ -400,6 +402,9 @@ struct RwmhArgs {
     unsigned *err;
 };
 cudaError_t launch_rwmh(const RwmhArgs &a, int d, cudaStream_t s);
+// Philox draws of the proposals of `a` (counters as in the chain) into
+// device arrays: items [n_prop], z [n_prop][D], log u [n_prop].
+cudaError_t launch_rwmh_draws(const RwmhArgs &a, int d, int64_t *items, double *z, double *logu, cudaStream_t s);
 
 // Y ingest: rows [r0, r1) of the caller's Y (full or packed layout; the
 // pointer addresses row r0) into the tile-packed FP32 layout.  Entries read

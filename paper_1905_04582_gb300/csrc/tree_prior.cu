@@ -91,10 +91,17 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_constant__ TreeArgs a) {
     extern __shared__ __align__(16) unsigned char tsm[];
     __shared__ double sm[kTreeThreads / 32];
+    __shared__ double s_sinv[D * D], s_mu[D];
     const T *x = static_cast<const T *>(a.x);
     const int tid = threadIdx.x;
     double acc = 0.0;  // this thread's quadratic terms (fixed node assignment)
     const int t = blockIdx.x;
+    if (tid < D * D) s_sinv[tid] = a.sigma_inv[tid];
+    if (tid < D) s_mu[tid] = a.mu[tid];
+    TreeArgs b = a;  // the same arguments, with Sigma^-1 and mu read from shared memory
+    b.sigma_inv = s_sinv;
+    b.mu = s_mu;
+    __syncthreads();
     if (t < a.n_trees) {
         const int m = a.node_off[t + 1] - a.node_off[t];
         const int k = a.tip_off[t + 1] - a.tip_off[t];
@@ -118,19 +125,27 @@ __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_c
         double *tx = dn + static_cast<int64_t>(m) * D;
         for (int i = tid; i < k * D; i += kTreeThreads)
             tx[i] = static_cast<double>(x[static_cast<int64_t>(tips[i / D]) * D + i % D]);
-        __syncthreads();
-        // ---- post-order: levels [lv0, lv1) of this tree
+        // the tree's level bounds, read at every level: in shared memory too
         const int lv0 = a.tree_lv[t], lv1 = a.tree_lv[t + 1];
-        for (int lv = lv0; lv < lv1; ++lv) {
-            const int end = lv + 1 < lv1 ? a.lv_start[lv + 1] : m;
-            for (int idx = a.lv_start[lv] + tid; idx < end; idx += kTreeThreads) {
+        const int32_t *lvs = a.lv_start + lv0;
+        if (a.smem_bytes > 0) {
+            int32_t *slv = reinterpret_cast<int32_t *>(tx + static_cast<int64_t>(k) * D);
+            for (int i = tid; i < lv1 - lv0; i += kTreeThreads) slv[i] = lvs[i];
+            lvs = slv;
+        }
+        __syncthreads();
+        // ---- post-order: levels [lv0, lv1) of this tree (lvs relative to lv0)
+        const int nlv = lv1 - lv0;
+        for (int lv = 0; lv < nlv; ++lv) {
+            const int end = lv + 1 < nlv ? lvs[lv + 1] : m;
+            for (int idx = lvs[lv] + tid; idx < end; idx += kTreeThreads) {
                 const TreeNode nd = rec[idx];
                 double ma[D], mb[D], dv[D];
                 mean_of<D>(up, tx, nd.c0, ma);
                 mean_of<D>(up, tx, nd.c1, mb);
 #pragma unroll
                 for (int c = 0; c < D; ++c) dv[c] = ma[c] - mb[c];
-                acc = fma(-0.5 * nd.cinv, quad_form<D>(a.sigma_inv, dv), acc);
+                acc = fma(-0.5 * nd.cinv, quad_form<D>(s_sinv, dv), acc);
 #pragma unroll
                 for (int c = 0; c < D; ++c) up[static_cast<int64_t>(idx) * D + c] = fma(nd.alpha, dv[c], mb[c]);
             }
@@ -141,16 +156,16 @@ __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_c
         if (tid == 0) {
             double dv[D];
 #pragma unroll
-            for (int c = 0; c < D; ++c) dv[c] = up[static_cast<int64_t>(m - 1) * D + c] - a.mu[c];
-            acc = fma(-0.5 * a.root_cinv[t], quad_form<D>(a.sigma_inv, dv), acc);
+            for (int c = 0; c < D; ++c) dv[c] = up[static_cast<int64_t>(m - 1) * D + c] - s_mu[c];
+            acc = fma(-0.5 * a.root_cinv[t], quad_form<D>(s_sinv, dv), acc);
 #pragma unroll
-            for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(m - 1) * D + c] = a.mu[c];
+            for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(m - 1) * D + c] = s_mu[c];
         }
         __syncthreads();
         // ---- pre-order: the same levels from the root down
-        for (int lv = lv1 - 1; lv >= lv0; --lv) {
-            const int end = lv + 1 < lv1 ? a.lv_start[lv + 1] : m;
-            for (int idx = a.lv_start[lv] + tid; idx < end; idx += kTreeThreads) {
+        for (int lv = nlv - 1; lv >= 0; --lv) {
+            const int end = lv + 1 < nlv ? lvs[lv + 1] : m;
+            for (int idx = lvs[lv] + tid; idx < end; idx += kTreeThreads) {
                 const TreeNode nd = rec[idx];
                 double mk[D], m0[D], m1[D];
 #pragma unroll
@@ -165,14 +180,14 @@ __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_c
                 }
                 if (nd.c0 < 0) {
                     const int tp = -nd.c0 - 1;
-                    tip_gradient<D>(a, tips[tp], tx + static_cast<int64_t>(tp) * D, d0, nd.g0);
+                    tip_gradient<D>(b, tips[tp], tx + static_cast<int64_t>(tp) * D, d0, nd.g0);
                 } else {
 #pragma unroll
                     for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(nd.c0) * D + c] = d0[c];
                 }
                 if (nd.c1 < 0) {
                     const int tp = -nd.c1 - 1;
-                    tip_gradient<D>(a, tips[tp], tx + static_cast<int64_t>(tp) * D, d1, nd.g1);
+                    tip_gradient<D>(b, tips[tp], tx + static_cast<int64_t>(tp) * D, d1, nd.g1);
                 } else {
 #pragma unroll
                     for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(nd.c1) * D + c] = d1[c];
@@ -188,14 +203,14 @@ __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_c
             double m[D], e[D];
 #pragma unroll
             for (int q = 0; q < D; ++q) {
-                m[q] = a.mu[q];
+                m[q] = s_mu[q];
                 e[q] = static_cast<double>(x[i * D + q]);
             }
             double dv[D];
 #pragma unroll
             for (int q = 0; q < D; ++q) dv[q] = e[q] - m[q];
-            acc = fma(-0.5 * g, quad_form<D>(a.sigma_inv, dv), acc);
-            tip_gradient<D>(a, i, e, m, g);
+            acc = fma(-0.5 * g, quad_form<D>(s_sinv, dv), acc);
+            tip_gradient<D>(b, i, e, m, g);
         }
     }
     const double tot = block_sum(acc, sm);
@@ -221,8 +236,21 @@ cudaError_t launch_t(const TreeArgs &a, int grid, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_bytes = a.smem_bytes;
     }
-    tree_prior_kernel<D, T><<<grid, kTreeThreads, a.smem_bytes, s>>>(a);
-    return cudaGetLastError();
+    // the highest stream priority, so that its few CTAs get SMs ahead of a
+    // concurrent pair pass's pending CTAs
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTreeThreads);
+    cfg.dynamicSmemBytes = static_cast<size_t>(a.smem_bytes);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = hi;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tree_prior_kernel<D, T>, a);
 }
 
 template <int D>
