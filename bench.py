@@ -53,7 +53,10 @@ def fp32_ops_per_pair(d, far_frac=0.0):
     return (1.0 - far_frac) * (8 * d + 22) + far_frac * (8 * d + 9)
 
 
-PAIR_KERNEL_SOURCES = ("pair_kernel.cu", "pair_math.cuh", "mds_internal.h", "mills_ratio_coeffs.h")
+PAIR_KERNEL_SOURCES = ("pair_kernel.cu", "pair_math.cuh", "mills_ratio_coeffs.h")
+# the part of mds_internal.h the pair kernel is compiled from: the tile
+# geometry through the end of its argument struct, and the error bits
+PAIR_KERNEL_INTERNAL = (("// Tile geometry of the pair pass.", "cudaError_t launch_pair_batch"),)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_f32_kernel_N5392_D2_traffic.txt")
 
 
@@ -61,9 +64,14 @@ def pair_kernel_sha256():
     """Hash of the sources the FP32C pair kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1905_04582_gb300", "csrc")
     for name in PAIR_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1905_04582_gb300", "csrc", name), "rb") as f:
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
+    text = open(os.path.join(csrc, "mds_internal.h")).read()
+    for begin, end in PAIR_KERNEL_INTERNAL:
+        i, j = text.index(begin), text.index(end)
+        h.update(text[i:j].encode())
     return h.hexdigest()
 
 
@@ -541,7 +549,7 @@ def run_batch(args):
     acc, dh = b.hmc(args.steps, N_LEAPFROG, [5e-4] * len(ds), seed=2)
     wall = time.perf_counter() - t0
     alu_peak = _alu_peak_tflops()
-    print(json.dumps({"batch": True, "datasets": [w.n for w in ds], "chains_per_dataset": chains,
+    print(json.dumps({"batch": True, "order": "caller", "datasets": [w.n for w in ds], "chains_per_dataset": chains,
                       "strip": b.get_strip(), "ms_per_pass": ms, "pair_evals_per_pass": evals,
                       "pair_evals_per_s": evals / (ms / 1e3),
                       "alu": {"achieved_tflops": evals * fp32_ops_per_pair(2) / (ms / 1e3) / 1e12,
@@ -715,6 +723,32 @@ def run_mixing(args):
     return 0
 
 
+def run_rwmh_only(args):
+    """Proposals per second of the single-item random-walk sampler at
+    N = 5392 (locality order), the command its kernel profile is taken with."""
+    import torch
+    from paper_1905_04582_gb300 import build as B
+    from paper_1905_04582_gb300 import workloads as W
+    from paper_1905_04582_gb300.mds import MDS
+    B.build()
+    torch.cuda.set_device(0)
+    wl = W.paper_scale()
+    with MDS(wl.n, wl.d, "fp32c") as m:
+        m.set_data(wl.y_packed)
+        m.set_locations(wl.x_eval)
+        m.set_sigma(wl.sigma)
+        m.reorder()
+        m.rwmh(args.props, 0.008, seed=1)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        acc, _ = m.rwmh(args.props, 0.008, seed=2)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    print(json.dumps({"rwmh_only": True, "n": wl.n, "proposals": args.props, "s": dt,
+                      "proposals_per_s": args.props / dt, "accept_rate": float(np.mean(acc))}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -735,6 +769,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="batched datasets x chains")
     ap.add_argument("--tree", action="store_true", help="HMC with the phylogenetic prior (section 2.2)")
     ap.add_argument("--mixing", action="store_true", help="ESS/s of HMC against single-item random-walk MH")
+    ap.add_argument("--rwmh-only", action="store_true", help="proposals/s of the random-walk sampler")
+    ap.add_argument("--props", type=int, default=5392)
     ap.add_argument("--order", default="locality", choices=["locality", "caller"],
                     help="tile layouts in the locality order (mds_reorder) or the caller's item order")
     args = ap.parse_args()
@@ -749,6 +785,8 @@ def main():
         return run_tree(args)
     if args.mixing:
         return run_mixing(args)
+    if args.rwmh_only:
+        return run_rwmh_only(args)
     if args.pass_only:
         return run_pass_only(args)
     if args.warmup < 3:

@@ -302,6 +302,38 @@ int build_strips(mds_ctx *c, int strip) {
     return MDS_OK;
 }
 
+// Longest-processing-time-first order of the strips from the far-block
+// counts of the last FP32C pass: a strip costs about its tiles' warp blocks,
+// a far block (Phi terms skipped) 25/38 of one that evaluates Phi.  Only the
+// assignment of strips to CTAs changes (results stay within tolerance; the
+// scalar partials are summed in the new order).
+int order_strips_by_cost(mds_ctx *c) {
+    if (c->fp64 || c->n_strips <= 0) return MDS_OK;
+    std::vector<int32_t> parts(static_cast<size_t>(c->n_strips) * kPairWarps);
+    CU(cudaMemcpyAsync(parts.data(), c->far_part, parts.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    const int n = c->n_strips;
+    std::vector<double> cost(n);
+    for (int k = 0; k < n; ++k) {
+        const Strip &st = c->strips_host[k];
+        int32_t far = 0;
+        for (int w = 0; w < kPairWarps; ++w) far += parts[static_cast<size_t>(k) * kPairWarps + w];
+        const double blocks = static_cast<double>(st.j1 - st.j0) * kPairWarps * 2;
+        cost[k] = (blocks - far) * 38.0 + far * 25.0;
+    }
+    std::vector<int> idx(n);
+    for (int k = 0; k < n; ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<Strip> v(n);
+    for (int k = 0; k < n; ++k) v[k] = c->strips_host[idx[k]];
+    c->strips_host = v;
+    CU(cudaMemcpyAsync(c->strips, v.data(), v.size() * sizeof(Strip), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->grad_valid = false;
+    c->gen++;
+    return MDS_OK;
+}
+
 constexpr int kMaxStrip = 64;  // bounds the FP32 row sums of a lane (<= 256 terms)
 
 // Choose the split quantum from max |x| of locations the caller sets and
@@ -1555,7 +1587,20 @@ int mds_locality_order(int64_t n, int32_t d, const double *x, int32_t *perm) {
     return MDS_OK;
 }
 
-int mds_reorder(mds_ctx *c) {
+namespace {
+int reorder_ctx(mds_ctx *c, bool order_strips);
+}
+
+int mds_reorder(mds_ctx *c) { return reorder_ctx(c, true); }
+
+}  // extern "C"
+
+namespace {
+
+// The locality order of the current locations; `order_strips`: then one
+// counted pass and the strips in order of their cost (single contexts; a
+// batch builds its own strip list).
+int reorder_ctx(mds_ctx *c, bool order_strips) {
     CHECK(check_ctx(c));
     if (!c->y_owned) return fail(c, MDS_ERR_STATE, "the chains of a batch share Y and cannot be reordered");
     if (!c->have_data || !c->have_x) return fail(c, MDS_ERR_STATE, "mds_reorder needs data and locations");
@@ -1575,9 +1620,19 @@ int mds_reorder(mds_ctx *c) {
         cudaError_t e = launch_resplit(xstate(c), np, c->d, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "reorder: %s", cudaGetErrorString(e));
+        // one counted pass at the autotuned strip length, then the strips in
+        // order of their cost
+        if (order_strips && c->have_sigma) {
+            CHECK(evaluate(c));
+            CHECK(order_strips_by_cost(c));
+        }
     }
     return MDS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int mds_far_blocks(mds_ctx *c, int64_t *far, int64_t *total) {
     CHECK(check_ctx(c));
@@ -1835,12 +1890,28 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
         tip_off.push_back(static_cast<int32_t>(tip_items.size()));
         const int64_t m = static_cast<int64_t>(mem.size()), kt = static_cast<int64_t>(tip_items.size()) - tip0;
         const int64_t n_lv = static_cast<int64_t>(lv_start.size()) - tree_lv.back();
-        const int64_t fp = m * static_cast<int64_t>(sizeof(TreeNode)) + (2 * m + kt) * d * 8 + 4 * n_lv;
+        // records, up / down means of internal nodes, tip locations, tip
+        // downward means and gradient scales, level bounds
+        const int64_t fp = m * static_cast<int64_t>(sizeof(TreeNode)) + ((2 * m + 2 * kt) * d + kt) * 8 + 4 * n_lv;
         max_fp = std::max(max_fp, fp);
         scr_off.push_back(scr_total);
-        scr_total += (2 * m + kt) * d;
+        scr_total += (2 * m + 2 * kt) * d + kt;
     }
     tree_lv.push_back(static_cast<int32_t>(lv_start.size()));
+    // per tree, the top run of levels with at most 32 nodes (one warp's work)
+    std::vector<int32_t> tree_small(roots.size());
+    for (size_t t = 0; t < roots.size(); ++t) {
+        const int32_t l0 = tree_lv[t], l1 = tree_lv[t + 1];
+        const int32_t m_t = node_off[t + 1] - node_off[t];
+        int32_t small = l1 - l0;
+        while (small > 0) {
+            const int32_t a0 = lv_start[l0 + small - 1];
+            const int32_t a1 = small < l1 - l0 ? lv_start[l0 + small] : m_t;
+            if (a1 - a0 > 32) break;
+            --small;
+        }
+        tree_small[t] = small;
+    }
     // ---- device copies
     drop();
     if (!c->tree_stream) {
@@ -1870,6 +1941,8 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
     ta.lv_start = static_cast<const int32_t *>(p);
     CHECK(up(&p, tree_lv.data(), tree_lv.size() * sizeof(int32_t)));
     ta.tree_lv = static_cast<const int32_t *>(p);
+    CHECK(up(&p, tree_small.data(), tree_small.size() * sizeof(int32_t)));
+    ta.tree_small = static_cast<const int32_t *>(p);
     CHECK(up(&p, root_cinv.data(), root_cinv.size() * sizeof(double)));
     ta.root_cinv = static_cast<const double *>(p);
     CHECK(up(&p, lone.data(), lone.size() * sizeof(int32_t)));
@@ -2013,6 +2086,14 @@ int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *
     a.iter0 = c->rw_iter;
     a.xmax_bits = c->fp64 ? nullptr : c->xmax_bits;
     a.err = c->err;
+    {
+        const PairArgs pa = pair_args(c);  // the FP32 Phi constants of the pass
+        for (int k = 0; k < 4; ++k) {
+            a.mp[k] = pa.mp[k].x;
+            a.md[k] = pa.md[k].x;
+        }
+        a.c_phi = pa.c_phi.x;
+    }
     // X in shared memory when it fits (160 KB)
     a.x_in_smem = static_cast<int64_t>(c->n) * d * static_cast<int64_t>(elem(c)) <= 160 * 1024;
     cudaError_t e = cudaSuccess;

@@ -359,6 +359,7 @@ struct TreeArgs {
     const int32_t *lv_start; // each level's first record, relative to its tree (a tree's last level
                              // ends at its node count)
     const int32_t *tree_lv;  // first level of each tree (+ end)
+    const int32_t *tree_small; // per tree: first level (relative) of the top run of levels with <= 32 nodes
     const double *root_cinv; // per tree: 1 / (v_root + tau0)
     int32_t n_lone;
     const int32_t *lone;     // unsequenced items (tips that are roots)
@@ -367,7 +368,7 @@ struct TreeArgs {
     const double *mu;        // D
     double const_term;       // sum of the log-determinant and 2 pi terms
     int32_t smem_bytes;      // > 0: a tree's CTA keeps its records, messages and tips in shared memory
-    double *scratch;         // otherwise: per tree (2 m_t + k_t) x D doubles at scr_off[t]
+    double *scratch;         // otherwise: per tree (2 m_t + 2 k_t) x D + k_t doubles at scr_off[t]
     const int64_t *scr_off;
     double *grad;            // [N][D] d log p / dX (out)
     double *part;            // [n_trees + 1] per-CTA sums (scratch)
@@ -400,6 +401,10 @@ struct RwmhArgs {
     double *dl_out;           // [n_prop] log-target differences (optional)
     unsigned *xmax_bits;      // FP32C running max |x| (atomicMax), or null
     unsigned *err;
+    // FP32 Phi constants (sigma folded in), as in PairArgs: -P(delta/sigma)/sqrt(2 pi)
+    // and D(delta/sigma) in powers of delta, and -log2(e) / (2 sigma^2)
+    float mp[4], md[4];
+    float c_phi;
 };
 cudaError_t launch_rwmh(const RwmhArgs &a, int d, cudaStream_t s);
 // Philox draws of the proposals of `a` (counters as in the chain) into

@@ -27,18 +27,32 @@ namespace {
 constexpr int kRwThreads = 1024;
 constexpr int kRwUnroll = 4;  // slots per thread per round
 
-// r_ij of Eq. (2) at distance delta; the log Phi term is dropped (FP32 path
-// only) where z >= 8.
+// r_ij(delta_old) - r_ij(delta_new) of Eq. (2) for one pair.  FP64: CUDA's
+// erfc and log1p.  FP32: Phi(z) = D(z) - phi(z) P(z) over D(z), the Mills-ratio
+// rational of the pair pass (coefficients folded with sigma on the host), so
+// the difference of the log Phi terms is one log2 of a ratio; where both
+// z >= 8 it is below 6.3e-16 and dropped.
+__device__ __forceinline__ float poly3(const float *c, float d) { return fmaf(fmaf(fmaf(c[3], d, c[2]), d, c[1]), d, c[0]); }
+
+__device__ __forceinline__ float phi_term_ratio(const RwmhArgs &a, float d0, float d1) {
+    // D Phi = D + exp(-z^2/2) (-P / sqrt(2 pi)) at each distance
+    const float e0 = exp2f(a.c_phi * d0 * d0), e1 = exp2f(a.c_phi * d1 * d1);
+    const float dd0 = poly3(a.md, d0), dd1 = poly3(a.md, d1);
+    const float den0 = fmaf(e0, poly3(a.mp, d0), dd0), den1 = fmaf(e1, poly3(a.mp, d1), dd1);
+    // log Phi(z0) - log Phi(z1) = ln((den0 dd1) / (dd0 den1))
+    return 0.69314718055994531f * __log2f((den0 * dd1) / (dd0 * den1));
+}
+
 template <typename T>
-__device__ __forceinline__ T r_term(T y, T delta, T half_inv_s2, T inv_s_sqrt2, T far_delta) {
-    const T e = y - delta;
-    T lphi = T(0);
+__device__ __forceinline__ T r_diff(const RwmhArgs &a, T y, T d0, T d1, T half_inv_s2, T inv_s_sqrt2, T far_delta) {
+    const T e0 = y - d0, e1 = y - d1;
+    T q = (e0 * e0 - e1 * e1) * half_inv_s2;
     if constexpr (sizeof(T) == 4) {
-        if (delta < far_delta) lphi = log1pf(-0.5f * erfcf(delta * inv_s_sqrt2));
+        if (d0 < far_delta || d1 < far_delta) q += phi_term_ratio(a, d0, d1);
     } else {
-        lphi = log1p(-0.5 * erfc(delta * inv_s_sqrt2));
+        q += log1p(-0.5 * erfc(d0 * inv_s_sqrt2)) - log1p(-0.5 * erfc(d1 * inv_s_sqrt2));
     }
-    return e * e * half_inv_s2 + lphi;
+    return q;
 }
 
 // Draws of proposals [0, n_prop) from Philox4x32-10, in parallel: proposal
@@ -76,7 +90,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant__ RwmhArgs a) {
     extern __shared__ __align__(16) unsigned char rsm[];
     __shared__ T xo[D], xn[D];
-    __shared__ int64_t s_item;
+    __shared__ int64_t s_item, s_slot;
     __shared__ double sm[kRwThreads / 32];
     T *xg = static_cast<T *>(a.x);
     T *xs = a.x_in_smem ? reinterpret_cast<T *>(rsm) : xg;
@@ -96,21 +110,23 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
         my_item[r] = (slots_in_regs && sj < n) ? static_cast<int32_t>(a.perm ? a.perm[sj] : sj) : -1;
     }
     // thread 0: the draws of the current proposal (and the next one, prefetched)
-    int64_t i_cur = 0;
+    int64_t i_cur = 0, si_cur = 0;
     double z_cur[D], lu_cur = 0.0;
     if (tid == 0 && a.n_prop > 0) {
         i_cur = a.items[0];
+        si_cur = (a.inv && i_cur >= 0 && i_cur < n) ? a.inv[i_cur] : i_cur;
 #pragma unroll
         for (int k = 0; k < D; ++k) z_cur[k] = a.z[k];
         lu_cur = a.logu[0];
     }
     __syncthreads();
     for (int t = 0; t < a.n_prop; ++t) {
-        int64_t i_nxt = 0;
+        int64_t i_nxt = 0, si_nxt = 0;
         double z_nxt[D], lu_nxt = 0.0;
         if (tid == 0) {
             if (t + 1 < a.n_prop) {
                 i_nxt = a.items[t + 1];
+                si_nxt = (a.inv && i_nxt >= 0 && i_nxt < n) ? a.inv[i_nxt] : i_nxt;
 #pragma unroll
                 for (int k = 0; k < D; ++k) z_nxt[k] = a.z[static_cast<int64_t>(t + 1) * D + k];
                 lu_nxt = a.logu[t + 1];
@@ -118,11 +134,13 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
             if (i_cur < 0 || i_cur >= n) {
                 atomicOr(a.err, kErrBadArgs);
                 i_cur = 0;
+                si_cur = a.inv ? a.inv[0] : 0;
                 lu_cur = INFINITY;  // never accepted
 #pragma unroll
                 for (int k = 0; k < D; ++k) z_cur[k] = 0.0;
             }
             s_item = i_cur;
+            s_slot = si_cur;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const T v = xs[i_cur * D + k];
@@ -132,8 +150,11 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
         }
         __syncthreads();
         const int64_t i = s_item;
-        const int64_t si = a.inv ? a.inv[i] : i;
-        double acc = 0.0;
+        const int64_t si = s_slot;
+        // this thread's share of the row: a compensated sum in the pair
+        // arithmetic's precision (FP64 conversions run at 1/64 rate on this
+        // GPU), widened to FP64 once before the block sum
+        T acc_s = T(0), acc_c = T(0);
         const int rounds = static_cast<int>((n + kRwThreads - 1) / kRwThreads);
         for (int r0 = 0; r0 < rounds; r0 += kRwUnroll) {
             int64_t item[kRwUnroll];
@@ -173,14 +194,26 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
                     d1 += a1 * a1;
                 }
                 const T y = static_cast<T>(yv[u]);
-                acc += static_cast<double>(r_term<T>(y, sqrt(d0), half_inv_s2, inv_s_sqrt2, far_delta) -
-                                           r_term<T>(y, sqrt(d1), half_inv_s2, inv_s_sqrt2, far_delta));
+                const T v = r_diff<T>(a, y, sqrt(d0), sqrt(d1), half_inv_s2, inv_s_sqrt2, far_delta);
+                const T yk = v - acc_c;  // Kahan
+                const T tk = acc_s + yk;
+                acc_c = (tk - acc_s) - yk;
+                acc_s = tk;
             }
         }
-        // fixed-order block sum
+        // fixed-order block sum: (sum, compensation) pairs through the warp,
+        // FP64 only for the 32 warp totals
+        T hs = acc_s, hc = acc_c;
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) sm[warp] = acc;
+        for (int o = 16; o >= 1; o >>= 1) {
+            const T os = __shfl_xor_sync(0xffffffffu, hs, o), oc = __shfl_xor_sync(0xffffffffu, hc, o);
+            const T s2 = hs + os;
+            const T bb = s2 - hs;
+            const T err = (hs - (s2 - bb)) + (os - bb);  // exact rounding error of hs + os
+            hs = s2;
+            hc = hc + oc - err;
+        }
+        if (lane == 0) sm[warp] = static_cast<double>(hs) - static_cast<double>(hc);
         __syncthreads();
         if (tid == 0) {
             double dl = 0.0;
@@ -207,6 +240,7 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
             if (a.acc_out) a.acc_out[t] = keep ? 1 : 0;
             if (a.dl_out) a.dl_out[t] = lp;
             i_cur = i_nxt;
+            si_cur = si_nxt;
 #pragma unroll
             for (int k = 0; k < D; ++k) z_cur[k] = z_nxt[k];
             lu_cur = lu_nxt;

@@ -59,22 +59,6 @@ __device__ __forceinline__ void mean_of(const double *up, const double *tx, int 
     for (int k = 0; k < D; ++k) m[k] = src[k];
 }
 
-// -Sigma^-1 (x - m) g into grad[item]
-template <int D>
-__device__ __forceinline__ void tip_gradient(const TreeArgs &a, int64_t item, const double *xv, const double (&m)[D],
-                                             double g) {
-    double e[D];
-#pragma unroll
-    for (int q = 0; q < D; ++q) e[q] = xv[q] - m[q];
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < D; ++q) s = fma(a.sigma_inv[r * D + q], e[q], s);
-        a.grad[item * D + r] = -s * g;
-    }
-}
-
 __device__ __forceinline__ double block_sum(double v, double *sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -87,6 +71,11 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return t;  // valid in thread 0
 }
 
+// The level-synchronous traversals move only means (a few dependent FP64
+// operations per node, so each level costs little more than a barrier); the
+// quadratic forms of the contrasts and the tips' gradients depend on the
+// finished messages alone and are computed afterwards by every thread in
+// parallel.
 template <int D, typename T>
 __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_constant__ TreeArgs a) {
     extern __shared__ __align__(16) unsigned char tsm[];
@@ -94,14 +83,10 @@ __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_c
     __shared__ double s_sinv[D * D], s_mu[D];
     const T *x = static_cast<const T *>(a.x);
     const int tid = threadIdx.x;
-    double acc = 0.0;  // this thread's quadratic terms (fixed node assignment)
+    double acc = 0.0;  // this thread's quadratic terms (fixed assignment)
     const int t = blockIdx.x;
     if (tid < D * D) s_sinv[tid] = a.sigma_inv[tid];
     if (tid < D) s_mu[tid] = a.mu[tid];
-    TreeArgs b = a;  // the same arguments, with Sigma^-1 and mu read from shared memory
-    b.sigma_inv = s_sinv;
-    b.mu = s_mu;
-    __syncthreads();
     if (t < a.n_trees) {
         const int m = a.node_off[t + 1] - a.node_off[t];
         const int k = a.tip_off[t + 1] - a.tip_off[t];
@@ -109,108 +94,181 @@ __global__ void __launch_bounds__(kTreeThreads) tree_prior_kernel(const __grid_c
         const TreeNode *rec;
         double *up;
         if (a.smem_bytes > 0) {
-            // stage the tree's records in shared memory (as 8-byte words)
+            // stage the tree's records in shared memory, in batches of
+            // independent loads (the copy is latency-bound)
             TreeNode *srec = reinterpret_cast<TreeNode *>(tsm);
             const uint64_t *src = reinterpret_cast<const uint64_t *>(a.nodes + a.node_off[t]);
             uint64_t *dst = reinterpret_cast<uint64_t *>(srec);
             constexpr int kWords = sizeof(TreeNode) / 8;
-            for (int i = tid; i < m * kWords; i += kTreeThreads) dst[i] = src[i];
+            constexpr int kB = 8;
+            const int words = m * kWords;
+            for (int i0 = tid; i0 < words; i0 += kTreeThreads * kB) {
+                uint64_t w[kB];
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const int i = i0 + b * kTreeThreads;
+                    if (i < words) w[b] = src[i];
+                }
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const int i = i0 + b * kTreeThreads;
+                    if (i < words) dst[i] = w[b];
+                }
+            }
             rec = srec;
             up = reinterpret_cast<double *>(srec + m);
         } else {
             rec = a.nodes + a.node_off[t];
             up = a.scratch + a.scr_off[t];
         }
-        double *dn = up + static_cast<int64_t>(m) * D;
-        double *tx = dn + static_cast<int64_t>(m) * D;
-        for (int i = tid; i < k * D; i += kTreeThreads)
-            tx[i] = static_cast<double>(x[static_cast<int64_t>(tips[i / D]) * D + i % D]);
+        double *dn = up + static_cast<int64_t>(m) * D;   // downward means of internal nodes
+        double *tx = dn + static_cast<int64_t>(m) * D;   // tip locations
+        double *tdn = tx + static_cast<int64_t>(k) * D;  // downward means of tips
+        double *tg = tdn + static_cast<int64_t>(k) * D;  // 1 / downward variance of tips
+        {
+            constexpr int kB = 8;
+            for (int i0 = tid; i0 < k * D; i0 += kTreeThreads * kB) {
+                int32_t item[kB];
+                T v[kB];
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const int i = i0 + b * kTreeThreads;
+                    item[b] = i < k * D ? tips[i / D] : -1;
+                }
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const int i = i0 + b * kTreeThreads;
+                    if (item[b] >= 0) v[b] = x[static_cast<int64_t>(item[b]) * D + i % D];
+                }
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const int i = i0 + b * kTreeThreads;
+                    if (item[b] >= 0) tx[i] = static_cast<double>(v[b]);
+                }
+            }
+        }
         // the tree's level bounds, read at every level: in shared memory too
         const int lv0 = a.tree_lv[t], lv1 = a.tree_lv[t + 1];
         const int32_t *lvs = a.lv_start + lv0;
         if (a.smem_bytes > 0) {
-            int32_t *slv = reinterpret_cast<int32_t *>(tx + static_cast<int64_t>(k) * D);
+            int32_t *slv = reinterpret_cast<int32_t *>(tg + k);
             for (int i = tid; i < lv1 - lv0; i += kTreeThreads) slv[i] = lvs[i];
             lvs = slv;
         }
         __syncthreads();
-        // ---- post-order: levels [lv0, lv1) of this tree (lvs relative to lv0)
+        // ---- post-order: upward means, level by level (lvs relative to lv0).
+        // Levels from `small` up hold at most 32 nodes each (the top of the
+        // tree): warp 0 alone runs them, with warp-level barriers.
         const int nlv = lv1 - lv0;
-        for (int lv = 0; lv < nlv; ++lv) {
+        const int small = a.tree_small[t];
+        auto up_node = [&](int idx) {
+            const int c0 = rec[idx].c0, c1 = rec[idx].c1;
+            const double al = rec[idx].alpha;
+            double ma[D], mb[D];
+            mean_of<D>(up, tx, c0, ma);
+            mean_of<D>(up, tx, c1, mb);
+#pragma unroll
+            for (int c = 0; c < D; ++c) up[static_cast<int64_t>(idx) * D + c] = fma(al, ma[c] - mb[c], mb[c]);
+        };
+        for (int lv = 0; lv < small; ++lv) {
             const int end = lv + 1 < nlv ? lvs[lv + 1] : m;
-            for (int idx = lvs[lv] + tid; idx < end; idx += kTreeThreads) {
-                const TreeNode nd = rec[idx];
-                double ma[D], mb[D], dv[D];
-                mean_of<D>(up, tx, nd.c0, ma);
-                mean_of<D>(up, tx, nd.c1, mb);
-#pragma unroll
-                for (int c = 0; c < D; ++c) dv[c] = ma[c] - mb[c];
-                acc = fma(-0.5 * nd.cinv, quad_form<D>(s_sinv, dv), acc);
-#pragma unroll
-                for (int c = 0; c < D; ++c) up[static_cast<int64_t>(idx) * D + c] = fma(nd.alpha, dv[c], mb[c]);
-            }
+            for (int idx = lvs[lv] + tid; idx < end; idx += kTreeThreads) up_node(idx);
             __syncthreads();
         }
-        // the root (the last record): m_root - mu ~ N(0, (v_root + tau0) Sigma);
-        // its downward mean is mu
-        if (tid == 0) {
-            double dv[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) dv[c] = up[static_cast<int64_t>(m - 1) * D + c] - s_mu[c];
-            acc = fma(-0.5 * a.root_cinv[t], quad_form<D>(s_sinv, dv), acc);
-#pragma unroll
-            for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(m - 1) * D + c] = s_mu[c];
+        if (tid < 32) {
+            for (int lv = small; lv < nlv; ++lv) {
+                const int end = lv + 1 < nlv ? lvs[lv + 1] : m;
+                const int idx = lvs[lv] + tid;
+                if (idx < end) up_node(idx);
+                __syncwarp();
+            }
+            // the root's downward mean is mu
+            if (tid < D) dn[static_cast<int64_t>(m - 1) * D + tid] = s_mu[tid];
+            __syncwarp();
         }
-        __syncthreads();
-        // ---- pre-order: the same levels from the root down
-        for (int lv = nlv - 1; lv >= 0; --lv) {
-            const int end = lv + 1 < nlv ? lvs[lv + 1] : m;
-            for (int idx = lvs[lv] + tid; idx < end; idx += kTreeThreads) {
+        // ---- pre-order: downward means, from the root down (the small
+        // levels by warp 0 again, then the rest by the block)
+        auto down_node = [&](int idx) {
                 const TreeNode nd = rec[idx];
                 double mk[D], m0[D], m1[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) mk[c] = dn[static_cast<int64_t>(idx) * D + c];
                 mean_of<D>(up, tx, nd.c0, m0);
                 mean_of<D>(up, tx, nd.c1, m1);
-                double d0[D], d1[D];  // downward means of child 0 (sibling 1) and child 1
+                // child 0 (its sibling is child 1) and child 1
+                double *o0 = nd.c0 < 0 ? tdn + static_cast<int64_t>(-nd.c0 - 1) * D : dn + static_cast<int64_t>(nd.c0) * D;
+                double *o1 = nd.c1 < 0 ? tdn + static_cast<int64_t>(-nd.c1 - 1) * D : dn + static_cast<int64_t>(nd.c1) * D;
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    d0[c] = fma(nd.beta0, mk[c] - m1[c], m1[c]);
-                    d1[c] = fma(nd.beta1, mk[c] - m0[c], m0[c]);
+                    o0[c] = fma(nd.beta0, mk[c] - m1[c], m1[c]);
+                    o1[c] = fma(nd.beta1, mk[c] - m0[c], m0[c]);
                 }
-                if (nd.c0 < 0) {
-                    const int tp = -nd.c0 - 1;
-                    tip_gradient<D>(b, tips[tp], tx + static_cast<int64_t>(tp) * D, d0, nd.g0);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(nd.c0) * D + c] = d0[c];
-                }
-                if (nd.c1 < 0) {
-                    const int tp = -nd.c1 - 1;
-                    tip_gradient<D>(b, tips[tp], tx + static_cast<int64_t>(tp) * D, d1, nd.g1);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < D; ++c) dn[static_cast<int64_t>(nd.c1) * D + c] = d1[c];
-                }
+                if (nd.c0 < 0) tg[-nd.c0 - 1] = nd.g0;
+                if (nd.c1 < 0) tg[-nd.c1 - 1] = nd.g1;
+        };
+        if (tid < 32) {
+            for (int lv = nlv - 1; lv >= small; --lv) {
+                const int end = lv + 1 < nlv ? lvs[lv + 1] : m;
+                const int idx = lvs[lv] + tid;
+                if (idx < end) down_node(idx);
+                __syncwarp();
             }
+        }
+        __syncthreads();
+        for (int lv = small - 1; lv >= 0; --lv) {
+            const int end = lv + 1 < nlv ? lvs[lv + 1] : m;
+            for (int idx = lvs[lv] + tid; idx < end; idx += kTreeThreads) down_node(idx);
             __syncthreads();
         }
+        // ---- in parallel: the contrast terms of every node and the root term
+        for (int idx = tid; idx < m; idx += kTreeThreads) {
+            double ma[D], mb[D], dv[D];
+            mean_of<D>(up, tx, rec[idx].c0, ma);
+            mean_of<D>(up, tx, rec[idx].c1, mb);
+#pragma unroll
+            for (int c = 0; c < D; ++c) dv[c] = ma[c] - mb[c];
+            acc = fma(-0.5 * rec[idx].cinv, quad_form<D>(s_sinv, dv), acc);
+        }
+        if (tid == 0) {
+            double dv[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) dv[c] = up[static_cast<int64_t>(m - 1) * D + c] - s_mu[c];
+            acc = fma(-0.5 * a.root_cinv[t], quad_form<D>(s_sinv, dv), acc);
+        }
+        // ---- in parallel: the tips' gradients -Sigma^-1 (x - m) / v
+        for (int tp = tid; tp < k; tp += kTreeThreads) {
+            double e[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) e[q] = tx[static_cast<int64_t>(tp) * D + q] - tdn[static_cast<int64_t>(tp) * D + q];
+            const int64_t item = tips[tp];
+            const double g = tg[tp];
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                double sg = 0.0;
+#pragma unroll
+                for (int q = 0; q < D; ++q) sg = fma(s_sinv[r * D + q], e[q], sg);
+                a.grad[item * D + r] = -sg * g;
+            }
+        }
     } else {
+        __syncthreads();  // Sigma^-1 and mu staged
         // unsequenced items: x_i ~ N(mu, tau_u Sigma) on their own
         const double g = 1.0 / a.tau_u;
         for (int idx = tid; idx < a.n_lone; idx += kTreeThreads) {
             const int64_t i = a.lone[idx];
-            double m[D], e[D];
+            double e[D];
 #pragma unroll
-            for (int q = 0; q < D; ++q) {
-                m[q] = s_mu[q];
-                e[q] = static_cast<double>(x[i * D + q]);
+            for (int q = 0; q < D; ++q) e[q] = static_cast<double>(x[i * D + q]) - s_mu[q];
+            double qf = 0.0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                double sg = 0.0;
+#pragma unroll
+                for (int q = 0; q < D; ++q) sg = fma(s_sinv[r * D + q], e[q], sg);
+                qf = fma(e[r], sg, qf);
+                a.grad[i * D + r] = -sg * g;
             }
-            double dv[D];
-#pragma unroll
-            for (int q = 0; q < D; ++q) dv[q] = e[q] - m[q];
-            acc = fma(-0.5 * g, quad_form<D>(s_sinv, dv), acc);
-            tip_gradient<D>(b, i, e, m, g);
+            acc = fma(-0.5 * g, qf, acc);
         }
     }
     const double tot = block_sum(acc, sm);
