@@ -352,6 +352,21 @@ int mds_tree_prior(mds_ctx *ctx, double *logp, void *grad, int dtype, int where)
 int mds_rwmh(mds_ctx *ctx, int n_prop, double step, uint64_t seed, const int64_t *items, const double *z_all,
              const double *u_all, int32_t *accepted, double *dlogpi);
 
+/* Checkpoint and resume of a chain: a snapshot holds the locations and
+ * momenta (FP64, the caller's order), sigma, lambda, the Phi cut-off, the
+ * counters that drive the Philox draws (HMC iterations, sigma updates,
+ * random-walk proposals) and the accept count, and the locality order if
+ * one is set; not Y, the fold or the tree prior (set those as before).
+ * mds_get_state with buf = NULL stores the size in *bytes; else buf (host,
+ * *bytes long) receives the snapshot.  mds_set_state restores one into a
+ * context of the same N, D and precision (with the same data set): the next
+ * draws are those the saved chain would have drawn, and with the same strip
+ * length and order the continuation is bitwise identical.  Errors:
+ * INVALID_ARG (size, magic, N / D / precision mismatch), STATE (queued HMC
+ * iterations; restoring an order while a fold is set). */
+int mds_get_state(mds_ctx *ctx, void *buf, int64_t *bytes);
+int mds_set_state(mds_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Number of pairs M = N(N-1)/2 and the bytes of tile-packed Y resident on
  * the device. */
 int mds_problem_size(const mds_ctx *ctx, int64_t *pairs, int64_t *y_bytes);

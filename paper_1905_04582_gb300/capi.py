@@ -89,6 +89,8 @@ SIGNATURES = {
     "mds_set_tree_prior": (_int, [_vp, _i64, _vp, _vp, _vp, _vp, _dbl, _dbl]),
     "mds_tree_prior": (_int, [_vp, _pdbl, _vp, _int, _int]),
     "mds_rwmh": (_int, [_vp, _int, _dbl, _u64, _vp, _vp, _vp, _vp, _vp]),
+    "mds_get_state": (_int, [_vp, _vp, _pi64]),
+    "mds_set_state": (_int, [_vp, _vp, _i64]),
     "mds_set_strip": (_int, [_vp, _i32]),
     "mds_get_strip": (_int, [_vp, _pi32]),
     "mds_time_pass": (_int, [_vp, _int, _pdbl]),

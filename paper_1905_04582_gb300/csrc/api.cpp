@@ -171,7 +171,19 @@ int fail(mds_ctx *c, int code, const char *fmt, ...) {
         if (s_ != MDS_OK) return s_;     \
     } while (0)
 
+// Fault injection for tests, from the environment: MDS_FAULT=alloc makes
+// device allocations fail as out of memory, MDS_FAULT=nan plants a NaN in the
+// scalar partials of an evaluation pass, MDS_FAULT=timeout runs a probe kernel
+// before an evaluation pass whose bounded device-side wait runs out.  Each
+// is active while the variable is set; nothing is injected into captured
+// graphs.
+bool fault_is(const char *kind) {
+    const char *v = std::getenv("MDS_FAULT");
+    return v && std::strcmp(v, kind) == 0;
+}
+
 int dev_alloc(mds_ctx *c, void **p, size_t bytes) {
+    if (fault_is("alloc")) return fail(c, MDS_ERR_OOM, "cudaMalloc of %zu bytes failed (injected: MDS_FAULT=alloc)", bytes);
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaErrorMemoryAllocation) {
@@ -451,7 +463,7 @@ int harvest_prof(mds_ctx *c) {
     return MDS_OK;
 }
 
-int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s) {
+int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_nan = false) {
     PairArgs a = pair_args(c);
     const int pk = c->prof_used;
     if (c->profiling) {
@@ -484,6 +496,14 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s) {
     if (c->tree_on) {
         e = cudaStreamWaitEvent(s, c->tree_join, 0);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior join: %s", cudaGetErrorString(e));
+    }
+    if (plant_nan) {
+        // fault injection: the first strip's sum of squared residuals is NaN
+        static const double nan64 = std::nan("");
+        static const float nan32 = std::nanf("");
+        e = cudaMemcpyAsync(c->scal_part, c->fp64 ? static_cast<const void *>(&nan64) : static_cast<const void *>(&nan32),
+                            elem(c), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "fault injection: %s", cudaGetErrorString(e));
     }
     if (c->profiling) {
         CHECK(record_prof(c, c->prof_b[pk], s));
@@ -573,7 +593,11 @@ int autotune(mds_ctx *c) {
 int evaluate(mds_ctx *c) {
     CHECK(ready(c));
     CHECK(autotune(c));
-    CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+    if (fault_is("timeout")) {
+        cudaError_t e = launch_wait_probe(c->err, c->stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "wait probe: %s", cudaGetErrorString(e));
+    }
+    CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream, fault_is("nan")));
     CU(cudaGetLastError());
     CHECK(check_device_err(c, "evaluation"));
     if (c->profiling) CHECK(harvest_prof(c));
@@ -2116,6 +2140,114 @@ int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *
     if (!c->fp64) CHECK(set_split_from_xmax(c));  // the split layouts follow the moved items
     if (accepted) std::memcpy(accepted, acc.data(), n_prop * sizeof(int32_t));
     if (dlogpi) std::memcpy(dlogpi, dl.data(), n_prop * sizeof(double));
+    return MDS_OK;
+}
+
+namespace {
+// Layout of a state snapshot (host bytes): this header, then X and p
+// (N x D FP64 each, the caller's item order), then the order (N int32) when
+// the context is reordered.
+struct StateHeader {
+    uint64_t magic;
+    int64_t n;
+    int32_t d, fp64;
+    double sigma, lambda, tail_z;
+    int64_t counters[kCounters];
+    int64_t sigma_iter, rw_iter;
+    int32_t reordered, have_sigma;
+};
+constexpr uint64_t kStateMagic = 0x3154415453534D44ull;  // "DMSSTAT1"
+
+int64_t state_bytes(const mds_ctx *c) {
+    return static_cast<int64_t>(sizeof(StateHeader)) + 2 * c->n * c->d * 8 + (c->reordered ? c->n * 4 : 0);
+}
+}  // namespace
+
+int mds_get_state(mds_ctx *c, void *buf, int64_t *bytes) {
+    CHECK(check_ctx(c));
+    if (!bytes) return fail(c, MDS_ERR_INVALID_ARG, "bytes is NULL");
+    const int64_t need = state_bytes(c);
+    if (!buf) {
+        *bytes = need;
+        return MDS_OK;
+    }
+    if (*bytes < need) return fail(c, MDS_ERR_INVALID_ARG, "state buffer holds %lld bytes, %lld needed",
+                                   (long long)*bytes, (long long)need);
+    if (!c->have_x) return fail(c, MDS_ERR_STATE, "no locations set");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.n = c->n;
+    h.d = c->d;
+    h.fp64 = c->fp64 ? 1 : 0;
+    h.sigma = c->sigma;
+    h.lambda = c->lambda;
+    h.tail_z = c->tail_z;
+    CU(cudaMemcpyAsync(h.counters, c->counters, sizeof(h.counters), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    h.sigma_iter = c->sigma_iter;
+    h.rw_iter = c->rw_iter;
+    h.reordered = c->reordered ? 1 : 0;
+    h.have_sigma = c->have_sigma ? 1 : 0;
+    unsigned char *out = static_cast<unsigned char *>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    double *xd = reinterpret_cast<double *>(out + sizeof(h));
+    const int64_t nd = c->n * c->d;
+    CHECK(copy_out(c, c->x, c->fp64 ? 1 : 0, xd, MDS_F64, MDS_HOST, nd));
+    CHECK(copy_out(c, c->p, c->fp64 ? 1 : 0, xd + nd, MDS_F64, MDS_HOST, nd));
+    if (c->reordered) std::memcpy(xd + 2 * nd, c->perm_h.data(), c->n * 4);
+    *bytes = need;
+    return MDS_OK;
+}
+
+int mds_set_state(mds_ctx *c, const void *buf, int64_t bytes) {
+    CHECK(check_ctx(c));
+    if (!buf || bytes < static_cast<int64_t>(sizeof(StateHeader)))
+        return fail(c, MDS_ERR_INVALID_ARG, "not a state snapshot (too short)");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic) return fail(c, MDS_ERR_INVALID_ARG, "not a state snapshot (bad magic)");
+    if (h.n != c->n || h.d != c->d || (h.fp64 != 0) != c->fp64)
+        return fail(c, MDS_ERR_INVALID_ARG, "snapshot of N = %lld, D = %d (%s) does not fit this context",
+                    (long long)h.n, h.d, h.fp64 ? "FP64" : "FP32C");
+    const int64_t nd = c->n * c->d;
+    const int64_t need = static_cast<int64_t>(sizeof(StateHeader)) + 2 * nd * 8 + (h.reordered ? c->n * 4 : 0);
+    if (bytes < need) return fail(c, MDS_ERR_INVALID_ARG, "snapshot truncated (%lld of %lld bytes)",
+                                  (long long)bytes, (long long)need);
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    if (c->ho_count > 0 && h.reordered)
+        return fail(c, MDS_ERR_STATE, "a cross-validation fold is set: restore the state before mds_set_heldout");
+    const unsigned char *in = static_cast<const unsigned char *>(buf);
+    const double *xd = reinterpret_cast<const double *>(in + sizeof(h));
+    if (h.have_sigma) CHECK(mds_set_sigma(c, h.sigma));
+    CHECK(mds_set_prior(c, h.lambda));
+    CHECK(mds_set_tail_cutoff(c, h.tail_z));
+    CHECK(mds_set_locations(c, xd, MDS_F64, MDS_HOST));
+    CHECK(mds_set_momentum(c, xd + nd, MDS_F64, MDS_HOST));
+    if (h.reordered && c->have_data) {
+        std::vector<int32_t> order(static_cast<size_t>(c->n_pad));
+        std::memcpy(order.data(), xd + 2 * nd, c->n * 4);
+        for (int64_t s = c->n; s < c->n_pad; ++s) order[s] = static_cast<int32_t>(s);
+        if (!c->reordered || order != c->perm_h) {
+            CHECK(repack_to(c, order, false));
+            if (!c->fp64) {
+                cudaError_t e = launch_resplit(xstate(c), c->n_pad, c->d, c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_state: %s", cudaGetErrorString(e));
+            }
+        }
+    }
+    int64_t cnt[kCounters];
+    std::memcpy(cnt, h.counters, sizeof(cnt));
+    cnt[kIterLocal] = 0;
+    CU(cudaMemcpyAsync(c->counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->sigma_iter = h.sigma_iter;
+    c->rw_iter = h.rw_iter;
+    c->grad_valid = false;
+    c->gen++;
     return MDS_OK;
 }
 

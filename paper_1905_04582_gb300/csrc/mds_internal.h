@@ -182,6 +182,10 @@ cudaError_t launch_pair_batch(const BatchPairArgs &a, int d, int grid, cudaStrea
 size_t pair_batch_smem(int d, int strip_cap);
 int pair_batch_blocks_per_sm(int d, int strip_cap);
 
+// Fault injection for tests: a kernel whose bounded wait on an mbarrier that
+// nothing completes runs out and sets kErrTimeout (pair_kernel.cu).
+cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s);
+
 // Kernel launchers (pair_kernel.cu).
 cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s);
 cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s);

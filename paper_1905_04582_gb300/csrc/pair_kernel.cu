@@ -381,7 +381,24 @@ cudaError_t launch_f64_d(const PairArgs &a, cudaStream_t s) {
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// A bounded wait on an mbarrier that nothing completes (fault injection for
+// tests of the timeout path): it gives up after the wait limit and sets the
+// timeout bit of the error word, as a stalled copy in the pair pass would.
+__global__ void wait_probe_kernel(unsigned *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_wait_bounded(&bar, 0, err);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s) {
     switch (d) {

@@ -139,6 +139,21 @@ class MDS:
         self._check(self._lib.mds_get_order(self._h, perm.ctypes.data_as(ctypes.c_void_p)))
         return perm
 
+    # -- checkpoint / resume
+    def get_state(self):
+        """A snapshot of the chain (bytes): locations, momenta, sigma, lambda,
+        RNG counters, order (mds_get_state)."""
+        n = ctypes.c_int64()
+        self._check(self._lib.mds_get_state(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._lib.mds_get_state(self._h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def set_state(self, state):
+        """Restore a snapshot of get_state (mds_set_state)."""
+        b = bytes(state)
+        self._check(self._lib.mds_set_state(self._h, ctypes.c_char_p(b), len(b)))
+
     # -- single-item random-walk Metropolis (section 2.3's prior art)
     def rwmh(self, n_prop, step, seed=0, items=None, z_all=None, u_all=None):
         """n_prop single-item random-walk proposals (injected draws or
