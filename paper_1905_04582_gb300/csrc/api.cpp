@@ -491,7 +491,11 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_na
         if (e == cudaSuccess) e = cudaEventRecord(c->tree_join, c->tree_stream);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior launch: %s", cudaGetErrorString(e));
     }
-    e = c->fp64 ? launch_pair_pass_f64(a, c->d, s) : launch_pair_pass_f32(a, c->d, s);
+    // with a tree prior the pass is launched without PDL: it then becomes
+    // eligible when the traversal does, and the traversal's high-priority
+    // CTAs (too large for a slot a drained pass CTA frees) take SMs first
+    const bool pdl = !c->tree_on;
+    e = c->fp64 ? launch_pair_pass_f64(a, c->d, s, pdl) : launch_pair_pass_f32(a, c->d, s, pdl);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
     if (c->tree_on) {
         e = cudaStreamWaitEvent(s, c->tree_join, 0);

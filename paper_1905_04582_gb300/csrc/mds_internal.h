@@ -187,8 +187,11 @@ int pair_batch_blocks_per_sm(int d, int strip_cap);
 cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s);
 
 // Kernel launchers (pair_kernel.cu).
-cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s);
-cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s);
+// pdl: launch with programmatic dependent launch (the kernel may become
+// resident while the previous one drains); off when a concurrent kernel on
+// another stream should get SMs first.
+cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true);
+cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s, bool pdl = true);
 
 // ---------------------------------------------------------------------------
 // Reduction, leapfrog updates and HMC bookkeeping (reduce_kernel.cu).
@@ -512,8 +515,8 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 #endif
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args... args) {
+inline cudaError_t launch_maybe_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t s, Args... args) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -523,8 +526,14 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    return launch_maybe_pdl(true, kernel, grid, block, smem, s, args...);
 }
 
 }  // namespace mds

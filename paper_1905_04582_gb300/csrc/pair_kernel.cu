@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
 }
 
 template <int D>
-cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s) {
+cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s, bool pdl) {
     using L = F32Layout<D>;
     static bool attr_set = false;  // per instantiation pair, set once per process
     if (!attr_set) {
@@ -369,15 +369,15 @@ cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s) {
     }
     if (a.n_strips <= 0) return cudaSuccess;
     const cudaError_t e =
-        a.tile_ho ? launch_pdl(pair_f32_kernel<D, true>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a)
-                  : launch_pdl(pair_f32_kernel<D, false>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a);
+        a.tile_ho ? launch_maybe_pdl(pdl, pair_f32_kernel<D, true>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a)
+                  : launch_maybe_pdl(pdl, pair_f32_kernel<D, false>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_f64_d(const PairArgs &a, cudaStream_t s) {
+cudaError_t launch_f64_d(const PairArgs &a, cudaStream_t s, bool pdl) {
     if (a.n_strips <= 0) return cudaSuccess;
-    const cudaError_t e = launch_pdl(pair_f64_kernel<D>, dim3(a.n_strips), dim3(kPairThreads), 0, s, a);
+    const cudaError_t e = launch_maybe_pdl(pdl, pair_f64_kernel<D>, dim3(a.n_strips), dim3(kPairThreads), 0, s, a);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -400,30 +400,30 @@ cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s) {
+cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl) {
     switch (d) {
-        case 1: return launch_f32_d<1>(a, s);
-        case 2: return launch_f32_d<2>(a, s);
-        case 3: return launch_f32_d<3>(a, s);
-        case 4: return launch_f32_d<4>(a, s);
-        case 5: return launch_f32_d<5>(a, s);
-        case 6: return launch_f32_d<6>(a, s);
-        case 7: return launch_f32_d<7>(a, s);
-        case 8: return launch_f32_d<8>(a, s);
+        case 1: return launch_f32_d<1>(a, s, pdl);
+        case 2: return launch_f32_d<2>(a, s, pdl);
+        case 3: return launch_f32_d<3>(a, s, pdl);
+        case 4: return launch_f32_d<4>(a, s, pdl);
+        case 5: return launch_f32_d<5>(a, s, pdl);
+        case 6: return launch_f32_d<6>(a, s, pdl);
+        case 7: return launch_f32_d<7>(a, s, pdl);
+        case 8: return launch_f32_d<8>(a, s, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s) {
+cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s, bool pdl) {
     switch (d) {
-        case 1: return launch_f64_d<1>(a, s);
-        case 2: return launch_f64_d<2>(a, s);
-        case 3: return launch_f64_d<3>(a, s);
-        case 4: return launch_f64_d<4>(a, s);
-        case 5: return launch_f64_d<5>(a, s);
-        case 6: return launch_f64_d<6>(a, s);
-        case 7: return launch_f64_d<7>(a, s);
-        case 8: return launch_f64_d<8>(a, s);
+        case 1: return launch_f64_d<1>(a, s, pdl);
+        case 2: return launch_f64_d<2>(a, s, pdl);
+        case 3: return launch_f64_d<3>(a, s, pdl);
+        case 4: return launch_f64_d<4>(a, s, pdl);
+        case 5: return launch_f64_d<5>(a, s, pdl);
+        case 6: return launch_f64_d<6>(a, s, pdl);
+        case 7: return launch_f64_d<7>(a, s, pdl);
+        case 8: return launch_f64_d<8>(a, s, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
