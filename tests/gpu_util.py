@@ -8,7 +8,11 @@ A relative error is ill-conditioned where a coordinate's terms cancel, so a
 gradient coordinate also passes when
   (a) its condition number kappa = S / |g_ref| exceeds 1e3 (S = sum of the
       absolute values of its terms, from the oracle) and its absolute error
-      is below tol * 1e-3 * S; or
+      is below max(tol * 1e-3, u) * S: terms summed in a precision of unit
+      roundoff u can be off by u * S in the worst case (each term rounded
+      once or twice on its way into a short partial sum), whatever the
+      grouping of the sum (the strip length, chosen by timing, sets it);
+      or
   (b) its absolute error is below 8 u * S2, S2 = sqrt(sum of its squared
       terms) and u the unit roundoff of the path (2^-24 for FP32C, 2^-53 for
       FP64): the size of the rounding error that any evaluation of the
@@ -33,7 +37,7 @@ def grad_check(g, g_ref, s_abs, tol, what="gradient", s_sq=None, u=None):
     err = np.abs(g - g_ref)
     rel_ok = err <= tol * np.abs(g_ref)
     kappa = s_abs / np.maximum(np.abs(g_ref), 1e-300)
-    cond_ok = (kappa > KAPPA) & (err <= tol * 1e-3 * s_abs)
+    cond_ok = (kappa > KAPPA) & (err <= max(tol * 1e-3, u or 0.0) * s_abs)
     if s_sq is not None and u is not None:
         round_ok = err <= ULPS * u * np.asarray(s_sq, dtype=np.float64)
     else:
