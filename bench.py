@@ -611,6 +611,14 @@ def run_tree(args):
                     m.tree_prior(out=g)
                 torch.cuda.synchronize()
                 out["tree_prior_call_us"] = 1e6 * (time.perf_counter() - t0) / reps
+                # the traversal kernel alone: evaluations queued back to back
+                # (no outputs copied, no synchronisation), CUDA events
+                ev0.record(stream)
+                for _ in range(reps):
+                    m._check(m._lib.mds_tree_prior(m._h, None, None, 0, 0))
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                out["tree_prior_kernel_us"] = 1e3 * ev0.elapsed_time(ev1) / reps
     out["tree_prior_cost_per_step_us"] = 1e3 * (out["with_tree_prior"]["ms_per_iteration"] -
                                                out["likelihood_only"]["ms_per_iteration"]) / N_LEAPFROG
     print(json.dumps(out), flush=True)

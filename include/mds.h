@@ -325,11 +325,30 @@ int mds_set_tail_cutoff(mds_ctx *ctx, double z);
 int mds_set_tree_prior(mds_ctx *ctx, int64_t n_nodes, const int64_t *parent, const double *length,
                        const double *sigma_mat, const double *mu, double tau0, double tau_u);
 
+/* Host-only (no GPU needed): checks the work split that mds_set_tree_prior
+ * would use for this forest (parent / length as there, over n tips, for D
+ * coordinates).  Each tree is cut into blocks (the largest subtrees of at
+ * most S = ceil(m / 4C) internal nodes, m the tree's internal nodes, C the
+ * CTAs of its cluster) and a top (the nodes above them); the device
+ * evaluates a tree with one cluster: each CTA its blocks upward, CTA 0 the
+ * top up and down, each CTA its blocks downward.  The check verifies that
+ * every node and tip of every tree lies in exactly one part, that child
+ * references, levels, block-root exchanges and buffer offsets are
+ * consistent.  stats (optional, 8 entries): cluster size C, parts, the
+ * longest chain of levels (2 x (block + top levels)), the largest part's
+ * shared-memory bytes, block roots in all, the largest top, the largest
+ * part's block nodes, trees.  Errors: INVALID_ARG (not a binary forest, as
+ * mds_set_tree_prior), STATE (the split is inconsistent: a library defect);
+ * the message from mds_last_error(NULL). */
+int mds_tree_plan_check(int64_t n, int64_t n_nodes, const int64_t *parent, const double *length, int32_t d,
+                        int64_t *stats);
+
 /* log p(X) of the prior at the current locations (optional) and its
  * gradient d log p / dX = -V^-1 (X - 1 mu^T) Sigma^-1 into `grad` (N x D,
  * optional, dtype and where as in mds_gradient), by two level-synchronous
- * traversals of each tree on the device (O(N D^2), FP64; section 2.3 cites
- * the linear-time post-order evaluation).  Synchronises when an output is
+ * traversals of each tree on the device, one cluster of CTAs per tree (the
+ * split of mds_tree_plan_check; O(N D^2), FP64; section 2.3 cites the
+ * linear-time post-order evaluation).  Synchronises when an output is
  * on the host.  Errors: STATE (no prior or no locations). */
 int mds_tree_prior(mds_ctx *ctx, double *logp, void *grad, int dtype, int where);
 

@@ -82,6 +82,7 @@ SIGNATURES = {
     "mds_hmc_collect": (_int, [_vp, _i64, _vp, _vp, _pi64, ctypes.POINTER(mds_hmc_stats)]),
     "mds_problem_size": (_int, [_vp, _pi64, _pi64]),
     "mds_locality_order": (_int, [_i64, _i32, _vp, _vp]),
+    "mds_tree_plan_check": (_int, [_i64, _i64, _vp, _vp, _i32, _vp]),
     "mds_reorder": (_int, [_vp]),
     "mds_get_order": (_int, [_vp, _vp]),
     "mds_set_tail_cutoff": (_int, [_vp, _dbl]),

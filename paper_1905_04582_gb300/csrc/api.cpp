@@ -19,6 +19,7 @@
 
 #include "mds_internal.h"
 #include "mills_ratio_coeffs.h"
+#include "tree_plan.h"
 
 using namespace mds;
 
@@ -135,7 +136,7 @@ struct mds_ctx {
     TreeArgs tree{};                      // device pointers and constants (x set per launch)
     double *tree_grad0 = nullptr;         // its gradient at the trajectory start (restored on reject)
     cudaStream_t tree_stream = nullptr;   // the traversal runs here, beside the pair pass
-    cudaEvent_t tree_fork = nullptr, tree_join = nullptr;
+    cudaEvent_t tree_fork = nullptr, tree_join = nullptr, tree_started = nullptr;
     int64_t rw_iter = 0;                  // random-walk proposals drawn so far (Philox counter)
     std::vector<void *> tree_bufs;        // its device allocations
 
@@ -427,6 +428,8 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.mode = mode;
     r.fp64 = c->fp64;
     r.sigma = c->sigma;
+    r.log_sigma = std::log(c->sigma);
+    r.inv_sigma = 1.0 / c->sigma;
     r.m_pairs = 0.5 * static_cast<double>(c->n) * static_cast<double>(c->n - 1) - static_cast<double>(c->ho_count);
     r.lambda = c->lambda;
     r.eps = eps;
@@ -487,13 +490,16 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_na
         ta.out = c->scal + kPriorLogp;
         e = cudaEventRecord(c->tree_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->tree_stream, c->tree_fork, 0);
-        if (e == cudaSuccess) e = launch_tree_prior(ta, c->d, c->tree_stream);
+        if (e == cudaSuccess) e = launch_tree_prior(ta, c->d, c->tree_stream, c->tree_started);
         if (e == cudaSuccess) e = cudaEventRecord(c->tree_join, c->tree_stream);
+        // the pass starts once every traversal CTA has begun: the traversal's
+        // clusters (8 CTAs on 8 SMs of one GPC at once) are placed before the
+        // pass's CTAs fill the SMs
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->tree_started, 0);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior launch: %s", cudaGetErrorString(e));
     }
-    // with a tree prior the pass is launched without PDL: it then becomes
-    // eligible when the traversal does, and the traversal's high-priority
-    // CTAs (too large for a slot a drained pass CTA frees) take SMs first
+    // with a tree prior the pass is launched without PDL (it waits for the
+    // traversal's start, not for the reduction's tail)
     const bool pdl = !c->tree_on;
     e = c->fp64 ? launch_pair_pass_f64(a, c->d, s, pdl) : launch_pair_pass_f32(a, c->d, s, pdl);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
@@ -1123,6 +1129,7 @@ int mds_destroy(mds_ctx *c) {
     }
     if (c->tree_fork) cudaEventDestroy(c->tree_fork);
     if (c->tree_join) cudaEventDestroy(c->tree_join);
+    if (c->tree_started) cudaEventDestroy(c->tree_started);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (cudaEvent_t e : c->prof_a) cudaEventDestroy(e);
@@ -1615,6 +1622,55 @@ int mds_locality_order(int64_t n, int32_t d, const double *x, int32_t *perm) {
     return MDS_OK;
 }
 
+int mds_tree_plan_check(int64_t n, int64_t n_nodes, const int64_t *parent, const double *length, int32_t d,
+                        int64_t *stats) {
+    if (n < 1 || n > INT32_MAX || d < 1 || d > MDS_MAX_D || !parent || !length) {
+        mds::set_thread_error("mds_tree_plan_check: need 1 <= n < 2^31, 1 <= d <= %d, parent and length", MDS_MAX_D);
+        return MDS_ERR_INVALID_ARG;
+    }
+    ForestShape f;
+    std::string err = parse_forest(n, n_nodes, parent, length, f);
+    if (!err.empty()) {
+        mds::set_thread_error("mds_tree_plan_check: %s", err.c_str());
+        return MDS_ERR_INVALID_ARG;
+    }
+    std::vector<TreeWeights> wt;
+    std::vector<double> root_cinv;
+    double cst = 0.0;
+    tree_weights(f, length, 1.0, 1.0, d, wt, root_cinv, cst);
+    TreePlan plan;
+    plan_forest(f, wt, d, plan);
+    err = check_plan(f, plan, d);
+    if (!err.empty()) {
+        mds::set_thread_error("mds_tree_plan_check: plan violates %s", err.c_str());
+        return MDS_ERR_STATE;
+    }
+    if (stats) {
+        int64_t chain = 0, top = 0, blk = 0, slots = 0;
+        for (size_t t = 0; t < f.roots.size(); ++t) {
+            int64_t lb = 0;
+            for (int cr = 0; cr < plan.cluster; ++cr) {
+                const TreePart &pt = plan.parts[t * plan.cluster + cr];
+                lb = std::max<int64_t>(lb, pt.nlv_blk);
+                blk = std::max<int64_t>(blk, pt.m_blk);
+            }
+            const TreePart &p0 = plan.parts[t * plan.cluster];
+            chain = std::max<int64_t>(chain, 2 * (lb + p0.nlv_top));
+            top = std::max<int64_t>(top, p0.m_top);
+            slots += p0.n_slots;
+        }
+        stats[0] = plan.cluster;
+        stats[1] = static_cast<int64_t>(plan.parts.size());
+        stats[2] = chain;
+        stats[3] = plan.max_fp;
+        stats[4] = slots;
+        stats[5] = top;
+        stats[6] = blk;
+        stats[7] = static_cast<int64_t>(f.roots.size());
+    }
+    return MDS_OK;
+}
+
 namespace {
 int reorder_ctx(mds_ctx *c, bool order_strips);
 }
@@ -1730,57 +1786,11 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
     if (!(tau0 > 0.0) || !std::isfinite(tau0) || !(tau_u > 0.0) || !std::isfinite(tau_u))
         return fail(c, MDS_ERR_INVALID_ARG, "tau0 and tau_u must be finite and > 0");
     // ---- the forest
-    std::vector<int32_t> c0(n_nodes, -1), c1(n_nodes, -1);
-    for (int64_t k = 0; k < n_nodes; ++k) {
-        const int64_t p = parent[k];
-        if (p == -1) continue;
-        if (p < n || p >= n_nodes)
-            return fail(c, MDS_ERR_INVALID_ARG, "node %lld: parent %lld is not an internal node", (long long)k,
-                        (long long)p);
-        if (!(length[k] > 0.0) || !std::isfinite(length[k]))
-            return fail(c, MDS_ERR_INVALID_ARG, "node %lld: branch length must be finite and > 0", (long long)k);
-        if (c0[p] < 0) c0[p] = static_cast<int32_t>(k);
-        else if (c1[p] < 0) c1[p] = static_cast<int32_t>(k);
-        else return fail(c, MDS_ERR_INVALID_ARG, "node %lld has more than two children", (long long)p);
+    ForestShape f;
+    {
+        const std::string err = parse_forest(n, n_nodes, parent, length, f);
+        if (!err.empty()) return fail(c, MDS_ERR_INVALID_ARG, "%s", err.c_str());
     }
-    for (int64_t k = n; k < n_nodes; ++k)
-        if (c1[k] < 0) return fail(c, MDS_ERR_INVALID_ARG, "internal node %lld needs two children", (long long)k);
-    // heights in post-order from every root (an iterative DFS); a node seen
-    // twice or never means a cycle
-    std::vector<int32_t> height(n_nodes, -1), roots, lone;
-    std::vector<int32_t> order;  // internal nodes, children before parents
-    for (int64_t r = 0; r < n_nodes; ++r) {
-        if (parent[r] != -1) continue;
-        if (r < n) {
-            lone.push_back(static_cast<int32_t>(r));
-            height[r] = 0;
-            continue;
-        }
-        roots.push_back(static_cast<int32_t>(r));
-        std::vector<std::pair<int32_t, int>> st{{static_cast<int32_t>(r), 0}};
-        while (!st.empty()) {
-            auto &top = st.back();
-            const int32_t u = top.first;
-            if (u < n) {
-                height[u] = 0;
-                st.pop_back();
-                continue;
-            }
-            if (top.second < 2) {
-                const int32_t ch = top.second == 0 ? c0[u] : c1[u];
-                top.second++;
-                if (height[ch] != -1 || static_cast<int64_t>(st.size()) > n_nodes)
-                    return fail(c, MDS_ERR_INVALID_ARG, "the parent links do not form a forest");
-                st.push_back({ch, 0});
-                continue;
-            }
-            height[u] = 1 + std::max(height[c0[u]], height[c1[u]]);
-            order.push_back(u);
-            st.pop_back();
-        }
-    }
-    for (int64_t k = 0; k < n_nodes; ++k)
-        if (height[k] < 0) return fail(c, MDS_ERR_INVALID_ARG, "node %lld is not connected to a root", (long long)k);
     // ---- Sigma: symmetric positive definite; its inverse and log-determinant
     std::vector<double> L(d * d, 0.0), sinv(d * d, 0.0);
     for (int i = 0; i < d; ++i)
@@ -1818,128 +1828,16 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
     }
     for (int k = 0; k < d; ++k)
         if (!std::isfinite(mu[k])) return fail(c, MDS_ERR_INVALID_ARG, "mu must be finite");
-    // ---- message variances (they depend on the tree alone) and the weights
-    const double log2pi = 1.8378770664093454836;
-    const double hd = 0.5 * d;
-    std::vector<double> up_v(n_nodes, 0.0), dn_v(n_nodes, 0.0);
-    // per node: weights (up: children before parents; down: parents first)
-    struct W {
-        double alpha = 0, cinv = 0, beta0 = 0, beta1 = 0, g0 = 0, g1 = 0;
-    };
-    std::vector<W> wt(n_nodes);
-    double cst = -0.5 * static_cast<double>(n) * logdet;
-    for (int32_t k : order) {
-        const double va = up_v[c0[k]] + length[c0[k]], vb = up_v[c1[k]] + length[c1[k]], sv = va + vb;
-        wt[k].alpha = vb / sv;
-        wt[k].cinv = 1.0 / sv;
-        up_v[k] = va * vb / sv;
-        cst -= hd * (log2pi + std::log(sv));
-    }
+    // ---- message variances and weights; the cut into per-CTA parts
+    std::vector<TreeWeights> wt;
     std::vector<double> root_cinv;
-    for (int32_t r : roots) {
-        const double sv = up_v[r] + tau0;
-        root_cinv.push_back(1.0 / sv);
-        cst -= hd * (log2pi + std::log(sv));
-        dn_v[r] = tau0;
-    }
-    cst -= hd * (log2pi + std::log(tau_u)) * static_cast<double>(lone.size());
-    for (auto it = order.rbegin(); it != order.rend(); ++it) {  // parents before children
-        const int32_t k = *it;
-        const double vk = dn_v[k];
-        for (int side = 0; side < 2; ++side) {
-            const int32_t ch = side == 0 ? c0[k] : c1[k], sib = side == 0 ? c1[k] : c0[k];
-            const double vs = up_v[sib] + length[sib];
-            const double beta = vs / (vk + vs);
-            const double vc = vk * vs / (vk + vs) + length[ch];
-            const double g = ch < n ? 1.0 / vc : 0.0;
-            if (side == 0) {
-                wt[k].beta0 = beta;
-                wt[k].g0 = g;
-            } else {
-                wt[k].beta1 = beta;
-                wt[k].g1 = g;
-            }
-            if (ch >= n) dn_v[ch] = vc;
-        }
-    }
-    // ---- level schedule: tree by tree (roots in id order), internal nodes by
-    // (height, id), the root last; children referenced by their index within
-    // the tree (internal) or in the tree's tip list (tips)
-    std::vector<int32_t> tree_of(n_nodes, -1);
-    for (size_t t = 0; t < roots.size(); ++t) tree_of[roots[t]] = static_cast<int32_t>(t);
-    std::vector<std::vector<int32_t>> members(roots.size());
-    for (auto it = order.rbegin(); it != order.rend(); ++it) {  // parents first: a child inherits its tree
-        const int32_t k = *it;
-        if (tree_of[k] < 0) tree_of[k] = tree_of[parent[k]];
-        members[tree_of[k]].push_back(k);
-    }
-    std::vector<TreeNode> nodes;
-    std::vector<int32_t> node_off{0}, tip_items, tip_off{0}, lv_start, tree_lv;
-    std::vector<int32_t> local(n_nodes, -1);
-    int64_t max_fp = 0, scr_total = 0;
-    std::vector<int64_t> scr_off;
-    for (size_t t = 0; t < roots.size(); ++t) {
-        auto &mem = members[t];
-        std::sort(mem.begin(), mem.end(), [&](int32_t a, int32_t b) {
-            return height[a] < height[b] || (height[a] == height[b] && a < b);
-        });
-        for (size_t q = 0; q < mem.size(); ++q) local[mem[q]] = static_cast<int32_t>(q);
-        tree_lv.push_back(static_cast<int32_t>(lv_start.size()));
-        const int32_t tip0 = static_cast<int32_t>(tip_items.size());
-        int prev = -1;
-        for (size_t q = 0; q < mem.size(); ++q) {
-            const int32_t k = mem[q];
-            if (height[k] != prev) {
-                lv_start.push_back(static_cast<int32_t>(q));
-                prev = height[k];
-            }
-            TreeNode r{};
-            int32_t ref[2];
-            for (int side = 0; side < 2; ++side) {
-                const int32_t ch = side == 0 ? c0[k] : c1[k];
-                if (ch >= n) {
-                    ref[side] = local[ch];
-                } else {
-                    ref[side] = -(static_cast<int32_t>(tip_items.size()) - tip0 + 1);
-                    tip_items.push_back(ch);
-                }
-            }
-            r.c0 = ref[0];
-            r.c1 = ref[1];
-            r.alpha = wt[k].alpha;
-            r.cinv = wt[k].cinv;
-            r.beta0 = wt[k].beta0;
-            r.beta1 = wt[k].beta1;
-            r.g0 = wt[k].g0;
-            r.g1 = wt[k].g1;
-            nodes.push_back(r);
-        }
-        node_off.push_back(static_cast<int32_t>(nodes.size()));
-        tip_off.push_back(static_cast<int32_t>(tip_items.size()));
-        const int64_t m = static_cast<int64_t>(mem.size()), kt = static_cast<int64_t>(tip_items.size()) - tip0;
-        const int64_t n_lv = static_cast<int64_t>(lv_start.size()) - tree_lv.back();
-        // records, up / down means of internal nodes, tip locations, tip
-        // downward means and gradient scales, level bounds
-        const int64_t fp = m * static_cast<int64_t>(sizeof(TreeNode)) + ((2 * m + 2 * kt) * d + kt) * 8 + 4 * n_lv;
-        max_fp = std::max(max_fp, fp);
-        scr_off.push_back(scr_total);
-        scr_total += (2 * m + 2 * kt) * d + kt;
-    }
-    tree_lv.push_back(static_cast<int32_t>(lv_start.size()));
-    // per tree, the top run of levels with at most 32 nodes (one warp's work)
-    std::vector<int32_t> tree_small(roots.size());
-    for (size_t t = 0; t < roots.size(); ++t) {
-        const int32_t l0 = tree_lv[t], l1 = tree_lv[t + 1];
-        const int32_t m_t = node_off[t + 1] - node_off[t];
-        int32_t small = l1 - l0;
-        while (small > 0) {
-            const int32_t a0 = lv_start[l0 + small - 1];
-            const int32_t a1 = small < l1 - l0 ? lv_start[l0 + small] : m_t;
-            if (a1 - a0 > 32) break;
-            --small;
-        }
-        tree_small[t] = small;
-    }
+    double cst = 0.0;
+    tree_weights(f, length, tau0, tau_u, d, wt, root_cinv, cst);
+    cst -= 0.5 * static_cast<double>(n) * logdet;
+    TreePlan plan;
+    plan_forest(f, wt, d, plan);
+    const std::vector<int32_t> &roots = f.roots, &lone = f.lone;
+    const int ncl = plan.cluster;
     // ---- device copies
     drop();
     if (!c->tree_stream) {
@@ -1948,6 +1846,7 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
         CU(cudaStreamCreateWithPriority(&c->tree_stream, cudaStreamNonBlocking, hi));
         CU(cudaEventCreateWithFlags(&c->tree_fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&c->tree_join, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&c->tree_started, cudaEventDisableTiming));
     }
     TreeArgs ta{};
     auto up = [&](void **dst, const void *src, size_t bytes) -> int {
@@ -1963,14 +1862,18 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
         return MDS_OK;
     };
     void *p = nullptr;
-    CHECK(up(&p, nodes.data(), nodes.size() * sizeof(TreeNode)));
+    CHECK(up(&p, plan.nodes.data(), plan.nodes.size() * sizeof(TreeNode)));
     ta.nodes = static_cast<const TreeNode *>(p);
-    CHECK(up(&p, lv_start.data(), lv_start.size() * sizeof(int32_t)));
+    CHECK(up(&p, plan.lv_start.data(), plan.lv_start.size() * sizeof(int32_t)));
     ta.lv_start = static_cast<const int32_t *>(p);
-    CHECK(up(&p, tree_lv.data(), tree_lv.size() * sizeof(int32_t)));
-    ta.tree_lv = static_cast<const int32_t *>(p);
-    CHECK(up(&p, tree_small.data(), tree_small.size() * sizeof(int32_t)));
-    ta.tree_small = static_cast<const int32_t *>(p);
+    CHECK(up(&p, plan.parts.data(), plan.parts.size() * sizeof(TreePart)));
+    ta.parts = static_cast<const TreePart *>(p);
+    CHECK(up(&p, plan.exp_loc.data(), plan.exp_loc.size() * sizeof(int32_t)));
+    ta.exp_loc = static_cast<const int32_t *>(p);
+    CHECK(up(&p, plan.exp_slot.data(), plan.exp_slot.size() * sizeof(int32_t)));
+    ta.exp_slot = static_cast<const int32_t *>(p);
+    CHECK(up(&p, nullptr, static_cast<size_t>(std::max<int64_t>(plan.xch_total, 1)) * sizeof(double)));
+    ta.xch = static_cast<double *>(p);
     CHECK(up(&p, root_cinv.data(), root_cinv.size() * sizeof(double)));
     ta.root_cinv = static_cast<const double *>(p);
     CHECK(up(&p, lone.data(), lone.size() * sizeof(int32_t)));
@@ -1979,35 +1882,37 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
     ta.sigma_inv = static_cast<const double *>(p);
     CHECK(up(&p, mu, d * sizeof(double)));
     ta.mu = static_cast<const double *>(p);
-    CHECK(up(&p, node_off.data(), node_off.size() * sizeof(int32_t)));
+    CHECK(up(&p, plan.node_off.data(), plan.node_off.size() * sizeof(int32_t)));
     ta.node_off = static_cast<const int32_t *>(p);
-    CHECK(up(&p, tip_items.data(), tip_items.size() * sizeof(int32_t)));
+    CHECK(up(&p, plan.tip_items.data(), plan.tip_items.size() * sizeof(int32_t)));
     ta.tip_items = static_cast<const int32_t *>(p);
-    CHECK(up(&p, tip_off.data(), tip_off.size() * sizeof(int32_t)));
+    CHECK(up(&p, plan.tip_off.data(), plan.tip_off.size() * sizeof(int32_t)));
     ta.tip_off = static_cast<const int32_t *>(p);
-    // messages and tip locations: in shared memory when the largest tree fits
+    // messages and tip locations: in shared memory when the largest part fits
     // (kTreeSmemMax bytes per CTA), else in global scratch
     constexpr int64_t kTreeSmemMax = 200 * 1024;
-    if (max_fp > 0 && max_fp <= kTreeSmemMax) {
-        ta.smem_bytes = static_cast<int32_t>((max_fp + 15) / 16 * 16);
+    if (plan.max_fp > 0 && plan.max_fp <= kTreeSmemMax) {
+        ta.smem_bytes = static_cast<int32_t>((plan.max_fp + 15) / 16 * 16);
     } else {
         ta.smem_bytes = 0;
-        CHECK(up(&p, nullptr, static_cast<size_t>(std::max<int64_t>(scr_total, 1)) * sizeof(double)));
+        CHECK(up(&p, nullptr, static_cast<size_t>(std::max<int64_t>(plan.scr_total, 1)) * sizeof(double)));
         ta.scratch = static_cast<double *>(p);
-        CHECK(up(&p, scr_off.data(), scr_off.size() * sizeof(int64_t)));
-        ta.scr_off = static_cast<const int64_t *>(p);
     }
     CHECK(up(&p, nullptr, static_cast<size_t>(c->n_pad) * d * sizeof(double)));
     ta.grad = static_cast<double *>(p);
     CHECK(up(&p, nullptr, static_cast<size_t>(c->n_pad) * d * sizeof(double)));
     c->tree_grad0 = static_cast<double *>(p);
-    CHECK(up(&p, nullptr, (roots.size() + 2) * sizeof(double)));
+    const size_t grid = (roots.size() + (lone.empty() ? 0 : 1)) * static_cast<size_t>(ncl);
+    CHECK(up(&p, nullptr, (grid + 2) * sizeof(double)));
     ta.part = static_cast<double *>(p);
-    ta.out = ta.part + roots.size() + 1;
+    ta.out = ta.part + grid;
+    ta.done = reinterpret_cast<unsigned *>(ta.part + grid + 1);
+    CU(cudaMemsetAsync(ta.done, 0, sizeof(unsigned), c->stream));
     CU(cudaMemsetAsync(ta.grad, 0, static_cast<size_t>(c->n_pad) * d * sizeof(double), c->stream));
     CU(cudaStreamSynchronize(c->stream));
     ta.n = n;
     ta.n_trees = static_cast<int32_t>(roots.size());
+    ta.cluster = ncl;
     ta.n_lone = static_cast<int32_t>(lone.size());
     ta.tau_u = tau_u;
     ta.const_term = cst;

@@ -255,6 +255,7 @@ struct ReduceArgs {
     bool fp64;                // context precision (x, p, partial types)
     double m_pairs;           // pairs in the likelihood (M less the held-out ones)
     double sigma;
+    double log_sigma, inv_sigma;  // log(sigma), 1 / sigma (host)
     double lambda;            // prior precision
     double eps;               // leapfrog step
     double *grad;             // [N][D] dL/dx (FP64 copy for the API)
@@ -346,12 +347,32 @@ cudaError_t launch_traj_end_batch(const AcceptArgs *cfg, int n_chains, int64_t m
 // the tree alone and are computed on the host.
 // ---------------------------------------------------------------------------
 struct TreeNode {
-    int32_t c0, c1;          // children: >= 0 an internal node (its record index within the tree),
-                             // < 0 the tree's tip -(c + 1) (index into the tree's tip list)
+    int32_t c0, c1;          // children: >= 0 a node of the same part (its local index),
+                             // < 0 the part's tip -(c + 1) (index into the part's tip list)
     double alpha;            // upward mean: m_k = m_c1 + alpha (m_c0 - m_c1)
     double cinv;             // 1 / (variance of the contrast m_c0 - m_c1)
     double beta0, beta1;     // downward mean of child i: m_s + beta_i (m_k - m_s), s its sibling
     double g0, g1;           // 1 / (downward variance) of a tip child (gradient scale)
+};
+
+// A tree is cut into blocks (whole subtrees of at most S internal nodes)
+// and a top (the internal nodes whose subtrees are larger); one cluster of
+// `cluster` CTAs evaluates it, CTA c holding part c: the blocks assigned to
+// it and, for c = 0, the top.  Local node indices of a part: its blocks'
+// internal nodes [0, m_blk) by height; for part 0 then one proxy per block
+// root of the tree [m_blk, m_blk + n_prox) (in slot order: they hold the
+// block roots' messages, exchanged through `xch`), and the top nodes
+// [m_blk + n_prox, m) by height.
+struct TreePart {
+    int32_t m_blk, n_prox, m_top;
+    int32_t lv0;             // the part's first level bound in lv_start: block levels, then top levels
+    int32_t nlv_blk, small_blk;  // block levels; levels from small_blk on hold <= 32 nodes each
+    int32_t nlv_top, small_top;  // the same for the top levels (part 0)
+    int32_t exp0, exp1;      // the part's block roots: exp_loc / exp_slot [exp0, exp1)
+    int32_t root_loc;        // part 0: local index of the tree's root (a top node or a proxy); else -1
+    int32_t n_slots;         // block roots of the tree
+    int64_t xch_off;         // the tree's exchange arrays: up means at xch_off, down means after them
+    int64_t scr_off;         // messages in global scratch (smem_bytes == 0): this part's offset
 };
 
 struct TreeArgs {
@@ -359,14 +380,17 @@ struct TreeArgs {
     const void *x;           // locations [N][D] (float or double, item order)
     bool x_f64;
     int32_t n_trees;
-    const TreeNode *nodes;   // tree t's internal nodes at [node_off[t], node_off[t+1]), by level, root last
-    const int32_t *node_off; // [n_trees + 1]
-    const int32_t *tip_items;// tree t's tips (their items) at [tip_off[t], tip_off[t+1])
-    const int32_t *tip_off;  // [n_trees + 1]
-    const int32_t *lv_start; // each level's first record, relative to its tree (a tree's last level
-                             // ends at its node count)
-    const int32_t *tree_lv;  // first level of each tree (+ end)
-    const int32_t *tree_small; // per tree: first level (relative) of the top run of levels with <= 32 nodes
+    int32_t cluster;         // CTAs (one cluster) per tree; part p = tree p / cluster, rank p % cluster
+    const TreePart *parts;   // [n_trees * cluster]
+    const TreeNode *nodes;   // part p's local nodes at [node_off[p], node_off[p+1]) (proxies: unused)
+    const int32_t *node_off; // [n_parts + 1]
+    const int32_t *tip_items;// part p's tips (their items) at [tip_off[p], tip_off[p+1])
+    const int32_t *tip_off;  // [n_parts + 1]
+    const int32_t *lv_start; // first local index of each level (a level ends where the next starts,
+                             // the last block level at m_blk, the last top level at the part's end)
+    const int32_t *exp_loc;  // block roots: local index in their part
+    const int32_t *exp_slot; //   and slot in the tree's exchange arrays
+    double *xch;             // exchange arrays (scratch)
     const double *root_cinv; // per tree: 1 / (v_root + tau0)
     int32_t n_lone;
     const int32_t *lone;     // unsequenced items (tips that are roots)
@@ -374,14 +398,18 @@ struct TreeArgs {
     const double *sigma_inv; // D x D
     const double *mu;        // D
     double const_term;       // sum of the log-determinant and 2 pi terms
-    int32_t smem_bytes;      // > 0: a tree's CTA keeps its records, messages and tips in shared memory
-    double *scratch;         // otherwise: per tree (2 m_t + 2 k_t) x D + k_t doubles at scr_off[t]
-    const int64_t *scr_off;
+    int32_t smem_bytes;      // > 0: each CTA keeps its part's records, messages and tips in shared memory
+    double *scratch;         // otherwise: per part (2 m + 2 k) x D + k doubles at scr_off
     double *grad;            // [N][D] d log p / dX (out)
-    double *part;            // [n_trees + 1] per-CTA sums (scratch)
+    double *part;            // [grid] per-CTA sums (scratch)
+    unsigned *done;          // CTAs finished (0 between launches; the last one resets it)
     double *out;             // log p (out, device scalar)
 };
-cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s);
+constexpr int kTreeMaxCluster = 8;  // CTAs per tree (portable cluster size)
+// started (optional): an event that fires once every CTA of the launch has
+// begun (a launch-completion event), for work that should start only after
+// the traversal holds its SMs.
+cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s, cudaEvent_t started = nullptr);
 
 // ---------------------------------------------------------------------------
 // Single-item random-walk Metropolis (rwmh.cu): one CTA runs the proposals

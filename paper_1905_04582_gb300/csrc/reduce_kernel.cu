@@ -173,10 +173,13 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     // the item at this thread's slot (the order is constant between passes,
     // so it is read before the wait)
     int64_t item_of_slot = -1;
+    int s0 = 0, s1 = 0;  // the column block's row-partial slots (fixed between passes too)
     if (Jq >= 0) {
         const int64_t ks = static_cast<int64_t>(Jq / kRedQuarters) * kTile + (Jq % kRedQuarters) * kRedRows +
                            (tid % kRedRows);
         item_of_slot = (a.perm && ks < a.n) ? a.perm[ks] : ks;
+        s0 = a.row_first_slot[Jq / kRedQuarters];
+        s1 = a.row_first_slot[Jq / kRedQuarters + 1];
     }
     // every input (partials, x, p) comes from the pass just before
     pdl_trigger();
@@ -219,13 +222,15 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             dlp = block_sum_d<kRedThreads>(lp, sm);
         }
         if (tid == 0) {
-            const double sg = a.sigma;
+            // log sigma and 1 / sigma come from the host: FP64 log and
+            // division are long dependency chains on this GPU
+            const double isg = a.inv_sigma, isg2 = isg * isg;
             const double m = a.m_pairs;
             const double sum_logphi = kF32 ? -kLn2 * dlp : dlp;      // FP32C: sum log2(1/Phi)
             const double sum_mdelta = kF32 ? dmd / kSqrt2Pi : dmd;   // FP32C: sqrt(2 pi) (phi/Phi) delta
-            const double sum_r = de2 / (2.0 * sg * sg) + sum_logphi;
-            const double ll = -m * log(sg) - sum_r;
-            const double ds = -m / sg + de2 / (sg * sg * sg) + sum_mdelta / (sg * sg);
+            const double sum_r = 0.5 * de2 * isg2 + sum_logphi;
+            const double ll = -m * a.log_sigma - sum_r;
+            const double ds = -m * isg + de2 * isg2 * isg + sum_mdelta * isg2;
             a.scal[kLogLik] = ll;
             a.scal[kSumR] = sum_r;
             a.scal[kDSigma] = ds;
@@ -263,49 +268,53 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     Acc acc[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) acc[d] = Acc{};
-    // the loads of a round are issued together (independent of the running
-    // sums), so one round costs one L2 latency; at N = 5392 a round covers
-    // every partial of the block
+    // the state this CTA's writers update: read now, beside the partials
+    // (it does not depend on them), so that it costs no L2 latency of its own
+    const bool writer = s == 0 && k < a.n && mode != kModeEval;
+    T xv0[D], pv0[D];
+    double pg0[D];
+    if (writer) {
+        const T *xs = reinterpret_cast<const T *>(a.xs.x);
+        const T *ps = reinterpret_cast<const T *>(a.p);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            xv0[d] = xs[item_of_slot * D + d];
+            pv0[d] = ps[item_of_slot * D + d];
+            pg0[d] = a.prior_grad ? a.prior_grad[item_of_slot * D + d] : 0.0;
+        }
+    }
+    // column partials (I <= J) added, row partials (slots [s0, s1))
+    // subtracted; the loads of a round, of both kinds, are issued together
+    // (independent of the running sums), so one round costs one L2 latency;
+    // at N = 5392 one round covers every partial of the block
     constexpr int kU = D <= 2 ? 8 : D <= 4 ? 4 : 2;
     const T *cp = reinterpret_cast<const T *>(a.col_part);
-    for (int I0 = s; I0 <= J; I0 += kSplits * kU) {
-        T v[kU][D];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int I = I0 + u * kSplits;
-            const T *c = cp + (tile_index(I, J, nt) * kTile + r) * D;
-#pragma unroll
-            for (int d = 0; d < D; ++d) v[u][d] = I <= J ? c[d] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                if constexpr (kF32)
-                    df_add(acc[d], v[u][d]);
-                else
-                    acc[d] += v[u][d];
-            }
-    }
     const T *rpart = reinterpret_cast<const T *>(a.row_part);
-    const int s0 = a.row_first_slot[J], s1 = a.row_first_slot[J + 1];
-    for (int sl0 = s0 + s; sl0 < s1; sl0 += kSplits * kU) {
-        T v[kU][D];
+    for (int q = 0; s + q <= J || s0 + s + q < s1; q += kSplits * kU) {
+        T vc[kU][D], vr[kU][D];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int slot = sl0 + u * kSplits;
+            const int I = s + q + u * kSplits;
+            const int slot = s0 + s + q + u * kSplits;
+            const T *c = cp + (tile_index(I, J, nt) * kTile + r) * D;
             const T *rp = rpart + (static_cast<int64_t>(slot) * kTile + r) * D;
 #pragma unroll
-            for (int d = 0; d < D; ++d) v[u][d] = slot < s1 ? rp[d] : T(0);
+            for (int d = 0; d < D; ++d) {
+                vc[u][d] = I <= J ? c[d] : T(0);
+                vr[u][d] = slot < s1 ? rp[d] : T(0);
+            }
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u)
 #pragma unroll
             for (int d = 0; d < D; ++d) {
-                if constexpr (kF32)
-                    df_add(acc[d], -v[u][d]);
-                else
-                    acc[d] -= v[u][d];
+                if constexpr (kF32) {
+                    df_add(acc[d], vc[u][d]);
+                    df_add(acc[d], -vr[u][d]);
+                } else {
+                    acc[d] += vc[u][d];
+                    acc[d] -= vr[u][d];
+                }
             }
     }
     // the kSplits partial sums of every (row, coordinate), combined one
@@ -352,17 +361,17 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             }
             bad |= !isfinite(gv);
             if (mode != kModeEval) {
-                const T xv = x[it * D + d];
+                const T xv = xv0[d];
                 T tg = gv - static_cast<T>(a.lambda) * xv;  // gradient of log pi
-                if (a.prior_grad) tg += static_cast<T>(a.prior_grad[it * D + d]);
+                if (a.prior_grad) tg += static_cast<T>(pg0[d]);
                 if (mode == kModeKickDrift) {
-                    const T pn = p[it * D + d] + static_cast<T>(a.eps) * tg;
+                    const T pn = pv0[d] + static_cast<T>(a.eps) * tg;
                     const T xn = xv + static_cast<T>(a.eps) * pn;
                     p[it * D + d] = pn;
                     store_x_at<T>(a.xs, it, k, D, d, xn);
                     xmax = fmaxf(xmax, fabsf(static_cast<float>(xn)));
                 } else {  // kModeHalfKick
-                    const T pn = p[it * D + d] + static_cast<T>(0.5 * a.eps) * tg;
+                    const T pn = pv0[d] + static_cast<T>(0.5 * a.eps) * tg;
                     p[it * D + d] = pn;
                     if constexpr (kF32) {
                         df_add(ke, 0.5f * pn * pn);
@@ -825,7 +834,10 @@ int grid_for(int64_t work, int threads) {
 }  // namespace
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t s) {
-    const dim3 grid(a.nt * kRedQuarters + 1);  // kRedQuarters CTAs per column block + one for the scalars
+    // kRedQuarters CTAs per column block + one for the scalars (L, sum r,
+    // dL/dsigma), which a kick-drift step inside a trajectory does not use:
+    // there it is left out
+    const dim3 grid(a.nt * kRedQuarters + (a.mode == kModeKickDrift ? 0 : 1));
     cudaError_t e = cudaSuccess;
     if (a.fp64) {
         MDS_SWITCH_D_PDL(reduce_kernel, double, grid, kRedThreads, s, a)

@@ -373,6 +373,19 @@ def locality_order(x):
     return perm
 
 
+def tree_plan_check(n, parent, length, d):
+    """Check the per-cluster work split of the tree prior for this forest
+    (mds_tree_plan_check; host only).  Returns its statistics as a dict."""
+    par = np.ascontiguousarray(parent, dtype=np.int64)
+    ln = np.ascontiguousarray(length, dtype=np.float64)
+    st = np.zeros(8, dtype=np.int64)
+    capi.check(capi.lib().mds_tree_plan_check(int(n), len(par), par.ctypes.data_as(ctypes.c_void_p),
+                                              ln.ctypes.data_as(ctypes.c_void_p), int(d),
+                                              st.ctypes.data_as(ctypes.c_void_p)))
+    keys = ("cluster", "parts", "chain_levels", "smem_bytes", "block_roots", "max_top", "max_block_nodes", "trees")
+    return dict(zip(keys, (int(v) for v in st)))
+
+
 class Batch:
     """Several datasets (uneven N, same D), each with several HMC chains,
     advanced together: one batched pair pass per leapfrog step for all chains."""

@@ -180,6 +180,45 @@ def random_forest(tree_sizes, n_lone=0, d=2, seed=0, tau0=1.0, tau_u=2.0, rate=1
                   float(tau0), float(tau_u))
 
 
+def _sigma_mu(rng, d):
+    a = rng.standard_normal((d, d))
+    return a @ a.T / d + 0.5 * np.eye(d), rng.standard_normal(d)
+
+
+def ladder_forest(n_tips, d=2, seed=0, tau0=1.0, tau_u=2.0):
+    """One caterpillar tree (the deepest shape: height n_tips - 1): internal
+    node n_tips + k joins the previous internal node (tips 0 and 1 for k = 0)
+    and tip k + 1; seeded branch lengths in (0.05, 1.05)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(n_tips)
+    parent = np.full(2 * n - 1, -1, dtype=np.int64)
+    parent[0] = parent[1] = n
+    for k in range(1, n - 1):
+        parent[n + k - 1] = n + k
+        parent[k + 1] = n + k
+    length = 0.05 + rng.uniform(size=2 * n - 1)
+    length[-1] = 0.0
+    sigma_mat, mu = _sigma_mu(rng, d)
+    return Forest(n, parent, length, sigma_mat, mu, float(tau0), float(tau_u))
+
+
+def balanced_forest(levels, d=2, seed=0, tau0=1.0, tau_u=2.0):
+    """One complete binary tree over 2^levels tips (height `levels`): node
+    ids by level, tips first; seeded branch lengths in (0.05, 1.05)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = 1 << int(levels)
+    parent = np.full(2 * n - 1, -1, dtype=np.int64)
+    first, width, nxt = 0, n, n
+    while width > 1:
+        for i in range(width):
+            parent[first + i] = nxt + i // 2
+        first, nxt, width = nxt, nxt + width // 2, width // 2
+    length = 0.05 + rng.uniform(size=2 * n - 1)
+    length[-1] = 0.0
+    sigma_mat, mu = _sigma_mu(rng, d)
+    return Forest(n, parent, length, sigma_mat, mu, float(tau0), float(tau_u))
+
+
 def brownian_tips(forest, seed=0):
     """One draw of X (N x D) from the Brownian diffusion down the forest:
     roots ~ N(mu, tau0 Sigma), children ~ N(parent, length Sigma),

@@ -2,7 +2,8 @@
 the dense FP64 oracle (oracle/tree_prior.py), through the C ABI: log p(X)
 and d log p / dX by the device's two tree traversals, for forests with
 several trees and unsequenced items, D = 1..6, both location precisions, up
-to the paper's four subtype trees (N = 5392).
+to the paper's four subtype trees (N = 5392), and the deepest (caterpillar)
+and shallowest (complete) tree shapes.
 
 Tolerance.  Both sides are FP64, but the oracle factorises the dense V,
 whose condition number kappa(V) grows with N (coalescent trees have very
@@ -62,6 +63,24 @@ def test_paper_scale_forest_matches_oracle():
     f = W.random_forest(W.SUBTYPE_SIZES, n_lone=0, d=2, seed=1)
     x = W.brownian_tips(f, seed=5)
     print("N=5392", check(f, x, "fp64", 1e-7))
+
+
+@pytest.mark.parametrize("n,d", [(600, 2), (2000, 3)])
+def test_caterpillar_matches_oracle(n, d):
+    # the deepest tree: one level per internal node, nearly all of them in the
+    # top (CTA 0); at n = 2000 the top's messages exceed shared memory and
+    # live in global scratch
+    f = W.ladder_forest(n, d=d, seed=n)
+    x = W.brownian_tips(f, seed=7)
+    print("ladder", n, check(f, x, "fp64", 1e-7))
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_complete_tree_matches_oracle(prec):
+    # the shallowest tree: wide levels spread over a full cluster
+    f = W.balanced_forest(11, d=2, seed=11)
+    x = W.brownian_tips(f, seed=8)
+    print("complete 2048", prec, check(f, x, prec, 1e-7))
 
 
 def test_only_unsequenced_items():
