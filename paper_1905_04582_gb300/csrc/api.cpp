@@ -136,7 +136,7 @@ struct mds_ctx {
     TreeArgs tree{};                      // device pointers and constants (x set per launch)
     double *tree_grad0 = nullptr;         // its gradient at the trajectory start (restored on reject)
     cudaStream_t tree_stream = nullptr;   // the traversal runs here, beside the pair pass
-    cudaEvent_t tree_fork = nullptr, tree_join = nullptr, tree_started = nullptr;
+    cudaEvent_t tree_fork = nullptr, tree_join = nullptr;
     int64_t rw_iter = 0;                  // random-walk proposals drawn so far (Philox counter)
     std::vector<void *> tree_bufs;        // its device allocations
 
@@ -490,16 +490,14 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_na
         ta.out = c->scal + kPriorLogp;
         e = cudaEventRecord(c->tree_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->tree_stream, c->tree_fork, 0);
-        if (e == cudaSuccess) e = launch_tree_prior(ta, c->d, c->tree_stream, c->tree_started);
+        if (e == cudaSuccess) e = launch_tree_prior(ta, c->d, c->tree_stream);
         if (e == cudaSuccess) e = cudaEventRecord(c->tree_join, c->tree_stream);
-        // the pass starts once every traversal CTA has begun: the traversal's
-        // clusters (8 CTAs on 8 SMs of one GPC at once) are placed before the
-        // pass's CTAs fill the SMs
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->tree_started, 0);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior launch: %s", cudaGetErrorString(e));
     }
-    // with a tree prior the pass is launched without PDL (it waits for the
-    // traversal's start, not for the reduction's tail)
+    // with a tree prior the pass is launched without PDL: it then becomes
+    // eligible when the traversal does, as the reduction completes, and the
+    // traversal's high-priority clusters are placed while SMs are free
+    // (launched early by PDL, the pass's CTAs would hold every SM)
     const bool pdl = !c->tree_on;
     e = c->fp64 ? launch_pair_pass_f64(a, c->d, s, pdl) : launch_pair_pass_f32(a, c->d, s, pdl);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
@@ -1129,7 +1127,6 @@ int mds_destroy(mds_ctx *c) {
     }
     if (c->tree_fork) cudaEventDestroy(c->tree_fork);
     if (c->tree_join) cudaEventDestroy(c->tree_join);
-    if (c->tree_started) cudaEventDestroy(c->tree_started);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (cudaEvent_t e : c->prof_a) cudaEventDestroy(e);
@@ -1846,7 +1843,6 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
         CU(cudaStreamCreateWithPriority(&c->tree_stream, cudaStreamNonBlocking, hi));
         CU(cudaEventCreateWithFlags(&c->tree_fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&c->tree_join, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&c->tree_started, cudaEventDisableTiming));
     }
     TreeArgs ta{};
     auto up = [&](void **dst, const void *src, size_t bytes) -> int {

@@ -406,10 +406,7 @@ struct TreeArgs {
     double *out;             // log p (out, device scalar)
 };
 constexpr int kTreeMaxCluster = 8;  // CTAs per tree (portable cluster size)
-// started (optional): an event that fires once every CTA of the launch has
-// begun (a launch-completion event), for work that should start only after
-// the traversal holds its SMs.
-cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s, cudaEvent_t started = nullptr);
+cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Single-item random-walk Metropolis (rwmh.cu): one CTA runs the proposals

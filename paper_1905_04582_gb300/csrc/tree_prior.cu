@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kTreeThreads, 1) tree_prior_kernel(const __gri
 }
 
 template <int D, typename T>
-cudaError_t launch_t(const TreeArgs &a, int grid, cudaStream_t s, cudaEvent_t started) {
+cudaError_t launch_t(const TreeArgs &a, int grid, cudaStream_t s) {
     static int attr_bytes = 0;  // per instantiation, raised once as needed
     if (a.smem_bytes > attr_bytes) {
         const cudaError_t e =
@@ -416,7 +416,7 @@ cudaError_t launch_t(const TreeArgs &a, int grid, cudaStream_t s, cudaEvent_t st
     cfg.blockDim = dim3(kTreeThreads);
     cfg.dynamicSmemBytes = static_cast<size_t>(a.smem_bytes);
     cfg.stream = s;
-    cudaLaunchAttribute attr[3];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributePriority;
     attr[0].val.priority = hi;
     attr[1].id = cudaLaunchAttributeClusterDimension;
@@ -425,35 +425,29 @@ cudaError_t launch_t(const TreeArgs &a, int grid, cudaStream_t s, cudaEvent_t st
     attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    if (started) {
-        attr[2].id = cudaLaunchAttributeLaunchCompletionEvent;
-        attr[2].val.launchCompletionEvent.event = started;
-        attr[2].val.launchCompletionEvent.flags = 0;
-        cfg.numAttrs = 3;
-    }
     return cudaLaunchKernelEx(&cfg, tree_prior_kernel<D, T>, a);
 }
 
 template <int D>
-cudaError_t launch_d(const TreeArgs &a, cudaStream_t s, cudaEvent_t started) {
+cudaError_t launch_d(const TreeArgs &a, cudaStream_t s) {
     const int grid = (a.n_trees + (a.n_lone > 0 ? 1 : 0)) * a.cluster;
     if (grid <= 0) return cudaErrorInvalidValue;
-    return a.x_f64 ? launch_t<D, double>(a, grid, s, started) : launch_t<D, float>(a, grid, s, started);
+    return a.x_f64 ? launch_t<D, double>(a, grid, s) : launch_t<D, float>(a, grid, s);
 }
 
 }  // namespace
 
-cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s, cudaEvent_t started) {
+cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s) {
     if (a.cluster < 1 || a.cluster > kTreeMaxCluster) return cudaErrorInvalidValue;
     switch (d) {
-        case 1: return launch_d<1>(a, s, started);
-        case 2: return launch_d<2>(a, s, started);
-        case 3: return launch_d<3>(a, s, started);
-        case 4: return launch_d<4>(a, s, started);
-        case 5: return launch_d<5>(a, s, started);
-        case 6: return launch_d<6>(a, s, started);
-        case 7: return launch_d<7>(a, s, started);
-        case 8: return launch_d<8>(a, s, started);
+        case 1: return launch_d<1>(a, s);
+        case 2: return launch_d<2>(a, s);
+        case 3: return launch_d<3>(a, s);
+        case 4: return launch_d<4>(a, s);
+        case 5: return launch_d<5>(a, s);
+        case 6: return launch_d<6>(a, s);
+        case 7: return launch_d<7>(a, s);
+        case 8: return launch_d<8>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
