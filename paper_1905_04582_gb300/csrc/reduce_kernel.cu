@@ -181,6 +181,11 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         s0 = a.row_first_slot[Jq / kRedQuarters];
         s1 = a.row_first_slot[Jq / kRedQuarters + 1];
     }
+    // the split's bound changes only at a trajectory's end (not in a
+    // kick-drift launch)
+    float xbound = 0.f;
+    if constexpr (kF32)
+        if (mode == kModeKickDrift) xbound = a.xs.split->bound;
     // every input (partials, x, p) comes from the pass just before
     pdl_trigger();
     pdl_wait();
@@ -317,30 +322,40 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
                 }
             }
     }
-    // the kSplits partial sums of every (row, coordinate), combined one
-    // coordinate at a time through shared memory, in a fixed order
-    Acc gsum[D];
+    // the kSplits partial sums of every (row, coordinate), in a fixed order:
+    // the two splits of a warp (lanes r and r + 16) by a shuffle, then the
+    // warps' sums through shared memory, all coordinates at once
+    constexpr int kRedWarps = kRedThreads / 32;
+    __shared__ Acc smw[kRedWarps * kRedRows * D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        const int rq = tid % kRedRows;
-        sm[s * kRedRows + rq] = acc[d];
-        __syncthreads();
-        if (s == 0) {
-            Acc g = sm[rq];
+        if constexpr (kF32)
+            df_add(acc[d], df_shfl_xor(acc[d], 16));
+        else
+            acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], 16);
+    }
+    if ((tid & 31) < kRedRows) {
 #pragma unroll
-            for (int q = 1; q < kSplits; ++q) {
+        for (int d = 0; d < D; ++d) smw[((tid >> 5) * kRedRows + (tid & 31)) * D + d] = acc[d];
+    }
+    __syncthreads();
+    Acc gsum[D];
+    if (s == 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            Acc g = smw[tid * D + d];
+#pragma unroll
+            for (int w = 1; w < kRedWarps; ++w) {
                 if constexpr (kF32)
-                    df_add(g, sm[q * kRedRows + rq]);
+                    df_add(g, smw[(w * kRedRows + tid) * D + d]);
                 else
-                    g += sm[q * kRedRows + rq];
+                    g += smw[(w * kRedRows + tid) * D + d];
             }
             gsum[d] = g;
         }
-        __syncthreads();
     }
 
     Acc ke{}, xx{};
-    float xmax = 0.f;
     if (s == 0 && k < a.n) {
         // slot k of the tile layouts holds item `it` of the state
         const int64_t it = item_of_slot;
@@ -369,7 +384,11 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
                     const T xn = xv + static_cast<T>(a.eps) * pn;
                     p[it * D + d] = pn;
                     store_x_at<T>(a.xs, it, k, D, d, xn);
-                    xmax = fmaxf(xmax, fabsf(static_cast<float>(xn)));
+                    // the running max |x| only matters once it passes the
+                    // split's bound (the end-of-trajectory reduction then
+                    // grows the quantum), so only such values are recorded
+                    if constexpr (kF32)
+                        if (fabsf(xn) > xbound) atomicMax(a.xs.xmax_bits, __float_as_uint(fabsf(xn)));
                 } else {  // kModeHalfKick
                     const T pn = pv0[d] + static_cast<T>(0.5 * a.eps) * tg;
                     p[it * D + d] = pn;
@@ -403,13 +422,6 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             }
         }
     }
-    if constexpr (kF32) {
-        if (mode == kModeKickDrift) {
-            __syncthreads();
-            const float m = block_max<kRedThreads>(xmax, reinterpret_cast<float *>(sm));
-            if (tid == 0 && m > 0.f) atomicMax(a.xs.xmax_bits, __float_as_uint(m));
-        }
-    }
 }
 
 template <typename T, int D>
@@ -436,6 +448,9 @@ __device__ __forceinline__ void traj_start_body(const TrajArgs &a, int bx) {
     using Acc = typename std::conditional<kF32, DF, double>::type;
     using G = typename GradT<T>::type;
     __shared__ Acc sm[kTrajThreads / 32];
+    // the first pass of the trajectory may become resident and stage its
+    // first Y tiles meanwhile (it waits for this kernel before reading x)
+    pdl_trigger();
     const int64_t nd = a.n * D;
     const int64_t q = static_cast<int64_t>(bx) * kTrajThreads + threadIdx.x;  // 4 elements each
     T *x = reinterpret_cast<T *>(a.xs.x);
@@ -537,6 +552,9 @@ __device__ __forceinline__ void traj_end_body(const AcceptArgs &a, int bx, int n
     // every CTA sums the same partials in the same order -> same decision
     __shared__ int keep_s;
     __shared__ double dh_s;
+    // launched with PDL after the trajectory's last reduction: every input
+    // comes from it or from kernels before it
+    pdl_wait();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         double ke0 = 0.0, xx0 = 0.0, ke1 = 0.0, xx1 = 0.0;
@@ -861,12 +879,13 @@ cudaError_t launch_traj_start(const TrajArgs &a, int *grid_out, cudaStream_t s) 
 
 cudaError_t launch_traj_end(const AcceptArgs &a, cudaStream_t s) {
     const int grid = grid_for(a.n * a.d, kTrajThreads);
+    cudaError_t e = cudaSuccess;
     if (a.fp64) {
-        MDS_SWITCH_D(traj_end_kernel, double, grid, kTrajThreads, s, a)
+        MDS_SWITCH_D_PDL(traj_end_kernel, double, grid, kTrajThreads, s, a)
     } else {
-        MDS_SWITCH_D(traj_end_kernel, float, grid, kTrajThreads, s, a)
+        MDS_SWITCH_D_PDL(traj_end_kernel, float, grid, kTrajThreads, s, a)
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 #define MDS_SWITCH_DB(KERNEL, GRID, BLOCK, STREAM, D, ...)                       \
