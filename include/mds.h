@@ -358,7 +358,8 @@ int mds_tree_prior(mds_ctx *ctx, double *logp, void *grad, int dtype, int where)
  * accepted iff log u_t < log pi(X') - log pi(X), log pi = L(X, sigma) -
  * (lambda/2) ||X||^2 (mds_set_prior; no tree prior), with
  * L(X') - L(X) = sum_{j != i} [r_ij(x_i) - r_ij(x_i')].  Proposals run in
- * order in one CTA (each depends on the decisions before it): O(N D) work
+ * order (each depends on the decisions before it), each row split over one
+ * cluster of up to 8 CTAs: O(N D) work
  * each.  Draws: items [n_prop] (0..N-1), z_all [n_prop x D] and u_all
  * [n_prop] in (0,1), host arrays, all three given or all NULL; NULL draws
  * from Philox4x32-10 keyed by seed: proposal t (a per-context counter)

@@ -2025,6 +2025,9 @@ int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *
     }
     // X in shared memory when it fits (160 KB)
     a.x_in_smem = static_cast<int64_t>(c->n) * d * static_cast<int64_t>(elem(c)) <= 160 * 1024;
+    // one 1024-thread CTA per 1024 slots of the row, up to a cluster of 8,
+    // each CTA with its own copy of X (so only when X fits in shared memory)
+    a.cluster = a.x_in_smem ? static_cast<int32_t>(std::min<int64_t>(8, std::max<int64_t>(1, (c->n + 1023) / 1024))) : 1;
     cudaError_t e = cudaSuccess;
     if (!inj)
         e = launch_rwmh_draws(a, d, const_cast<int64_t *>(a.items), const_cast<double *>(a.z),

@@ -426,6 +426,7 @@ struct RwmhArgs {
     const double *z;          // [n_prop][D]
     const double *logu;       // [n_prop] log of the uniforms
     bool x_in_smem;           // keep X in shared memory (N D values fit)
+    int32_t cluster;          // CTAs (one cluster) that share each proposal's row; > 1 only with x_in_smem
     uint64_t seed;
     uint32_t chain;
     int64_t iter0;            // Philox counter of the first proposal

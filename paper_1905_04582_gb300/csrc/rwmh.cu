@@ -5,11 +5,12 @@
 // is
 //   L(X') - L(X) = sum_{j != i} [r_ij(x_i) - r_ij(x_i')] - (lambda/2)(|x_i'|^2 - |x_i|^2)
 // (the -M log sigma of Eq. (2) cancels).  Proposals are sequential (each
-// depends on the decisions before it), so one CTA runs them in a loop: its
-// threads split the row by slot of the tile layout (in the locality order of
-// mds_reorder neighbouring slots hold nearby items), four slots per thread
-// per round with their loads issued together, and thread 0 takes the
-// decision.  Per-pair arithmetic is in the precision of the context's state
+// depends on the decisions before it), so one cluster of CTAs runs them in a
+// loop: its threads split the row by slot of the tile layout (in the locality
+// order of mds_reorder neighbouring slots hold nearby items), four slots per
+// thread per round with their loads issued together, the CTAs' partial sums
+// meet through distributed shared memory, and thread 0 of every CTA takes
+// the same decision.  Per-pair arithmetic is in the precision of the context's state
 // (FP32 with CUDA's erfcf / log1pf, or FP64), sums in FP64.  The FP32 path
 // skips log Phi where both z = delta / sigma are >= 8 (each term is then
 // below 6.3e-16), as the pair pass does.  Held-out pairs of a
@@ -81,33 +82,74 @@ __global__ void rwmh_draws_kernel(RwmhArgs a, int64_t *items, double *z, double 
     }
 }
 
-constexpr int kRwSlotRegs = 8;  // slots per thread whose items stay in registers (N <= 8192)
+// (s, c): a sum and the compensation to subtract from it; the 32 lanes'
+// pairs added in a fixed butterfly, each addition's rounding error carried
+// (two-sum), so every lane ends with the same pair.
+template <typename T>
+__device__ __forceinline__ void pair_tree(T &hs, T &hc) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const T os = __shfl_xor_sync(0xffffffffu, hs, o), oc = __shfl_xor_sync(0xffffffffu, hc, o);
+        const T s2 = hs + os;
+        const T bb = s2 - hs;
+        const T err = (hs - (s2 - bb)) + (os - bb);  // exact rounding error of hs + os
+        hs = s2;
+        hc = hc + oc - err;
+    }
+}
 
-// The chain.  X is kept in shared memory when a.x_in_smem (N D values), the
-// items of this thread's slots in registers when N <= kRwSlotRegs * threads;
-// thread 0 prefetches the next proposal's draws while the block works.
+constexpr int kRwSlotRegs = 8;  // slots per thread whose items stay in registers
+constexpr int kRwMaxCluster = 8;
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
+}
+
+// v into the shared-memory word `local` of CTA `rank` of this cluster.
+__device__ __forceinline__ void st_cluster(double *local, unsigned rank, double v) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(local));
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+
+// The chain, on one cluster of a.cluster CTAs (gridDim.x).  Every CTA keeps
+// its own copy of X (shared memory when a.x_in_smem, which a cluster of more
+// than one CTA requires), takes the rounds r = rank, rank + C, ... of the
+// row's 1024-slot rounds, and sends its partial sum of the row to every
+// CTA; after one cluster barrier per proposal each CTA adds the C partials
+// in rank order and takes the same decision.  CTA 0 writes the state and the
+// outputs.  Thread 0 of each CTA prefetches the next proposal's draws while
+// the block works.
 template <typename T, int D>
 __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant__ RwmhArgs a) {
     extern __shared__ __align__(16) unsigned char rsm[];
     __shared__ T xo[D], xn[D];
     __shared__ int64_t s_item, s_slot;
-    __shared__ double sm[kRwThreads / 32];
+    __shared__ T sm_s[kRwThreads / 32], sm_c[kRwThreads / 32];
+    __shared__ double s_dsq;  // |x_i'|^2 - |x_i|^2 of the current proposal
+    __shared__ double cl_part[2][kRwMaxCluster];  // per proposal parity: the CTAs' partial sums
     T *xg = static_cast<T *>(a.x);
     T *xs = a.x_in_smem ? reinterpret_cast<T *>(rsm) : xg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncl = static_cast<int>(gridDim.x), rank = static_cast<int>(blockIdx.x);
     const T half_inv_s2 = static_cast<T>(0.5 / (a.sigma * a.sigma));
     const T inv_s_sqrt2 = static_cast<T>(0.70710678118654752440 / a.sigma);
     const T far_delta = static_cast<T>(8.0 * a.sigma);
     const int64_t n = a.n;
     if (a.x_in_smem)
         for (int64_t e = tid; e < n * D; e += kRwThreads) xs[e] = xg[e];
+    // this CTA's rounds of the row: r = rank + lr * ncl, lr < nr
+    const int rounds = static_cast<int>((n + kRwThreads - 1) / kRwThreads);
+    const int nr = rounds > rank ? (rounds - rank + ncl - 1) / ncl : 0;
     // items of this thread's slots (fixed for the whole chain)
-    const bool slots_in_regs = n <= static_cast<int64_t>(kRwSlotRegs) * kRwThreads;
+    const bool slots_in_regs = nr <= kRwSlotRegs;
     int32_t my_item[kRwSlotRegs];
 #pragma unroll
-    for (int r = 0; r < kRwSlotRegs; ++r) {
-        const int64_t sj = tid + static_cast<int64_t>(r) * kRwThreads;
-        my_item[r] = (slots_in_regs && sj < n) ? static_cast<int32_t>(a.perm ? a.perm[sj] : sj) : -1;
+    for (int q = 0; q < kRwSlotRegs; ++q) {
+        const int64_t sj = tid + static_cast<int64_t>(rank + q * ncl) * kRwThreads;
+        my_item[q] = (slots_in_regs && q < nr && sj < n) ? static_cast<int32_t>(a.perm ? a.perm[sj] : sj) : -1;
     }
     // thread 0: the draws of the current proposal (and the next one, prefetched)
     int64_t i_cur = 0, si_cur = 0;
@@ -141,12 +183,17 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
             }
             s_item = i_cur;
             s_slot = si_cur;
+            double sq0 = 0.0, sq1 = 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const T v = xs[i_cur * D + k];
+                const T w = v + static_cast<T>(a.step * z_cur[k]);
                 xo[k] = v;
-                xn[k] = v + static_cast<T>(a.step * z_cur[k]);
+                xn[k] = w;
+                sq0 += static_cast<double>(v) * static_cast<double>(v);
+                sq1 += static_cast<double>(w) * static_cast<double>(w);
             }
+            s_dsq = sq1 - sq0;
         }
         __syncthreads();
         const int64_t i = s_item;
@@ -155,20 +202,19 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
         // arithmetic's precision (FP64 conversions run at 1/64 rate on this
         // GPU), widened to FP64 once before the block sum
         T acc_s = T(0), acc_c = T(0);
-        const int rounds = static_cast<int>((n + kRwThreads - 1) / kRwThreads);
-        for (int r0 = 0; r0 < rounds; r0 += kRwUnroll) {
+        for (int lr0 = 0; lr0 < nr; lr0 += kRwUnroll) {
             int64_t item[kRwUnroll];
             float yv[kRwUnroll];
 #pragma unroll
             for (int u = 0; u < kRwUnroll; ++u) {
-                const int r = r0 + u;
-                const int64_t sj = tid + static_cast<int64_t>(r) * kRwThreads;
+                const int lr = lr0 + u;
+                const int64_t sj = tid + static_cast<int64_t>(rank + lr * ncl) * kRwThreads;
                 int64_t it = -1;
-                if (sj < n && sj != si) {
+                if (lr < nr && sj < n && sj != si) {
                     if (slots_in_regs) {
 #pragma unroll
                         for (int q = 0; q < kRwSlotRegs; ++q)
-                            if (q == r) it = my_item[q];
+                            if (q == lr) it = my_item[q];
                     } else {
                         it = a.perm ? a.perm[sj] : sj;
                     }
@@ -201,44 +247,50 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
                 acc_s = tk;
             }
         }
-        // fixed-order block sum: (sum, compensation) pairs through the warp,
-        // FP64 only for the 32 warp totals
+        // fixed-order block sum of (sum, compensation) pairs: a shuffle tree
+        // in each warp, then one over the 32 warp totals in warp 0 (trees,
+        // not serial sums: a dependent FP64 addition costs ~64 cycles here);
+        // then the CTA's partial to every CTA of the cluster
         T hs = acc_s, hc = acc_c;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const T os = __shfl_xor_sync(0xffffffffu, hs, o), oc = __shfl_xor_sync(0xffffffffu, hc, o);
-            const T s2 = hs + os;
-            const T bb = s2 - hs;
-            const T err = (hs - (s2 - bb)) + (os - bb);  // exact rounding error of hs + os
-            hs = s2;
-            hc = hc + oc - err;
+        pair_tree(hs, hc);
+        if (lane == 0) {
+            sm_s[warp] = hs;
+            sm_c[warp] = hc;
         }
-        if (lane == 0) sm[warp] = static_cast<double>(hs) - static_cast<double>(hc);
         __syncthreads();
+        if (warp == 0) {
+            hs = sm_s[lane];
+            hc = sm_c[lane];
+            pair_tree(hs, hc);
+            if (lane == 0) {
+                const double dc = static_cast<double>(hs) - static_cast<double>(hc);
+                for (int r = 0; r < ncl; ++r) st_cluster(&cl_part[t & 1][rank], static_cast<unsigned>(r), dc);
+            }
+        }
+        // the partials of proposal t are in every CTA; a partial of proposal
+        // t + 2 (same buffer) is written only after every CTA has passed the
+        // next barrier, that is after it has read these
+        cluster_sync_all();
         if (tid == 0) {
             double dl = 0.0;
-            for (int w = 0; w < kRwThreads / 32; ++w) dl += sm[w];
-            double sq0 = 0.0, sq1 = 0.0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                sq0 += static_cast<double>(xo[k]) * static_cast<double>(xo[k]);
-                sq1 += static_cast<double>(xn[k]) * static_cast<double>(xn[k]);
-            }
-            const double lp = dl - 0.5 * a.lambda * (sq1 - sq0);
+            for (int r = 0; r < ncl; ++r) dl += cl_part[t & 1][r];
+            const double lp = dl - 0.5 * a.lambda * s_dsq;
             const bool keep = isfinite(lp) && lu_cur < lp;
             if (keep) {
                 float mx = 0.f;
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     xs[i * D + k] = xn[k];
-                    xg[i * D + k] = xn[k];
+                    if (rank == 0) xg[i * D + k] = xn[k];
                     mx = fmaxf(mx, fabsf(static_cast<float>(xn[k])));
                 }
-                if (a.xmax_bits && mx > 0.f) atomicMax(a.xmax_bits, __float_as_uint(mx));
+                if (rank == 0 && a.xmax_bits && mx > 0.f) atomicMax(a.xmax_bits, __float_as_uint(mx));
             }
-            if (!isfinite(lp)) atomicOr(a.err, kErrNonfinite);
-            if (a.acc_out) a.acc_out[t] = keep ? 1 : 0;
-            if (a.dl_out) a.dl_out[t] = lp;
+            if (rank == 0) {
+                if (!isfinite(lp)) atomicOr(a.err, kErrNonfinite);
+                if (a.acc_out) a.acc_out[t] = keep ? 1 : 0;
+                if (a.dl_out) a.dl_out[t] = lp;
+            }
             i_cur = i_nxt;
             si_cur = si_nxt;
 #pragma unroll
@@ -249,18 +301,35 @@ __global__ void __launch_bounds__(kRwThreads) rwmh_kernel(const __grid_constant_
     }
 }
 
+template <typename T, int D>
+cudaError_t launch_td(const RwmhArgs &a, int smem, cudaStream_t s) {
+    if (smem) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(rwmh_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(static_cast<unsigned>(a.cluster));
+    cfg.blockDim = dim3(kRwThreads);
+    cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(a.cluster);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, rwmh_kernel<T, D>, a);
+}
+
 template <int D>
 cudaError_t launch_d(const RwmhArgs &a, cudaStream_t s) {
+    // a cluster of several CTAs needs each CTA's own copy of X
+    if (a.cluster < 1 || a.cluster > kRwMaxCluster || (a.cluster > 1 && !a.x_in_smem)) return cudaErrorInvalidValue;
     const size_t xbytes = static_cast<size_t>(a.n) * D * (a.fp64 ? 8 : 4);
     const int smem = a.x_in_smem ? static_cast<int>(xbytes) : 0;
-    cudaError_t e = cudaSuccess;
-    if (a.fp64) {
-        if (smem) e = cudaFuncSetAttribute(rwmh_kernel<double, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) rwmh_kernel<double, D><<<1, kRwThreads, smem, s>>>(a);
-    } else {
-        if (smem) e = cudaFuncSetAttribute(rwmh_kernel<float, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) rwmh_kernel<float, D><<<1, kRwThreads, smem, s>>>(a);
-    }
+    const cudaError_t e = a.fp64 ? launch_td<double, D>(a, smem, s) : launch_td<float, D>(a, smem, s);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

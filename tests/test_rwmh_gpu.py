@@ -2,7 +2,8 @@
 GPU against the FP64 oracle, through the C ABI: the same decisions and
 log-target differences with injected draws and with the device's Philox
 draws, both precisions, in the caller's and the locality order, held-out
-pairs left out of the target, and the argument checks.
+pairs left out of the target, a row split over a cluster of CTAs (N > 1024),
+and the argument checks.
 
 The FP32C state is FP32, so a proposal x_i + step z is rounded to FP32
 before it is evaluated; its reference is a replay at exactly those FP32
@@ -109,6 +110,21 @@ def test_philox_draws_match_oracle(prec):
         acc, dl = m.rwmh(k, 0.04, seed=seed)
         x = m.get_locations()
     assert compare_chain(prec, acc, dl, x, acc_r, dl_r, u, xr) > 50
+
+
+@pytest.mark.parametrize("prec,n,k", [("fp64", 5000, 300), ("fp32c", 2100, 40)])
+def test_cluster_of_ctas_matches_oracle(prec, n, k):
+    # N > 1024: the row is split over a cluster of ceil(N / 1024) CTAs whose
+    # partial sums meet in every CTA before the decision
+    wl = W.custom(n, 2, sigma=0.3, seed=67, mixture=(5, 0.3))
+    rng = np.random.default_rng(68)
+    items, z, u = rng.integers(0, wl.n, k), rng.standard_normal((k, 2)), rng.uniform(size=k)
+    xr, acc_r, dl_r = reference(prec, wl, items, z, u, 0.02, lam=0.05)
+    with model(wl, prec, reorder=True, lam=0.05) as m:
+        acc, dl = m.rwmh(k, 0.02, items=items, z_all=z, u_all=u)
+        x = m.get_locations()
+    assert compare_chain(prec, acc, dl, x, acc_r, dl_r, u, xr) > k // 3
+    assert 0 < acc_r.sum() < k
 
 
 def test_held_out_pairs_are_left_out():
