@@ -47,8 +47,6 @@ struct DF {
     float hi, lo;
 };
 
-__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
-
 __device__ __forceinline__ void df_add(DF &a, float v) {
     const float s = __fadd_rn(a.hi, v);
     const float bp = __fsub_rn(s, a.hi);
@@ -359,7 +357,6 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     if (s == 0 && k < a.n) {
         // slot k of the tile layouts holds item `it` of the state
         const int64_t it = item_of_slot;
-        T *x = reinterpret_cast<T *>(a.xs.x);
         T *p = reinterpret_cast<T *>(a.p);
         G *grad = reinterpret_cast<G *>(a.grad);
         bool bad = false;
