@@ -160,6 +160,23 @@ struct GradT<double> {
 
 // One CTA of the reduction: column block J of one problem, or its scalar
 // sums when J < 0.  `a` may live in global memory (batched launches).
+// The D coordinates of one partial (zeros when !ok): FP32 pairs as one 8-byte
+// load (a partial's row starts at a multiple of D floats).
+template <typename T, int D>
+__device__ __forceinline__ void load_coords(const T *p, bool ok, T (&v)[D]) {
+    if constexpr (std::is_same<T, float>::value && D % 2 == 0) {
+#pragma unroll
+        for (int d = 0; d < D; d += 2) {
+            const float2 w = ok ? *reinterpret_cast<const float2 *>(p + d) : make_float2(0.f, 0.f);
+            v[d] = w.x;
+            v[d + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) v[d] = ok ? p[d] : T(0);
+    }
+}
+
 template <typename T, int D>
 __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int Jq) {
     constexpr bool kF32 = std::is_same<T, float>::value;
@@ -301,11 +318,8 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             const int slot = s0 + s + q + u * kSplits;
             const T *c = cp + (tile_index(I, J, nt) * kTile + r) * D;
             const T *rp = rpart + (static_cast<int64_t>(slot) * kTile + r) * D;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                vc[u][d] = I <= J ? c[d] : T(0);
-                vr[u][d] = slot < s1 ? rp[d] : T(0);
-            }
+            load_coords<T, D>(c, I <= J, vc[u]);
+            load_coords<T, D>(rp, slot < s1, vr[u]);
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u)
