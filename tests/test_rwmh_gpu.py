@@ -3,7 +3,8 @@ GPU against the FP64 oracle, through the C ABI: the same decisions and
 log-target differences with injected draws and with the device's Philox
 draws, both precisions, in the caller's and the locality order, held-out
 pairs left out of the target, a row split over a cluster of CTAs (N > 1024),
-and the argument checks.
+the state in global memory (N D beyond shared memory), and the argument
+checks.
 
 The FP32C state is FP32, so a proposal x_i + step z is rounded to FP32
 before it is evaluated; its reference is a replay at exactly those FP32
@@ -124,6 +125,21 @@ def test_cluster_of_ctas_matches_oracle(prec, n, k):
         acc, dl = m.rwmh(k, 0.02, items=items, z_all=z, u_all=u)
         x = m.get_locations()
     assert compare_chain(prec, acc, dl, x, acc_r, dl_r, u, xr) > k // 3
+    assert 0 < acc_r.sum() < k
+
+
+def test_state_in_global_memory_matches_oracle():
+    # N D FP64 values beyond shared memory: one CTA, X read and written in
+    # global memory
+    wl = W.custom(12000, 2, sigma=0.3, seed=69, mixture=(6, 0.3))
+    rng = np.random.default_rng(70)
+    k = 120
+    items, z, u = rng.integers(0, wl.n, k), rng.standard_normal((k, 2)), rng.uniform(size=k)
+    xr, acc_r, dl_r = reference("fp64", wl, items, z, u, 0.02)
+    with model(wl, "fp64") as m:
+        acc, dl = m.rwmh(k, 0.02, items=items, z_all=z, u_all=u)
+        x = m.get_locations()
+    assert compare_chain("fp64", acc, dl, x, acc_r, dl_r, u, xr) > k // 3
     assert 0 < acc_r.sum() < k
 
 
