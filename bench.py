@@ -367,6 +367,13 @@ def run_gpu(args):
         m_u.set_sigma(wl.sigma)
         ms32_unordered = m_u.time_pass(20)
     pass_dist = pass_distribution(model, wl, flush_l2, stream)
+    # the measured ceiling of the pass's per-pair arithmetic: the same bodies
+    # with their operands in registers, no memory traffic or epilogue; far
+    # blocks take the body without the Phi terms
+    ceil_near = model.pair_body_ceiling(far=False)
+    ceil_far = model.pair_body_ceiling(far=True)
+    ceil_w = 1.0 / (far_frac / ceil_far + (1.0 - far_frac) / ceil_near)
+    kernel_rate = m_pairs / (pass_avg_ms / 1e3)
 
     # end to end through the C ABI with host buffers: X in, one HMC
     # iteration, X and the statistics out
@@ -425,7 +432,13 @@ def run_gpu(args):
                          "avg_launch_ms": pass_avg_ms, "pairs_per_launch": m_pairs,
                          "hbm_view": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                                       "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                                      "algorithmic_bytes_per_launch": alg_bytes}},
+                                      "algorithmic_bytes_per_launch": alg_bytes},
+                         "measured_ceiling": {"near_pairs_per_s": ceil_near, "far_pairs_per_s": ceil_far,
+                                              "weighted_pairs_per_s": ceil_w, "kernel_pairs_per_s": kernel_rate,
+                                              "frac": kernel_rate / ceil_w,
+                                              "note": "mds_pair_body_ceiling: the pass's per-pair bodies on "
+                                                      "operands in registers at its occupancy, weighted by the "
+                                                      "far-block fraction"}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": wl.n * wl.d * 4,
                     "d2h_bytes_per_step": wl.n * wl.d * 4 + 8 + 8 + 4,
@@ -549,12 +562,20 @@ def run_batch(args):
     acc, dh = b.hmc(args.steps, N_LEAPFROG, [5e-4] * len(ds), seed=2)
     wall = time.perf_counter() - t0
     alu_peak = _alu_peak_tflops()
+    # the measured ceiling of the full per-pair body (no far blocks in the
+    # batched pass): operands in registers, the first dataset's sigma
+    from paper_1905_04582_gb300.mds import MDS
+    with MDS(128, 2, "fp32c") as mc:
+        mc.set_sigma(ds[0].sigma)
+        ceil_near = mc.pair_body_ceiling(far=False)
     print(json.dumps({"batch": True, "order": "caller", "datasets": [w.n for w in ds], "chains_per_dataset": chains,
                       "strip": b.get_strip(), "ms_per_pass": ms, "pair_evals_per_pass": evals,
                       "pair_evals_per_s": evals / (ms / 1e3),
                       "alu": {"achieved_tflops": evals * fp32_ops_per_pair(2) / (ms / 1e3) / 1e12,
                               "peak_tflops": alu_peak,
                               "frac": evals * fp32_ops_per_pair(2) / (ms / 1e3) / 1e12 / alu_peak},
+                      "measured_ceiling": {"near_pairs_per_s": ceil_near,
+                                           "frac": evals / (ms / 1e3) / ceil_near},
                       "hmc_iterations": args.steps, "leapfrog_steps_per_s_all_chains":
                           args.steps * N_LEAPFROG * len(ds) * chains / wall,
                       "accept_rate": float(np.mean(acc)), "wall_s": wall}), flush=True)

@@ -267,6 +267,18 @@ int mds_lpd_reset(mds_ctx *ctx);
  * either way; only the speed changes.
  * ------------------------------------------------------------------------ */
 
+/* Measured ceiling of the FP32C pass's per-pair arithmetic on this GPU:
+ * pairs/s of the pass's own per-pair bodies (far != 0: the body without the
+ * Phi terms that far warp blocks take; 0: the full body of Eq. (2) and its
+ * gradient) run on operands held in registers (four row pairs against two
+ * columns per round, as the tiles call them), at the pass's occupancy, over
+ * every SM, with no memory traffic, no tile epilogue and no reductions.  The
+ * context's sigma and D set the constants and the body; nothing of its state
+ * is read or changed.  Synchronises (about 10^10 pair evaluations, tens of
+ * ms).  Errors: INVALID_ARG (NULL output), STATE (FP64 context, no sigma,
+ * HMC iterations queued), OOM, CUDA. */
+int mds_pair_body_ceiling(mds_ctx *ctx, int32_t far, double *pairs_per_s);
+
 /* Host-only (no GPU needed): a locality-preserving order of N points x
  * (N x D row-major, FP64, finite): recursive bisection of the widest
  * coordinate, cut at multiples of 64 items, so that each run of 64

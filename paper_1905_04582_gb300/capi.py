@@ -87,6 +87,7 @@ SIGNATURES = {
     "mds_get_order": (_int, [_vp, _vp]),
     "mds_set_tail_cutoff": (_int, [_vp, _dbl]),
     "mds_far_blocks": (_int, [_vp, _pi64, _pi64]),
+    "mds_pair_body_ceiling": (_int, [_vp, _i32, _pdbl]),
     "mds_set_tree_prior": (_int, [_vp, _i64, _vp, _vp, _vp, _vp, _dbl, _dbl]),
     "mds_tree_prior": (_int, [_vp, _pdbl, _vp, _int, _int]),
     "mds_rwmh": (_int, [_vp, _int, _dbl, _u64, _vp, _vp, _vp, _vp, _vp]),

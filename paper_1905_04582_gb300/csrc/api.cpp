@@ -1736,6 +1736,32 @@ int mds_far_blocks(mds_ctx *c, int64_t *far, int64_t *total) {
     return MDS_OK;
 }
 
+int mds_pair_body_ceiling(mds_ctx *c, int32_t far, double *pairs_per_s) {
+    CHECK(check_ctx(c));
+    if (!pairs_per_s) return fail(c, MDS_ERR_INVALID_ARG, "pairs_per_s must not be NULL");
+    if (c->fp64) return fail(c, MDS_ERR_STATE, "the per-pair ceiling is measured for the FP32C pass");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    if (!(c->sigma > 0.0)) return fail(c, MDS_ERR_STATE, "sigma is not set (mds_set_sigma)");
+    const PairArgs a = pair_args(c);
+    const int grid = c->sm_count * pair_ceiling_blocks_per_sm(c->d);
+    float *sink = nullptr;
+    CHECK(dev_alloc_t(c, &sink, static_cast<size_t>(grid) * kPairThreads * sizeof(float)));
+    // a short launch to warm up, then a timed one of 2e10 pair evaluations
+    const int iters = std::max(64, static_cast<int>(2.0e10 / (16.0 * grid * kPairThreads)));
+    cudaError_t e = launch_pair_ceiling(a, c->d, far != 0, grid, 64, sink, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev0, c->stream);
+    if (e == cudaSuccess) e = launch_pair_ceiling(a, c->d, far != 0, grid, iters, sink, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    dev_free(sink);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair ceiling: %s", cudaGetErrorString(e));
+    *pairs_per_s = 16.0 * grid * kPairThreads * static_cast<double>(iters) / (ms * 1e-3);
+    return MDS_OK;
+}
+
 int mds_get_order(const mds_ctx *c, int32_t *perm) {
     if (!c || !perm) return MDS_ERR_INVALID_ARG;
     for (int64_t s = 0; s < c->n; ++s) perm[s] = c->reordered ? c->perm_h[s] : static_cast<int32_t>(s);

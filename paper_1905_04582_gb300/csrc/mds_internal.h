@@ -405,6 +405,13 @@ struct TreeArgs {
     unsigned *done;          // CTAs finished (0 between launches; the last one resets it)
     double *out;             // log p (out, device scalar)
 };
+// Measured ceiling of the pass's per-pair arithmetic (ceiling.cu): grid
+// CTAs of kPairThreads threads, each thread `iters` rounds of 16 pairs (four
+// row pairs against two columns, two pairs per call) with every operand in
+// registers; sink [grid * kPairThreads] keeps the results live.
+int pair_ceiling_blocks_per_sm(int d);
+cudaError_t launch_pair_ceiling(const PairArgs &a, int d, bool far, int grid, int iters, float *sink, cudaStream_t s);
+
 constexpr int kTreeMaxCluster = 8;  // CTAs per tree (portable cluster size)
 cudaError_t launch_tree_prior(const TreeArgs &a, int d, cudaStream_t s);
 

@@ -197,6 +197,13 @@ class MDS:
         self._check(self._lib.mds_tree_prior(self._h, ctypes.byref(lp), ptr, dt, where))
         return lp.value, out
 
+    def pair_body_ceiling(self, far=False):
+        """Pairs/s of the FP32C pass's per-pair body with its operands in
+        registers (far: the body without the Phi terms); mds_pair_body_ceiling."""
+        v = ctypes.c_double()
+        self._check(self._lib.mds_pair_body_ceiling(self._h, 1 if far else 0, ctypes.byref(v)))
+        return v.value
+
     def far_blocks(self):
         """(far, total) warp blocks of one evaluation pass (far: Phi terms skipped)."""
         f = ctypes.c_int64()
