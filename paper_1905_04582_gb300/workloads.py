@@ -219,6 +219,41 @@ def balanced_forest(levels, d=2, seed=0, tau0=1.0, tau_u=2.0):
     return Forest(n, parent, length, sigma_mat, mu, float(tau0), float(tau_u))
 
 
+def mixed_shape_forest(rng, d=2, tau0=1.0, tau_u=2.0):
+    """A forest of 1 to 7 trees (1 to 299 tips each) plus up to 4 unsequenced
+    items, whose trees join lineages in a random mix of three ways: a random
+    pair (coalescent-like), the newest node with a random lineage
+    (caterpillar-like), or the two newest (balanced-like).  rng: a numpy
+    Generator; branch lengths uniform in (0.05, 1.05); Sigma and mu from rng."""
+    sizes = [int(v) for v in rng.integers(1, 300, size=int(rng.integers(1, 8)))]
+    n_lone = int(rng.integers(0, 5))
+    n = sum(sizes) + n_lone
+    items = rng.permutation(n)
+    parent = [-1] * n
+    pos = 0
+    for size in sizes:
+        lin = [int(v) for v in items[pos:pos + size]]
+        pos += size
+        while len(lin) > 1:
+            mode = rng.integers(0, 3)
+            if mode == 0:
+                a, b = rng.choice(len(lin), size=2, replace=False)
+            elif mode == 1:
+                a, b = len(lin) - 1, int(rng.integers(0, len(lin) - 1))
+            else:
+                a, b = len(lin) - 1, len(lin) - 2
+            u, v = lin[a], lin[b]
+            node = len(parent)
+            parent.append(-1)
+            parent[u] = parent[v] = node
+            lin = [w for j, w in enumerate(lin) if j not in (a, b)] + [node]
+    parent = np.array(parent, dtype=np.int64)
+    length = 0.05 + rng.uniform(size=len(parent))
+    length[parent < 0] = 0.0
+    sigma_mat, mu = _sigma_mu(rng, d)
+    return Forest(n, parent, length, sigma_mat, mu, float(tau0), float(tau_u))
+
+
 def brownian_tips(forest, seed=0):
     """One draw of X (N x D) from the Brownian diffusion down the forest:
     roots ~ N(mu, tau0 Sigma), children ~ N(parent, length Sigma),

@@ -6,7 +6,8 @@ internal node and tip in exactly one part, child references and levels
 consistent, block roots exchanged with matching proxies, buffers in bounds.
 Shapes: coalescent forests up to the paper's four subtype trees, the deepest
 (caterpillar) and the shallowest (complete) binary trees, many small trees,
-unsequenced items."""
+unsequenced items, and 60 seeded forests that mix the three ways of joining
+lineages."""
 import numpy as np
 import pytest
 
@@ -82,3 +83,13 @@ def test_not_a_forest_is_rejected():
     with pytest.raises(MDSError) as e:
         tree_plan_check(f.n, f.parent, ln, 2)
     assert e.value.status == MDS_ERR_INVALID_ARG
+
+
+def test_random_shapes_and_sizes():
+    rng = np.random.default_rng(2024)
+    for _ in range(60):
+        f = W.mixed_shape_forest(rng)
+        n, parent, length = f.n, f.parent, f.length
+        d = int(rng.integers(1, 7))
+        st = tree_plan_check(n, parent, length, d)
+        assert st["parts"] == st["trees"] * st["cluster"]

@@ -83,6 +83,15 @@ def test_complete_tree_matches_oracle(prec):
     print("complete 2048", prec, check(f, x, prec, 1e-7))
 
 
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_random_shapes_match_oracle(seed):
+    # trees that mix random, caterpillar-like and balanced-like joins, cut
+    # into blocks and tops of uneven depth
+    f = W.mixed_shape_forest(np.random.default_rng(seed))
+    x = W.brownian_tips(f, seed=seed)
+    print("random shape", seed, f.n, check(f, x, "fp64", 1e-7))
+
+
 def test_only_unsequenced_items():
     f = W.random_forest((), n_lone=40, d=3, seed=9, tau_u=0.7)
     x = W.brownian_tips(f, seed=6)
