@@ -57,6 +57,9 @@ __global__ void __launch_bounds__(kPairThreads, 3) pair_batch_kernel(const __gri
         mbar_init(&bar_x[1], 1);
         fence_mbar_init();
     }
+    // under PDL the next kernel may become resident now; this one reads the
+    // chains' locations and writes their partials only after pdl_wait()
+    pdl_trigger();
     __syncthreads();
     uint32_t ph_y = 0, ph_x0 = 0, ph_x1 = 0;
     // copies issued by thread 0 and not yet waited for (for the drain on errors)
@@ -76,8 +79,11 @@ __global__ void __launch_bounds__(kPairThreads, 3) pair_batch_kernel(const __gri
         if (tid == 0) {
             fence_proxy_async();  // earlier generic reads of these buffers before the new copies
             mbar_expect_tx(bar_y, nst * kTileElems * 4);
-            tma_load_1d(ybuf, ds.y + t0 * kTileElems, nst * kTileElems * 4, bar_y);
+            tma_load_1d(ybuf, ds.y + t0 * kTileElems, nst * kTileElems * 4, bar_y);  // Y is constant
             pend_y = true;
+        }
+        pdl_wait();  // returns at once after the first strip
+        if (tid == 0) {
             const BatchChain c0 = a.ch[ds.chain0];
             mbar_expect_tx(&bar_x[0], xbytes);
             tma_load_1d(smem + L.off_xj(0), c0.xcol + static_cast<int64_t>(st.j0) * kTile * D, xbytes, &bar_x[0]);
@@ -202,15 +208,16 @@ int pair_batch_blocks_per_sm(int d, int strip_cap) {
 cudaError_t launch_pair_batch(const BatchPairArgs &a, int d, int grid, cudaStream_t s) {
     if (a.n_strips <= 0 || grid <= 0) return cudaSuccess;
     const size_t bytes = pair_batch_smem(d, a.strip_cap);
+    cudaError_t e = cudaSuccess;
     switch (d) {
 #define MDS_PB_CASE(DD) \
-    case DD: pair_batch_kernel<DD><<<grid, kPairThreads, bytes, s>>>(a); break;
+    case DD: e = launch_pdl(pair_batch_kernel<DD>, dim3(grid), dim3(kPairThreads), bytes, s, a); break;
         MDS_PB_CASE(1) MDS_PB_CASE(2) MDS_PB_CASE(3) MDS_PB_CASE(4)
         MDS_PB_CASE(5) MDS_PB_CASE(6) MDS_PB_CASE(7) MDS_PB_CASE(8)
 #undef MDS_PB_CASE
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace mds

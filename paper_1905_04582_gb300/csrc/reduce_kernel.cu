@@ -914,8 +914,17 @@ cudaError_t launch_traj_end(const AcceptArgs &a, cudaStream_t s) {
 
 cudaError_t launch_reduce_batch(const ReduceArgs *cfg, const int2 *jobs, int n_jobs, int d, int mode, cudaStream_t s) {
     if (n_jobs <= 0) return cudaSuccess;
-    MDS_SWITCH_DB(reduce_batch_kernel, n_jobs, kRedThreads, s, d, cfg, jobs, mode)
-    return cudaGetLastError();
+    // under PDL after the batched pass (reduce_body waits for it)
+    cudaError_t e = cudaSuccess;
+    switch (d) {
+#define MDS_RB_CASE(DD) \
+    case DD: e = launch_pdl(reduce_batch_kernel<DD>, dim3(n_jobs), dim3(kRedThreads), 0, s, cfg, jobs, mode); break;
+        MDS_RB_CASE(1) MDS_RB_CASE(2) MDS_RB_CASE(3) MDS_RB_CASE(4)
+        MDS_RB_CASE(5) MDS_RB_CASE(6) MDS_RB_CASE(7) MDS_RB_CASE(8)
+#undef MDS_RB_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int traj_start_grid(int64_t n, int d) { return static_cast<int>(((n * d + 3) / 4 + kTrajThreads - 1) / kTrajThreads); }
