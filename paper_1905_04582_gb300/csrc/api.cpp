@@ -1027,7 +1027,7 @@ int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out
     e = cudaGetDeviceProperties(&prop, dev);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
     if (prop.major != 10)
-        return fail(c, MDS_ERR_UNSUPPORTED, "device %s is compute capability %d.%d; this build needs sm_103a",
+        return fail(c, MDS_ERR_UNSUPPORTED, "device %s is compute capability %d.%d; the library is compiled for sm_103a",
                     prop.name, prop.major, prop.minor);
     c = new (std::nothrow) mds_ctx();
     if (!c) return fail(nullptr, MDS_ERR_OOM, "host allocation failed");
