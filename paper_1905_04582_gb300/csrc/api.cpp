@@ -137,6 +137,7 @@ struct mds_ctx {
     double *tree_grad0 = nullptr;         // its gradient at the trajectory start (restored on reject)
     cudaStream_t tree_stream = nullptr;   // the traversal runs here, beside the pair pass
     cudaEvent_t tree_fork = nullptr, tree_join = nullptr;
+    int tree_pass_smem = 0;               // > 0: the pass's padded shared memory beside the traversal
     int64_t rw_iter = 0;                  // random-walk proposals drawn so far (Philox counter)
     std::vector<void *> tree_bufs;        // its device allocations
 
@@ -439,6 +440,11 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.p = c->p;
     r.energy_part = c->e_end;
     r.prior_grad = c->tree_on ? c->tree.grad : nullptr;
+    if (c->tree_on) {
+        r.tree_part = c->tree.part;
+        r.n_tree_parts = (c->tree.n_trees + (c->tree.n_lone > 0 ? 1 : 0)) * c->tree.cluster;
+        r.tree_const = c->tree.const_term;
+    }
     r.err = c->err;
     return r;
 }
@@ -487,19 +493,23 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_na
         TreeArgs ta = c->tree;
         ta.x = c->x;
         ta.x_f64 = c->fp64;
-        ta.out = c->scal + kPriorLogp;
+        ta.out = nullptr;  // the reduction's scalar CTA adds the parts when it needs log p
         e = cudaEventRecord(c->tree_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->tree_stream, c->tree_fork, 0);
         if (e == cudaSuccess) e = launch_tree_prior(ta, c->d, c->tree_stream);
         if (e == cudaSuccess) e = cudaEventRecord(c->tree_join, c->tree_stream);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "tree prior launch: %s", cudaGetErrorString(e));
     }
-    // with a tree prior the pass is launched without PDL: it then becomes
-    // eligible when the traversal does, as the reduction completes, and the
-    // traversal's high-priority clusters are placed while SMs are free
-    // (launched early by PDL, the pass's CTAs would hold every SM)
-    const bool pdl = !c->tree_on;
-    e = c->fp64 ? launch_pair_pass_f64(a, c->d, s, pdl) : launch_pair_pass_f32(a, c->d, s, pdl);
+    // With a tree prior, launched early by PDL the pass's CTAs would hold
+    // every SM before the traversal's clusters could be placed.  So either
+    // the FP32C pass keeps PDL with its shared memory padded to leave room
+    // for one traversal CTA beside three pass CTAs on every SM (tree_pass_smem,
+    // chosen when the tree prior is set), or it is launched without PDL and
+    // becomes eligible when the traversal does.
+    const bool capped = c->tree_on && !c->fp64 && c->tree_pass_smem > 0;
+    const bool pdl = !c->tree_on || capped;
+    e = c->fp64 ? launch_pair_pass_f64(a, c->d, s, pdl)
+                : launch_pair_pass_f32(a, c->d, s, pdl, capped ? c->tree_pass_smem : 0);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
     if (c->tree_on) {
         e = cudaStreamWaitEvent(s, c->tree_join, 0);
@@ -1925,13 +1935,23 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
     CHECK(up(&p, nullptr, static_cast<size_t>(c->n_pad) * d * sizeof(double)));
     c->tree_grad0 = static_cast<double *>(p);
     const size_t grid = (roots.size() + (lone.empty() ? 0 : 1)) * static_cast<size_t>(ncl);
-    CHECK(up(&p, nullptr, (grid + 2) * sizeof(double)));
+    CHECK(up(&p, nullptr, (grid + 1) * sizeof(double)));
     ta.part = static_cast<double *>(p);
     ta.out = ta.part + grid;
-    ta.done = reinterpret_cast<unsigned *>(ta.part + grid + 1);
-    CU(cudaMemsetAsync(ta.done, 0, sizeof(unsigned), c->stream));
     CU(cudaMemsetAsync(ta.grad, 0, static_cast<size_t>(c->n_pad) * d * sizeof(double), c->stream));
     CU(cudaStreamSynchronize(c->stream));
+    // room for one traversal CTA beside three pass CTAs on every SM: the
+    // pass's shared memory padded so that a fourth does not fit
+    c->tree_pass_smem = 0;
+    {
+        int smem_sm = 0, reserved = 0;
+        CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
+        CU(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, c->device));
+        const int tree_cta = ta.smem_bytes + 1024 + reserved;  // dynamic + static (< 1 KB) + reserved
+        const int pad = (smem_sm - tree_cta) / 3 - reserved;
+        const int base = pair_f32_smem_bytes(d);
+        if (!c->fp64 && base > 0 && pad >= base && 4 * (pad + reserved) > smem_sm) c->tree_pass_smem = pad;
+    }
     ta.n = n;
     ta.n_trees = static_cast<int32_t>(roots.size());
     ta.cluster = ncl;

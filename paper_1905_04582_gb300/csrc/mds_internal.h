@@ -190,7 +190,10 @@ cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s);
 // pdl: launch with programmatic dependent launch (the kernel may become
 // resident while the previous one drains); off when a concurrent kernel on
 // another stream should get SMs first.
-cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true);
+// smem_min: dynamic shared memory of each CTA at least this (the layout's
+// size otherwise): more only to cap the pass's CTAs per SM.
+cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true, int smem_min = 0);
+int pair_f32_smem_bytes(int d);
 cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s, bool pdl = true);
 
 // ---------------------------------------------------------------------------
@@ -264,6 +267,9 @@ struct ReduceArgs {
     void *p;                  // [N][D]
     double *energy_part;      // [nt * kReduceQuarters][2] (kModeHalfKick): kinetic, ||x||^2
     const double *prior_grad; // [N][D] d log p / dX of the tree prior at x (added to the kicks), or null
+    const double *tree_part;  // the tree prior's per-CTA sums (or null); with tree_const, summed into
+    int32_t n_tree_parts;     //   scal[kPriorLogp] by the scalar CTA (evaluations, a trajectory's end)
+    double tree_const;
     unsigned *err;
 };
 
@@ -402,9 +408,21 @@ struct TreeArgs {
     double *scratch;         // otherwise: per part (2 m + 2 k) x D + k doubles at scr_off
     double *grad;            // [N][D] d log p / dX (out)
     double *part;            // [grid] per-CTA sums (scratch)
-    unsigned *done;          // CTAs finished (0 between launches; the last one resets it)
-    double *out;             // log p (out, device scalar)
+    double *out;             // log p (device scalar): the sum of part and const_term, written by a
+                             // one-warp kernel after the traversal when not null
 };
+
+// log p of the tree prior from its per-CTA sums: const_term plus the parts
+// in a fixed order (lane-strided sums, then a butterfly).  Called by all 32
+// lanes of one warp; every lane returns the total.
+__device__ inline double tree_parts_sum(const double *part, int n, double const_term) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += part[i];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return const_term + s;
+}
 // Measured ceiling of the pass's per-pair arithmetic (ceiling.cu): grid
 // CTAs of kPairThreads threads, each thread `iters` rounds of 16 pairs (four
 // row pairs against two columns, two pairs per call) with every operand in

@@ -356,21 +356,22 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
 }
 
 template <int D>
-cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s, bool pdl) {
+cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s, bool pdl, int smem_min) {
     using L = F32Layout<D>;
-    static bool attr_set = false;  // per instantiation pair, set once per process
-    if (!attr_set) {
+    const int smem = smem_min > L::kBytes ? smem_min : L::kBytes;  // more only to cap the CTAs per SM
+    static int attr_bytes = 0;  // per instantiation pair, raised as needed
+    if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(pair_f32_kernel<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             L::kBytes);
+                                             smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pair_f32_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+            e = cudaFuncSetAttribute(pair_f32_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_bytes = smem;
     }
     if (a.n_strips <= 0) return cudaSuccess;
     const cudaError_t e =
-        a.tile_ho ? launch_maybe_pdl(pdl, pair_f32_kernel<D, true>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a)
-                  : launch_maybe_pdl(pdl, pair_f32_kernel<D, false>, dim3(a.n_strips), dim3(kPairThreads), L::kBytes, s, a);
+        a.tile_ho ? launch_maybe_pdl(pdl, pair_f32_kernel<D, true>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a)
+                  : launch_maybe_pdl(pdl, pair_f32_kernel<D, false>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -400,16 +401,30 @@ cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl) {
+int pair_f32_smem_bytes(int d) {
     switch (d) {
-        case 1: return launch_f32_d<1>(a, s, pdl);
-        case 2: return launch_f32_d<2>(a, s, pdl);
-        case 3: return launch_f32_d<3>(a, s, pdl);
-        case 4: return launch_f32_d<4>(a, s, pdl);
-        case 5: return launch_f32_d<5>(a, s, pdl);
-        case 6: return launch_f32_d<6>(a, s, pdl);
-        case 7: return launch_f32_d<7>(a, s, pdl);
-        case 8: return launch_f32_d<8>(a, s, pdl);
+        case 1: return F32Layout<1>::kBytes;
+        case 2: return F32Layout<2>::kBytes;
+        case 3: return F32Layout<3>::kBytes;
+        case 4: return F32Layout<4>::kBytes;
+        case 5: return F32Layout<5>::kBytes;
+        case 6: return F32Layout<6>::kBytes;
+        case 7: return F32Layout<7>::kBytes;
+        case 8: return F32Layout<8>::kBytes;
+        default: return 0;
+    }
+}
+
+cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl, int smem_min) {
+    switch (d) {
+        case 1: return launch_f32_d<1>(a, s, pdl, smem_min);
+        case 2: return launch_f32_d<2>(a, s, pdl, smem_min);
+        case 3: return launch_f32_d<3>(a, s, pdl, smem_min);
+        case 4: return launch_f32_d<4>(a, s, pdl, smem_min);
+        case 5: return launch_f32_d<5>(a, s, pdl, smem_min);
+        case 6: return launch_f32_d<6>(a, s, pdl, smem_min);
+        case 7: return launch_f32_d<7>(a, s, pdl, smem_min);
+        case 8: return launch_f32_d<8>(a, s, pdl, smem_min);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -241,6 +241,15 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             dmd = block_sum_d<kRedThreads>(md, sm);
             dlp = block_sum_d<kRedThreads>(lp, sm);
         }
+        if (a.tree_part && tid < 32) {
+            // the tree prior's log density at this x (its traversal ran
+            // beside the pass and completed before this kernel)
+            const double lp = tree_parts_sum(a.tree_part, a.n_tree_parts, a.tree_const);
+            if (tid == 0) {
+                a.scal[kPriorLogp] = lp;
+                if (!isfinite(lp)) atomicOr(a.err, kErrNonfinite);
+            }
+        }
         if (tid == 0) {
             // log sigma and 1 / sigma come from the host: FP64 log and
             // division are long dependency chains on this GPU

@@ -36,8 +36,9 @@
 // are as many as its height however it is cut; the cut spreads the wide
 // levels and the contrast and gradient sweeps (FP64-throughput bound) over
 // the cluster.  Unsequenced items (tips that are roots, variance tau_u) go to
-// one more cluster.  FP64 throughout; every sum has a fixed order, so
-// results are deterministic.
+// one more cluster.  Each CTA leaves its sum of the contrast terms; the
+// consumer adds them (tree_parts_sum).  FP64 throughout; every sum has a
+// fixed order, so results are deterministic.
 #include <cstdint>
 
 #include "mds_internal.h"
@@ -375,27 +376,14 @@ __global__ void __launch_bounds__(kTreeThreads, 1) tree_prior_kernel(const __gri
             acc = fma(-0.5 * g, qf, acc);
         }
     }
-    // the CTA's sum; the last CTA to finish adds all of them (fixed order)
-    // and the constant (log-determinant) terms, and re-arms the counter
-    __shared__ unsigned s_last;
+    // the CTA's sum (the consumers add the parts: tree_parts_sum)
     const double tot = block_sum(acc, sm);
-    if (tid == 0) {
-        __stcg(a.part + blockIdx.x, tot);
-        __threadfence();
-        s_last = atomicAdd(a.done, 1u) == gridDim.x - 1 ? 1u : 0u;
-    }
-    __syncthreads();
-    if (s_last && tid < 32) {
-        __threadfence();
-        double s = 0.0;
-        for (int i = tid; i < static_cast<int>(gridDim.x); i += 32) s += __ldcg(a.part + i);
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (tid == 0) {
-            *a.out = a.const_term + s;
-            *a.done = 0u;
-        }
-    }
+    if (tid == 0) a.part[blockIdx.x] = tot;
+}
+
+__global__ void tree_prior_sum_kernel(const double *part, int n, double const_term, double *out) {
+    const double v = tree_parts_sum(part, n, const_term);
+    if (threadIdx.x == 0) *out = v;
 }
 
 template <int D, typename T>
@@ -432,7 +420,10 @@ template <int D>
 cudaError_t launch_d(const TreeArgs &a, cudaStream_t s) {
     const int grid = (a.n_trees + (a.n_lone > 0 ? 1 : 0)) * a.cluster;
     if (grid <= 0) return cudaErrorInvalidValue;
-    return a.x_f64 ? launch_t<D, double>(a, grid, s) : launch_t<D, float>(a, grid, s);
+    const cudaError_t e = a.x_f64 ? launch_t<D, double>(a, grid, s) : launch_t<D, float>(a, grid, s);
+    if (e != cudaSuccess || !a.out) return e;
+    tree_prior_sum_kernel<<<1, 32, 0, s>>>(a.part, grid, a.const_term, a.out);
+    return cudaGetLastError();
 }
 
 }  // namespace
