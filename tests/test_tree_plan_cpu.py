@@ -93,3 +93,17 @@ def test_random_shapes_and_sizes():
         d = int(rng.integers(1, 7))
         st = tree_plan_check(n, parent, length, d)
         assert st["parts"] == st["trees"] * st["cluster"]
+
+
+def test_argument_checks():
+    from paper_1905_04582_gb300 import capi
+    f = W.random_forest((5, 4), n_lone=1, d=2, seed=4)
+    for d in (0, 9):
+        with pytest.raises(MDSError) as e:
+            tree_plan_check(f.n, f.parent, f.length, d)
+        assert e.value.status == MDS_ERR_INVALID_ARG
+    st = capi.lib().mds_tree_plan_check(f.n, len(f.parent), None, None, 2, None)
+    assert st == MDS_ERR_INVALID_ARG
+    with pytest.raises(MDSError) as e:  # fewer nodes than tips
+        tree_plan_check(f.n, f.parent[:f.n - 1], f.length[:f.n - 1], 2)
+    assert e.value.status == MDS_ERR_INVALID_ARG
