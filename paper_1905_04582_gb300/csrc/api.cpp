@@ -1950,7 +1950,10 @@ int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const
         const int tree_cta = ta.smem_bytes + 1024 + reserved;  // dynamic + static (< 1 KB) + reserved
         const int pad = (smem_sm - tree_cta) / 3 - reserved;
         const int base = pair_f32_smem_bytes(d);
-        if (!c->fp64 && base > 0 && pad >= base && 4 * (pad + reserved) > smem_sm) c->tree_pass_smem = pad;
+        // measured at D = 2, where the pass's registers allow 4 CTAs per SM and
+        // 3 of them leave room for a traversal CTA's registers too; for
+        // larger D the pass's register use leaves none, so it runs without PDL
+        if (!c->fp64 && d <= 2 && base > 0 && pad >= base && 4 * (pad + reserved) > smem_sm) c->tree_pass_smem = pad;
     }
     ta.n = n;
     ta.n_trees = static_cast<int32_t>(roots.size());
