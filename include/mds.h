@@ -172,7 +172,7 @@ typedef struct mds_hmc_stats {
 int mds_hmc(mds_ctx *ctx, int n_iter, int n_steps, double eps, uint64_t seed, const double *p_all,
             const double *u_all, int *accepted, double *dh, mds_hmc_stats *stats);
 
-/* Asynchronous HMC (Algorithm 1 of arXiv:1905.04582, as mds_hmc, Philox
+/* Asynchronous HMC (section 2.3 of arXiv:1905.04582, Eq. (6)-(8), as mds_hmc, Philox
  * momenta only): queue n_iter iterations on the context's stream and return
  * without waiting for the device.  The chain state stays on the device; the
  * per-iteration decisions and H1 - H0 accumulate there (moved to the host
@@ -489,7 +489,10 @@ const char *mds_batch_last_error(const mds_batch *b);
  * the caller.  Nothing in it needs clearing: every slot a call reads is
  * written earlier in the same call.  The first call on each device looks up
  * the scratch's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Each pair is
+ * current and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not use this entry point on a device
+ * after cudaDeviceReset there (the kept address would belong to the
+ * destroyed context).  Each pair is
  * evaluated twice in FP64 (once per row), so this call is slower than the
  * context path. */
 int mds_loglik_grad_noalloc(int64_t n, int32_t d, const float *y, int64_t ld, const double *x, double sigma,

@@ -549,6 +549,13 @@ __host__ __device__ inline bool choose_split(float m, int d, Split &sp) {
     return true;
 }
 
+// Raise the dynamic shared memory limit of `func` to at least `bytes` on the
+// current device.  The attribute belongs to the device's context, so the
+// largest value set so far is cached per (kernel, device ordinal) under a
+// mutex: a second device gets its own call, and concurrent host threads do
+// not race on the cache (defined in pair_kernel.cu).
+cudaError_t raise_dyn_smem(const void *func, int bytes);
+
 // Programmatic dependent launch.  The pair pass and the reduction alternate
 // 2 L times per trajectory; launched with launch_pdl, a kernel may become
 // resident while the previous kernel of the stream is still draining, runs

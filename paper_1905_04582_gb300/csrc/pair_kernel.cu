@@ -36,7 +36,10 @@
 // log1p / exp per pair and FP64 sums (the plain FP64 GPU path).
 #include <cfloat>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "mds_internal.h"
 #include "pair_math.cuh"
@@ -359,14 +362,10 @@ template <int D>
 cudaError_t launch_f32_d(const PairArgs &a, cudaStream_t s, bool pdl, int smem_min) {
     using L = F32Layout<D>;
     const int smem = smem_min > L::kBytes ? smem_min : L::kBytes;  // more only to cap the CTAs per SM
-    static int attr_bytes = 0;  // per instantiation pair, raised as needed
-    if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(pair_f32_kernel<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pair_f32_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    {
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(pair_f32_kernel<D, false>), smem);
+        if (e == cudaSuccess) e = raise_dyn_smem(reinterpret_cast<const void *>(pair_f32_kernel<D, true>), smem);
         if (e != cudaSuccess) return e;
-        attr_bytes = smem;
     }
     if (a.n_strips <= 0) return cudaSuccess;
     const cudaError_t e =
@@ -395,6 +394,20 @@ __global__ void wait_probe_kernel(unsigned *err) {
 }
 
 }  // namespace
+
+cudaError_t raise_dyn_smem(const void *func, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> set;  // (kernel, device) -> bytes set so far
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    int &cur = set[std::make_pair(func, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s) {
     wait_probe_kernel<<<1, 32, 0, s>>>(err);

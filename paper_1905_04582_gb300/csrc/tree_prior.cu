@@ -388,12 +388,9 @@ __global__ void tree_prior_sum_kernel(const double *part, int n, double const_te
 
 template <int D, typename T>
 cudaError_t launch_t(const TreeArgs &a, int grid, cudaStream_t s) {
-    static int attr_bytes = 0;  // per instantiation, raised once as needed
-    if (a.smem_bytes > attr_bytes) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(tree_prior_kernel<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
+    {
+        const cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(tree_prior_kernel<D, T>), a.smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_bytes = a.smem_bytes;
     }
     // one cluster per tree, at the highest stream priority, so that its CTAs
     // get SMs ahead of a concurrent pair pass's pending CTAs

@@ -18,7 +18,10 @@ gradient coordinate also passes when
       FP64): the size of the rounding error that any evaluation of the
       per-pair terms with a few units in the last place each leaves in their
       sum (random-walk model).
-Coordinates that pass only through (a) or (b) are counted and reported.
+Coordinates that pass only through (a) or (b) are counted and reported, and
+they must stay rare: at most ESCAPE_FRAC (0.1%) of the coordinates, and at
+least one allowed on small cases (a regression that pushed many coordinates
+into the escape branches fails even when each of them is within (a) or (b)).
 """
 import numpy as np
 
@@ -28,6 +31,11 @@ TOL = {
 }
 KAPPA = 1e3
 ULPS = 8.0
+ESCAPE_FRAC = 1e-3
+
+
+def escape_cap(n):
+    return max(1, int(ESCAPE_FRAC * n))
 
 
 def grad_check(g, g_ref, s_abs, tol, what="gradient", s_sq=None, u=None):
@@ -55,6 +63,9 @@ def grad_check(g, g_ref, s_abs, tol, what="gradient", s_sq=None, u=None):
     assert bad.size == 0, (f"{what}: {len(bad)} of {g.size} coordinates out of tolerance {tol}; first "
                            f"{bad[:5].tolist()}: got {g[tuple(bad[0])]}, ref {g_ref[tuple(bad[0])]}, "
                            f"kappa {kappa[tuple(bad[0])]:.3g}; {info}")
+    n_escape = info["n_kappa_branch"] + info["n_rounding_branch"]
+    assert n_escape <= escape_cap(g.size), (f"{what}: {n_escape} of {g.size} coordinates passed only through "
+                                            f"the cancellation or rounding branch (cap {escape_cap(g.size)}); {info}")
     return info
 
 

@@ -49,7 +49,7 @@ def test_leapfrog_matches_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32c", "fp64"])
-@pytest.mark.parametrize("eps", [1e-3, 1.5e-2])
+@pytest.mark.parametrize("eps", [1e-3, 1.5e-2, 3.5e-2])
 def test_hmc_injected_draws_match_oracle(prec, eps):
     wl = W.small()
     n_iter, n_steps = 10, 10
@@ -69,8 +69,12 @@ def test_hmc_injected_draws_match_oracle(prec, eps):
         assert acc[t] == acc_r[t], (t, dh[t], dh_r[t], u_all[t])
     assert stats["accepted"] == int(acc_r.sum())
     np.testing.assert_allclose(x, xr, rtol=0, atol=(2e-5 if prec == "fp32c" else 1e-11) * (1 + np.abs(xr).max()))
-    if eps > 1e-2:
-        assert 0 < acc_r.sum() < n_iter or True  # informative: both branches usually occur
+    if eps > 3e-2:
+        # with these draws the larger step accepts 7 and rejects 3 proposals
+        # (smallest |log u + H1 - H0| = 0.39): both branches of the
+        # Metropolis step (Eq. (8)) are exercised and agree with the oracle
+        assert 0 < acc_r.sum() < n_iter, acc_r
+        assert 0 < int(np.sum(acc)) < n_iter, acc
 
 
 @pytest.mark.parametrize("prec", ["fp32c", "fp64"])
