@@ -409,6 +409,39 @@ int mds_problem_size(const mds_ctx *ctx, int64_t *pairs, int64_t *y_bytes);
 int mds_set_strip(mds_ctx *ctx, int32_t strip);
 int mds_get_strip(const mds_ctx *ctx, int32_t *strip);
 
+/* Shape of the FP32C pair pass (section 2.5 of arXiv:1905.04582: the
+ * pairwise transformation split into work units and the partial sums reduced;
+ * the paper fixes its work-group shapes, this library picks one by timing).
+ * kind MDS_PASS_STRIPS: one CTA per strip of `param` tiles of a row block;
+ * kind MDS_PASS_CHUNKS: the tiles cut into `param` x (resident CTA slots)
+ * chunks of equal estimated cost, one CTA each (the estimate uses the
+ * per-tile counts of pairs whose Phi terms were skipped in an earlier pass);
+ * kind MDS_PASS_CHUNK_COUNT: the same with exactly `param` chunks (at most
+ * one per tile; param >= 1).
+ * param 0 returns to the autotuner, which times the candidates once per
+ * (GPU name, N, D, precision, item order) and keeps the result in memory and
+ * in the file named by MDS_TUNE_CACHE (default: tune_cache.txt beside the
+ * library).  The FP64 context has the strip pass only (INVALID_ARG for
+ * chunks).  mds_get_pass_shape returns the kind, its param and the number of
+ * CTAs of the pass in use (any pointer may be NULL).  Changing the shape
+ * changes the summation order (results stay within tolerance). */
+#define MDS_PASS_STRIPS 0
+#define MDS_PASS_CHUNKS 1
+#define MDS_PASS_CHUNK_COUNT 2
+int mds_set_pass_shape(mds_ctx *ctx, int32_t kind, int32_t param);
+int mds_get_pass_shape(const mds_ctx *ctx, int32_t *kind, int32_t *param, int32_t *ctas);
+
+/* Span of the pair pass inside real work, without events between launches
+ * (benchmarks): while on, every pair-pass warp records %globaltimer after
+ * its dependency wait (earliest, atomic min) and at its end (latest, atomic
+ * max), and the reduction that follows adds end - start to a device total;
+ * this keeps programmatic dependent launch intact, so the span is the pass's
+ * time inside an HMC step.  mds_set_pass_stamps resets the total;
+ * mds_get_pass_span synchronises the stream and returns the number of
+ * passes and their total milliseconds since then. */
+int mds_set_pass_stamps(mds_ctx *ctx, int on);
+int mds_get_pass_span(mds_ctx *ctx, int64_t *passes, double *total_ms);
+
 /* Time the fused pass: run `reps` evaluations back to back on the context's
  * stream and return the mean milliseconds per pass (CUDA events). */
 int mds_time_pass(mds_ctx *ctx, int reps, double *ms_per_pass);

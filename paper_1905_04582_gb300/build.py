@@ -21,7 +21,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libmds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["pair_kernel.cu", "batch_kernel.cu", "reduce_kernel.cu", "heldout.cu", "noalloc.cu", "tree_prior.cu", "rwmh.cu", "ceiling.cu", "tree_plan.cpp", "api.cpp"]
+SOURCES = ["pair_kernel.cu", "chunk_kernel.cu", "batch_kernel.cu", "reduce_kernel.cu", "heldout.cu", "noalloc.cu", "tree_prior.cu", "rwmh.cu", "ceiling.cu", "tree_plan.cpp", "api.cpp"]
 HEADERS = ["mds_internal.h", "mills_ratio_coeffs.h", "pair_math.cuh", "philox.cuh", "tree_plan.h"]
 
 

@@ -32,6 +32,9 @@ MDS_DEVICE = 1
 MDS_Y_FULL = 0
 MDS_Y_PACKED_UPPER = 1
 MDS_MAX_D = 8
+MDS_PASS_STRIPS = 0
+MDS_PASS_CHUNKS = 1
+MDS_PASS_CHUNK_COUNT = 2
 
 STATUS_NAMES = {
     0: "MDS_OK", 1: "MDS_ERR_INVALID_ARG", 2: "MDS_ERR_STATE", 3: "MDS_ERR_CUDA", 4: "MDS_ERR_OOM",
@@ -95,6 +98,10 @@ SIGNATURES = {
     "mds_set_state": (_int, [_vp, _vp, _i64]),
     "mds_set_strip": (_int, [_vp, _i32]),
     "mds_get_strip": (_int, [_vp, _pi32]),
+    "mds_set_pass_shape": (_int, [_vp, _i32, _i32]),
+    "mds_get_pass_shape": (_int, [_vp, _pi32, _pi32, _pi32]),
+    "mds_set_pass_stamps": (_int, [_vp, _int]),
+    "mds_get_pass_span": (_int, [_vp, _pi64, _pdbl]),
     "mds_time_pass": (_int, [_vp, _int, _pdbl]),
     "mds_set_profiling": (_int, [_vp, _int]),
     "mds_get_pass_time": (_int, [_vp, _pi64, _pdbl]),

@@ -4,6 +4,8 @@
 #include "mds.h"
 
 #include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
@@ -27,6 +29,10 @@ namespace {
 
 thread_local std::string g_create_error = "no error";
 
+// Shapes of the FP32C pair pass (mds_ctx::pass_kind).
+constexpr int kPassStrips = 0;
+constexpr int kPassChunks = 1;
+
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -44,10 +50,25 @@ struct mds_ctx {
     int64_t nt = 0;
     int64_t n_pad = 0;
     int64_t tiles = 0;
-    int32_t strip = 0;        // in use
+    int32_t strip = 0;        // in use (strip pass)
     int32_t strip_req = 0;    // 0 = autotune
-    int32_t n_strips = 0;
+    int32_t n_strips = 0;     // CTAs of the pair pass (strips, or chunks of the chunked pass)
+    int32_t n_scal_parts = 0; // scalar partial records the pass writes
     int32_t n_row_slots = 0;
+    // the FP32C pass's shape: kPassStrips (one CTA per strip of `strip` tiles)
+    // or kPassChunks (one CTA per chunk, chunk_mult chunks per resident CTA slot)
+    int32_t pass_kind = 0;
+    int32_t chunk_mult = 0;       // in use (chunked pass)
+    int32_t chunk_req = 0;        // > 0: chunked pass forced with this multiple
+    Chunk *chunks = nullptr;
+    size_t chunks_bytes = 0;
+    std::vector<Chunk> chunks_host;
+    unsigned char *far_tile = nullptr;       // [tiles][4] far column pairs of the last chunked pass
+    std::vector<float> tile_cost;            // cost model of the chunking (empty: uniform)
+    float2 *xcol2 = nullptr;                 // FP32C column layout of the chunked pass
+    bool stamping = false;                   // pass spans measured with %globaltimer
+    unsigned long long *stamps = nullptr;    // [2]
+    double *pass_ns = nullptr;               // [2]: total ns, passes
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -216,6 +237,7 @@ XState xstate(const mds_ctx *c) {
     xs.x = c->x;
     xs.xrow = c->xrow;
     xs.xcol = c->xcol;
+    xs.xcol2 = c->xcol2;
     xs.split = c->split;
     xs.xmax_bits = c->xmax_bits;
     xs.inv = c->reordered ? c->inv_d : nullptr;
@@ -252,6 +274,8 @@ int check_device_err(mds_ctx *c, const char *what) {
 
 // ---------------------------------------------------------------- strips
 
+int ensure_part_buffers(mds_ctx *c, size_t row_slots, size_t scal_parts, size_t far_parts);
+
 int build_strips(mds_ctx *c, int strip) {
     const int64_t nt = c->nt;
     std::vector<Strip> v;
@@ -284,35 +308,154 @@ int build_strips(mds_ctx *c, int strip) {
         CHECK(dev_alloc_t(c, &c->strips, sb));
         c->strips_bytes = sb;
     }
-    const size_t rb = static_cast<size_t>(slot) * kTile * c->d * elem(c);
-    if (rb > c->row_part_bytes) {
-        dev_free(c->row_part);
-        c->row_part = nullptr;
-        CHECK(dev_alloc_t(c, &c->row_part, rb));
-        c->row_part_bytes = rb;
-    }
-    const size_t fpb = v.size() * kPairWarps * sizeof(int32_t);
-    if (fpb > c->far_part_bytes) {
-        dev_free(c->far_part);
-        c->far_part = nullptr;
-        CHECK(dev_alloc_t(c, &c->far_part, fpb));
-        c->far_part_bytes = fpb;
-    }
-    const size_t spb = v.size() * kScalarParts * elem(c);
-    if (spb > c->scal_part_bytes) {
-        dev_free(c->scal_part);
-        c->scal_part = nullptr;
-        CHECK(dev_alloc_t(c, &c->scal_part, spb));
-        c->scal_part_bytes = spb;
-    }
+    CHECK(ensure_part_buffers(c, static_cast<size_t>(slot), v.size(), v.size() * kPairWarps));
     c->strips_host = v;
     CU(cudaMemcpyAsync(c->strips, v.data(), sb, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->row_first, first.data(), (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     c->n_strips = static_cast<int32_t>(v.size());
+    c->n_scal_parts = c->n_strips;
     c->n_row_slots = slot;
     c->strip = strip;
+    c->pass_kind = kPassStrips;
+    c->chunk_mult = 0;
     c->gen++;
+    return MDS_OK;
+}
+
+int ensure_part_buffers(mds_ctx *c, size_t row_slots, size_t scal_parts, size_t far_parts) {
+    const size_t rb = row_slots * kTile * c->d * elem(c);
+    if (rb > c->row_part_bytes) {
+        dev_free(c->row_part);
+        c->row_part = nullptr;
+        c->row_part_bytes = 0;
+        CHECK(dev_alloc(c, &c->row_part, rb));
+        c->row_part_bytes = rb;
+    }
+    const size_t spb = scal_parts * kScalarParts * elem(c);
+    if (spb > c->scal_part_bytes) {
+        dev_free(c->scal_part);
+        c->scal_part = nullptr;
+        c->scal_part_bytes = 0;
+        CHECK(dev_alloc(c, &c->scal_part, spb));
+        c->scal_part_bytes = spb;
+    }
+    const size_t fpb = far_parts * sizeof(int32_t);
+    if (fpb > c->far_part_bytes) {
+        dev_free(c->far_part);
+        c->far_part = nullptr;
+        c->far_part_bytes = 0;
+        CHECK(dev_alloc_t(c, &c->far_part, fpb));
+        c->far_part_bytes = fpb;
+    }
+    return MDS_OK;
+}
+
+// Cost model of the chunking, in FP32 lane-operations per warp: a tile is 8
+// warp blocks (64 rows x 8 columns; a warp takes two), 16 pairs per lane
+// each, at 23 operations per pair for a far block (Phi terms skipped) and 36
+// for the others (chunk_kernel.cu), plus about 70 per tile (column
+// transposes, block tests, sums, the ring refill) and 150 where a row block
+// starts (row sums out, row buffer, row box).
+constexpr double kCostFar = 23.0, kCostNear = 36.0, kCostTile = 70.0, kCostSeg = 150.0;
+
+// The chunked pass's work list: the tiles, in row-block order, cut into
+// G = (SMs x resident CTAs of the pass) x mult chunks of equal estimated
+// cost (c->tile_cost from the far counts of an earlier chunked pass, else
+// every block counted near), one CTA each.
+int build_chunks(mds_ctx *c, int mult) {
+    const int64_t nt = c->nt, T = c->tiles;
+    int per_sm = pair_chunk_blocks_per_sm(c->d);
+    if (per_sm < 1) per_sm = 1;
+    // mult > 0: chunks per resident CTA slot; mult < 0: exactly -mult chunks
+    const int64_t want = mult > 0 ? static_cast<int64_t>(c->sm_count) * per_sm * mult : -static_cast<int64_t>(mult);
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(T, want));
+    const bool have_cost = static_cast<int64_t>(c->tile_cost.size()) == T;
+    std::vector<double> pre(static_cast<size_t>(T) + 1, 0.0);
+    {
+        int64_t t = 0;
+        for (int64_t I = 0; I < nt; ++I)
+            for (int64_t J = I; J < nt; ++J, ++t) {
+                double cst = have_cost ? c->tile_cost[t] : kCostTile + 4.0 * 8.0 * kCostNear;
+                if (J == I) cst += kCostSeg;
+                pre[t + 1] = pre[t] + cst;
+            }
+    }
+    const double total = pre[T];
+    std::vector<int64_t> cut(static_cast<size_t>(G) + 1, 0);
+    cut[G] = T;
+    for (int64_t g = 1; g < G; ++g) {
+        const double target = total * static_cast<double>(g) / static_cast<double>(G);
+        // first tile boundary whose prefix reaches the target
+        int64_t b = std::lower_bound(pre.begin(), pre.end(), target) - pre.begin();
+        if (b > 0 && target - pre[b - 1] < pre[b] - target) --b;
+        b = std::max(b, cut[g - 1] + 1);
+        b = std::min(b, T - (G - g));
+        cut[g] = b;
+    }
+    // blocks of every tile boundary, segments, the first segment of each row block
+    std::vector<Chunk> v(static_cast<size_t>(G));
+    std::vector<int32_t> first(nt + 1, -1);
+    int64_t t = 0, I = 0, J = 0;
+    int32_t seg = 0;
+    for (int64_t g = 0; g < G; ++g) {
+        while (t < cut[g]) {  // advance (I, J) to tile cut[g]
+            if (++J == nt) J = ++I;
+            ++t;
+        }
+        Chunk ch{};
+        ch.t0 = cut[g];
+        ch.t1 = cut[g + 1];
+        ch.I0 = static_cast<int32_t>(I);
+        ch.J0 = static_cast<int32_t>(J);
+        // row block of the last tile: the largest I with tile_index(I, I) <= t1 - 1
+        int64_t Il = I;
+        while (Il + 1 < nt && tile_index(Il + 1, Il + 1, nt) <= ch.t1 - 1) ++Il;
+        ch.I1 = static_cast<int32_t>(Il);
+        ch.seg0 = seg;
+        for (int64_t r = I; r <= Il; ++r)
+            if (first[r] < 0) first[r] = 4 * (seg + static_cast<int32_t>(r - I));
+        seg += static_cast<int32_t>(Il - I + 1);
+        v[g] = ch;
+    }
+    first[nt] = 4 * seg;
+    for (int64_t r = 0; r < nt; ++r)
+        if (first[r] < 0) return fail(c, MDS_ERR_STATE, "chunking left row block %lld without a segment", (long long)r);
+    CHECK(ensure_part_buffers(c, static_cast<size_t>(4) * seg, static_cast<size_t>(4 * G), static_cast<size_t>(4 * G)));
+    const size_t cb = v.size() * sizeof(Chunk);
+    if (cb > c->chunks_bytes) {
+        dev_free(c->chunks);
+        c->chunks = nullptr;
+        c->chunks_bytes = 0;
+        CHECK(dev_alloc_t(c, &c->chunks, cb));
+        c->chunks_bytes = cb;
+    }
+    c->chunks_host = v;
+    CU(cudaMemcpyAsync(c->chunks, v.data(), cb, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->row_first, first.data(), (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->n_strips = static_cast<int32_t>(G);
+    c->n_scal_parts = static_cast<int32_t>(4 * G);
+    c->n_row_slots = 4 * seg;
+    c->pass_kind = kPassChunks;
+    c->chunk_mult = mult;
+    c->strip = 0;
+    c->gen++;
+    return MDS_OK;
+}
+
+// Per-tile costs from the far counts of the last chunked pass.
+int read_tile_costs(mds_ctx *c) {
+    std::vector<unsigned char> f(static_cast<size_t>(c->tiles) * kPairWarps);
+    CU(cudaMemcpyAsync(f.data(), c->far_tile, f.size(), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->tile_cost.assign(static_cast<size_t>(c->tiles), 0.f);
+    for (int64_t t = 0; t < c->tiles; ++t) {
+        int far = 0;
+        for (int w = 0; w < kPairWarps; ++w) far += f[static_cast<size_t>(t) * kPairWarps + w];
+        far = std::min(far, 8);
+        c->tile_cost[t] = static_cast<float>(kCostTile + 4.0 * (far * kCostFar + (8 - far) * kCostNear));
+    }
     return MDS_OK;
 }
 
@@ -323,6 +466,13 @@ int build_strips(mds_ctx *c, int strip) {
 // scalar partials are summed in the new order).
 int order_strips_by_cost(mds_ctx *c) {
     if (c->fp64 || c->n_strips <= 0) return MDS_OK;
+    if (c->pass_kind == kPassChunks) {
+        // the chunked pass: cut the tiles again by the measured far counts
+        CHECK(read_tile_costs(c));
+        CHECK(build_chunks(c, c->chunk_mult));
+        c->grad_valid = false;
+        return MDS_OK;
+    }
     std::vector<int32_t> parts(static_cast<size_t>(c->n_strips) * kPairWarps);
     CU(cudaMemcpyAsync(parts.data(), c->far_part, parts.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -390,6 +540,12 @@ PairArgs pair_args(const mds_ctx *c) {
     a.perm = c->reordered ? c->perm_d : nullptr;
     a.far_part = c->far_part;
     a.err = c->err;
+    a.stamps = c->stamping ? c->stamps : nullptr;
+    if (!c->fp64 && c->pass_kind == kPassChunks) {
+        a.chunks = c->chunks;
+        a.xcol2 = c->xcol2;
+        a.far_tile = c->far_tile;
+    }
     const double s = c->sigma;
     // far warp blocks: every pair at z >= z_c (the squared-distance bound in
     // FP32; an overflow to +inf only turns the shortcut off)
@@ -409,6 +565,8 @@ PairArgs pair_args(const mds_ctx *c) {
     a.c_phi = make_float2(cphi, cphi);
     a.neg_inv_s2 = make_float2(nis2, nis2);
     a.m_coef = make_float2(mc, mc);
+    const float cm2 = static_cast<float>(-s * inv_sqrt_2pi);
+    a.c_m2 = make_float2(cm2, cm2);
     a.sigma = s;
     a.inv_sigma = 1.0 / s;
     a.inv_s2 = 1.0 / (s * s);
@@ -422,7 +580,10 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.scal_part = c->scal_part;
     r.row_first_slot = c->row_first;
     r.perm = c->reordered ? c->perm_d : nullptr;
-    r.n_strips = c->n_strips;
+    r.n_strips = c->n_scal_parts;
+    r.part_scale = (!c->fp64 && c->pass_kind == kPassChunks) ? -1.0 / (c->sigma * c->sigma) : 1.0;
+    r.stamps = c->stamping ? c->stamps : nullptr;
+    r.pass_ns = c->pass_ns;
     r.nt = static_cast<int32_t>(c->nt);
     r.n = c->n;
     r.d = c->d;
@@ -508,8 +669,12 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_na
     // becomes eligible when the traversal does.
     const bool capped = c->tree_on && !c->fp64 && c->tree_pass_smem > 0;
     const bool pdl = !c->tree_on || capped;
-    e = c->fp64 ? launch_pair_pass_f64(a, c->d, s, pdl)
-                : launch_pair_pass_f32(a, c->d, s, pdl, capped ? c->tree_pass_smem : 0);
+    if (c->fp64)
+        e = launch_pair_pass_f64(a, c->d, s, pdl);
+    else if (c->pass_kind == kPassChunks)
+        e = launch_pair_chunks_f32(a, c->d, s, pdl, capped ? c->tree_pass_smem : 0);
+    else
+        e = launch_pair_pass_f32(a, c->d, s, pdl, capped ? c->tree_pass_smem : 0);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
     if (c->tree_on) {
         e = cudaStreamWaitEvent(s, c->tree_join, 0);
@@ -540,60 +705,186 @@ int ready(mds_ctx *c) {
     return MDS_OK;
 }
 
-std::mutex g_tune_mu;
-std::map<std::tuple<std::string, int64_t, int, bool>, int> g_tune_cache;
+// ------------------------------------------------------------ autotuner
+//
+// The pass's shape (strip pass with S tiles per strip, or chunked pass with
+// m chunks per resident CTA slot) is chosen by timing candidates, once per
+// (GPU name, N, D, precision, item order).  The choice is kept in memory and
+// in a text file, so that later processes on the same machine reuse it: the
+// file named by MDS_TUNE_CACHE, else tune_cache.txt beside this library (one
+// line per key, tab-separated: GPU name, N, D, precision, order, kind, param,
+// milliseconds per pass).  MDS_STRIP or MDS_CHUNKS in the environment, or
+// mds_set_strip / mds_set_pass_shape, force a shape.
 
-// Pick the strip length by timing the pass for a few candidates (once per
-// process and (GPU, N, D, precision)); MDS_STRIP in the environment forces it.
+struct TuneKey {
+    std::string gpu;
+    int64_t n;
+    int d;
+    bool fp64;
+    bool reordered;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(gpu, n, d, fp64, reordered) < std::tie(o.gpu, o.n, o.d, o.fp64, o.reordered);
+    }
+};
+struct TuneVal {
+    int kind;
+    int param;
+    double ms;
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_file() {
+    if (const char *env = getenv("MDS_TUNE_CACHE")) return env;
+    Dl_info info{};
+    if (dladdr(reinterpret_cast<const void *>(&mds_create), &info) && info.dli_fname) {
+        std::string f = info.dli_fname;
+        const size_t k = f.find_last_of('/');
+        return (k == std::string::npos ? std::string(".") : f.substr(0, k)) + "/tune_cache.txt";
+    }
+    return "";
+}
+
+// Read the file into the cache (caller holds g_tune_mu).
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const std::string path = tune_file();
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        std::vector<std::string> fld;
+        std::string cur;
+        for (const char *p = line; *p && *p != '\n'; ++p) {
+            if (*p == '\t') {
+                fld.push_back(cur);
+                cur.clear();
+            } else {
+                cur.push_back(*p);
+            }
+        }
+        fld.push_back(cur);
+        if (fld.size() != 8) continue;
+        TuneKey k{fld[0], atoll(fld[1].c_str()), atoi(fld[2].c_str()), fld[3] == "fp64", fld[4] == "locality"};
+        TuneVal v{atoi(fld[5].c_str()), atoi(fld[6].c_str()), atof(fld[7].c_str())};
+        if ((v.kind == kPassStrips && v.param >= 1 && v.param <= kMaxStrip) ||
+            (v.kind == kPassChunks && v.param >= 1 && v.param <= 8))
+            g_tune_cache[k] = v;
+    }
+    fclose(f);
+}
+
+// Write the cache back (caller holds g_tune_mu): a temporary file, then a rename.
+void tune_save() {
+    const std::string path = tune_file();
+    if (path.empty()) return;
+    const std::string tmp = path + "." + std::to_string(static_cast<long long>(getpid())) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const auto &kv : g_tune_cache)
+        fprintf(f, "%s\t%lld\t%d\t%s\t%s\t%d\t%d\t%.6f\n", kv.first.gpu.c_str(), static_cast<long long>(kv.first.n),
+                kv.first.d, kv.first.fp64 ? "fp64" : "fp32c", kv.first.reordered ? "locality" : "caller",
+                kv.second.kind, kv.second.param, kv.second.ms);
+    const bool ok = fclose(f) == 0;
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+}
+
+int apply_shape(mds_ctx *c, int kind, int param) {
+    if (kind == kPassChunks) {
+        if (c->pass_kind != kPassChunks || c->chunk_mult != param) CHECK(build_chunks(c, param));
+    } else if (c->pass_kind != kPassStrips || c->strip != param) {
+        CHECK(build_strips(c, param));
+    }
+    return MDS_OK;
+}
+
+// Mean milliseconds of `reps` passes (with their reductions) after one warm-up.
+int time_shape(mds_ctx *c, int reps, float *ms) {
+    CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+    CU(cudaEventRecord(c->ev0, c->stream));
+    for (int w = 0; w < reps; ++w) CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+    CU(cudaEventRecord(c->ev1, c->stream));
+    CU(cudaEventSynchronize(c->ev1));
+    CU(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+    *ms /= static_cast<float>(reps);
+    return MDS_OK;
+}
+
 int autotune(mds_ctx *c) {
-    if (c->strip_req > 0) {
-        if (c->strip != c->strip_req) CHECK(build_strips(c, c->strip_req));
+    if (c->strip_req > 0) return apply_shape(c, kPassStrips, c->strip_req);
+    if (c->chunk_req != 0 && !c->fp64) {
+        CHECK(apply_shape(c, kPassChunks, c->chunk_req));
+        if (c->tile_cost.empty()) {
+            // cut by measured costs: one counted pass, then the chunks again
+            CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+            CHECK(check_device_err(c, "chunk costs"));
+            CHECK(read_tile_costs(c));
+            CHECK(build_chunks(c, c->chunk_req));
+        }
         return MDS_OK;
     }
     if (const char *env = getenv("MDS_STRIP")) {
         const int s = atoi(env);
-        if (s > 0) {
-            if (c->strip != s) CHECK(build_strips(c, std::min(s, kMaxStrip)));
-            return MDS_OK;
-        }
+        if (s > 0) return apply_shape(c, kPassStrips, std::min(s, kMaxStrip));
     }
-    const auto key = std::make_tuple(c->device_name, c->n, static_cast<int>(c->d), c->fp64);
+    if (const char *env = getenv("MDS_CHUNKS")) {
+        const int m = atoi(env);
+        if (m > 0 && !c->fp64) return apply_shape(c, kPassChunks, std::min(m, 8));
+    }
+    const TuneKey key{c->device_name, c->n, static_cast<int>(c->d), c->fp64, c->reordered};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            if (c->strip != it->second) CHECK(build_strips(c, it->second));
+            CHECK(apply_shape(c, it->second.kind, it->second.param));
+            if (it->second.kind == kPassChunks && c->tile_cost.empty()) {
+                // cut by measured costs: one counted pass, then the chunks again
+                CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+                CHECK(check_device_err(c, "autotune"));
+                CHECK(read_tile_costs(c));
+                CHECK(build_chunks(c, it->second.param));
+            }
             return MDS_OK;
         }
     }
-    const int smax = kMaxStrip;
-    std::vector<int> cands;
+    std::vector<std::pair<int, int>> cands;
     for (int s : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
-        if (s > smax || s > c->nt) continue;
+        if (s > kMaxStrip || s > c->nt) continue;
         const int64_t strips_est = (c->tiles + s - 1) / s;
         // keep enough CTAs for every SM, unless the problem is tiny anyway
         if (!cands.empty() && strips_est < 2 * c->sm_count) continue;
-        cands.push_back(s);
+        cands.emplace_back(kPassStrips, s);
     }
-    if (cands.empty()) cands.push_back(1);
-    int best = cands[0];
+    if (cands.empty()) cands.emplace_back(kPassStrips, 1);
+    if (!c->fp64 && c->tiles >= 2) {
+        const int per_sm = std::max(1, pair_chunk_blocks_per_sm(c->d));
+        for (int m : {1, 2, 3})
+            if (static_cast<int64_t>(c->sm_count) * per_sm * m <= c->tiles || m == 1) cands.emplace_back(kPassChunks, m);
+    }
+    std::pair<int, int> best = cands[0];
     float best_ms = 1e30f;
     const bool prof = c->profiling;
     c->profiling = false;
     if (cands.size() > 1) {
-        for (int s : cands) {
-            CHECK(build_strips(c, s));
-            for (int w = 0; w < 2; ++w) CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
-            CU(cudaEventRecord(c->ev0, c->stream));
-            const int reps = 5;
-            for (int w = 0; w < reps; ++w) CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
-            CU(cudaEventRecord(c->ev1, c->stream));
-            CU(cudaEventSynchronize(c->ev1));
+        for (const auto &cd : cands) {
+            CHECK(apply_shape(c, cd.first, cd.second));
+            if (cd.first == kPassChunks) {
+                // one counted pass, then cut by its far counts
+                CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+                CHECK(read_tile_costs(c));
+                CHECK(build_chunks(c, cd.second));
+            }
             float ms = 0.f;
-            CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            CHECK(time_shape(c, 5, &ms));
             if (ms < best_ms) {
                 best_ms = ms;
-                best = s;
+                best = cd;
             }
         }
         CHECK(check_device_err(c, "autotune"));
@@ -601,9 +892,10 @@ int autotune(mds_ctx *c) {
     c->profiling = prof;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = best;
+        g_tune_cache[key] = TuneVal{best.first, best.second, static_cast<double>(best_ms)};
+        if (cands.size() > 1) tune_save();
     }
-    if (c->strip != best) CHECK(build_strips(c, best));
+    CHECK(apply_shape(c, best.first, best.second));
     return MDS_OK;
 }
 
@@ -957,6 +1249,7 @@ int repack_to(mds_ctx *c, const std::vector<int32_t> &order, bool from_identity)
     c->perm_h = order;
     c->inv_h = inv;
     c->reordered = true;
+    c->tile_cost.clear();  // far counts of the old order
     c->gen++;  // the captured graph holds the old Y pointer
     c->grad_valid = false;
     return MDS_OK;
@@ -1067,6 +1360,8 @@ int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out
     if (!c->fp64) {
         if ((st = dev_alloc_t(c, &c->xrow, nd_pad / 2 * sizeof(float4)))) return cleanup(st);
         if ((st = dev_alloc_t(c, &c->xcol, nd_pad * sizeof(float4)))) return cleanup(st);
+        if ((st = dev_alloc_t(c, &c->xcol2, nd_pad * sizeof(float2)))) return cleanup(st);
+        if ((st = dev_alloc_t(c, &c->far_tile, static_cast<size_t>(c->tiles) * kPairWarps))) return cleanup(st);
         if ((st = dev_alloc_t(c, &c->split, sizeof(Split)))) return cleanup(st);
         if ((st = dev_alloc_t(c, &c->xmax_bits, sizeof(unsigned)))) return cleanup(st);
     }
@@ -1078,6 +1373,8 @@ int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out
     if ((st = dev_alloc_t(c, &c->counters, kCounters * sizeof(int64_t)))) return cleanup(st);
     if ((st = dev_alloc_t(c, &c->err, sizeof(unsigned)))) return cleanup(st);
     if ((st = dev_alloc_t(c, &c->bad, sizeof(unsigned long long)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->stamps, 2 * sizeof(unsigned long long)))) return cleanup(st);
+    if ((st = dev_alloc_t(c, &c->pass_ns, 2 * sizeof(double)))) return cleanup(st);
     const int64_t start_grid_max = (nd_pad + 4 * 256 - 1) / (4 * 256) + 1;
     if ((st = dev_alloc_t(c, &c->e_start, start_grid_max * 2 * sizeof(double)))) return cleanup(st);
     if ((st = dev_alloc_t(c, &c->e_end, (c->nt * kReduceQuarters + 1) * 2 * sizeof(double)))) return cleanup(st);
@@ -1091,10 +1388,14 @@ int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out
               cudaMemset(c->grad, 0, nd_pad * grad_elem(c)) == cudaSuccess &&
               cudaMemset(c->scal, 0, kScalars * 8) == cudaSuccess &&
               cudaMemset(c->counters, 0, kCounters * 8) == cudaSuccess &&
-              cudaMemset(c->err, 0, sizeof(unsigned)) == cudaSuccess;
+              cudaMemset(c->err, 0, sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(c->stamps, 0, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMemset(c->pass_ns, 0, 2 * sizeof(double)) == cudaSuccess;
     if (ok && !c->fp64) {
         ok = cudaMemset(c->xrow, 0, nd_pad / 2 * sizeof(float4)) == cudaSuccess &&
              cudaMemset(c->xcol, 0, nd_pad * sizeof(float4)) == cudaSuccess &&
+             cudaMemset(c->xcol2, 0, nd_pad * sizeof(float2)) == cudaSuccess &&
+             cudaMemset(c->far_tile, 0, static_cast<size_t>(c->tiles) * kPairWarps) == cudaSuccess &&
              cudaMemset(c->xmax_bits, 0, sizeof(unsigned)) == cudaSuccess;
         Split sp{1.0f, 12582912.0f, 0.0f, 0};  // q = 1 until locations are set
         ok = ok && cudaMemcpy(c->split, &sp, sizeof(sp), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -1124,7 +1425,8 @@ int mds_destroy(mds_ctx *c) {
                     c->split,    c->xmax_bits, c->grad,     c->grad0,    c->col_part,  c->row_part,
                     c->scal_part, c->strips,  c->row_first, c->scal,     c->counters,  c->err,
                     c->bad,      c->e_start,  c->e_end,     c->stage,    c->p_inj,     c->u_inj,
-                    c->acc_out,  c->dh_out,    c->perm_d,    c->inv_d,     c->far_part};
+                    c->acc_out,  c->dh_out,    c->perm_d,    c->inv_d,     c->far_part,  c->chunks,
+                    c->far_tile, c->xcol2,     c->stamps,    c->pass_ns};
     for (void *b : bufs) dev_free(b);
     void *ho_bufs[] = {c->ho_off, c->ho_pairs, c->ho_y, c->tile_ho, c->lse_m, c->lse_s, c->lpd_part, c->sigma_draws};
     for (void *b : ho_bufs) dev_free(b);
@@ -2220,13 +2522,73 @@ int mds_set_strip(mds_ctx *c, int32_t strip) {
     if (strip < 0) return fail(c, MDS_ERR_INVALID_ARG, "strip must be >= 0");
     if (strip > kMaxStrip) return fail(c, MDS_ERR_INVALID_ARG, "strip %d exceeds the limit %d", strip, kMaxStrip);
     c->strip_req = strip;
-    if (strip > 0 && strip != c->strip) CHECK(build_strips(c, strip));
+    c->chunk_req = 0;
+    if (strip > 0) CHECK(apply_shape(c, kPassStrips, strip));
     return MDS_OK;
 }
 
 int mds_get_strip(const mds_ctx *c, int32_t *strip) {
     if (!c || !strip) return MDS_ERR_INVALID_ARG;
     *strip = c->strip;
+    return MDS_OK;
+}
+
+int mds_set_pass_shape(mds_ctx *c, int32_t kind, int32_t param) {
+    CHECK(check_ctx(c));
+    if (kind != MDS_PASS_STRIPS && kind != MDS_PASS_CHUNKS && kind != MDS_PASS_CHUNK_COUNT)
+        return fail(c, MDS_ERR_INVALID_ARG, "kind must be MDS_PASS_STRIPS, MDS_PASS_CHUNKS or MDS_PASS_CHUNK_COUNT");
+    if (param < 0) return fail(c, MDS_ERR_INVALID_ARG, "param must be >= 0");
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    if (kind == MDS_PASS_STRIPS) {
+        if (param > kMaxStrip) return fail(c, MDS_ERR_INVALID_ARG, "strip %d exceeds the limit %d", param, kMaxStrip);
+        c->chunk_req = 0;
+        c->strip_req = param;
+        if (param > 0) CHECK(apply_shape(c, kPassStrips, param));
+    } else {
+        if (c->fp64) return fail(c, MDS_ERR_INVALID_ARG, "the FP64 context has the strip pass only");
+        if (kind == MDS_PASS_CHUNKS && param > 8)
+            return fail(c, MDS_ERR_INVALID_ARG, "chunks per CTA slot must be <= 8, got %d", param);
+        if (kind == MDS_PASS_CHUNK_COUNT && param == 0)
+            return fail(c, MDS_ERR_INVALID_ARG, "MDS_PASS_CHUNK_COUNT needs a chunk count >= 1");
+        c->strip_req = 0;
+        c->chunk_req = kind == MDS_PASS_CHUNK_COUNT ? -param : param;
+        if (param > 0) CHECK(apply_shape(c, kPassChunks, c->chunk_req));
+    }
+    c->grad_valid = false;
+    return MDS_OK;
+}
+
+int mds_get_pass_shape(const mds_ctx *c, int32_t *kind, int32_t *param, int32_t *ctas) {
+    if (!c) return MDS_ERR_INVALID_ARG;
+    const bool counted = c->pass_kind == kPassChunks && c->chunk_mult < 0;
+    if (kind) *kind = counted ? MDS_PASS_CHUNK_COUNT : c->pass_kind;
+    if (param) *param = c->pass_kind == kPassChunks ? (counted ? -c->chunk_mult : c->chunk_mult) : c->strip;
+    if (ctas) *ctas = c->n_strips;
+    return MDS_OK;
+}
+
+int mds_set_pass_stamps(mds_ctx *c, int on) {
+    CHECK(check_ctx(c));
+    if (c->hmc_pending > 0 || !c->acc_spill.empty())
+        return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
+    const unsigned long long init[2] = {~0ull, 0ull};
+    const double zero[2] = {0.0, 0.0};
+    CU(cudaMemcpyAsync(c->stamps, init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->pass_ns, zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->stamping != (on != 0)) c->gen++;  // captured launches carry the stamp pointers
+    c->stamping = on != 0;
+    return MDS_OK;
+}
+
+int mds_get_pass_span(mds_ctx *c, int64_t *passes, double *total_ms) {
+    CHECK(check_ctx(c));
+    double v[2] = {0.0, 0.0};
+    CU(cudaMemcpyAsync(v, c->pass_ns, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (passes) *passes = static_cast<int64_t>(v[1]);
+    if (total_ms) *total_ms = v[0] * 1e-6;
     return MDS_OK;
 }
 

@@ -19,16 +19,20 @@ namespace mds {
 // row block are contiguous.
 //
 // Work split inside a tile (one CTA of 4 warps): warp w takes columns
-// [16w, 16w+16); lane l = 8b + a takes the 4 columns 16w + 4b + {0..3} and
-// the 8 rows 2(a + 8q) + {0, 1}, q = 0..3 (4 row pairs).  Y inside a tile is
-// stored in exactly the order the lanes read it:
-//   element (r, c) at  ((w * 8 + t) * 32 + lane) * 4 + e,
+// [16w, 16w+16).  In the strip pass (and the chunked pass for D > 2) lane
+// l = 8b + a takes the 4 columns 16w + 4b + {0..3} and the 8 rows
+// 2(a + 8q) + {0, 1}, q = 0..3 (4 row pairs); in the chunked pass for D <= 2
+// lane l = 4b + a takes the 2 columns 16w + 2b + {0, 1} and the 16 rows
+// 2(a + 4q) + {0, 1}, q = 0..7 (8 row pairs).  Y inside a tile is stored as
+// float4 {y(r,c), y(r+1,c), y(r,c+1), y(r+1,c+1)} (two row-packed operands of
+// the f32x2 instructions) in the order the first mapping reads them:
+//   element (r, c) at  ((w * 8 + t) * 32 + slot) * 4 + e,
 //   w = c / 16, b = (c / 4) % 4, half = (c % 4) / 2, rp = r / 2, a = rp % 8,
-//   q = rp / 8, lane = 8b + a, t = 2q + half, e = 2 (c % 2) + (r % 2),
-// so that warp w's quarter of a tile is 4 KB contiguous (one bulk TMA copy)
-// and every 128-bit shared-memory load of the 32 lanes reads 512 contiguous
-// bytes (no bank conflicts), giving {y(r,c), y(r+1,c), y(r,c+1), y(r+1,c+1)}
-// -- two row-packed operands of the f32x2 instructions.
+//   q = rp / 8, slot = 8b + (a XOR 4 half), t = 2q + half, e = 2 (c % 2) + (r % 2),
+// so that warp w's quarter of a tile is 4 KB contiguous (one bulk TMA copy).
+// A 128-bit shared-memory load of the first mapping reads 512 contiguous
+// bytes (lane l at slot l XOR 4 half); the XOR keeps the second mapping's
+// loads free of bank conflicts too (each group of 8 lanes covers all banks).
 // ---------------------------------------------------------------------------
 constexpr int kTile = 64;
 constexpr int kTileElems = kTile * kTile;   // 4096 FP32 values = 16 KB
@@ -47,8 +51,8 @@ __host__ __device__ inline int64_t tile_count(int64_t nt) { return nt * (nt + 1)
 __host__ __device__ inline int tile_offset(int r, int c) {
     const int w = c >> 4, b = (c >> 2) & 3, half = (c >> 1) & 1, ec = c & 1;
     const int rp = r >> 1, a = rp & 7, q = rp >> 3;
-    const int lane = 8 * b + a, t = 2 * q + half, e = 2 * ec + (r & 1);
-    return ((w * 8 + t) * 32 + lane) * 4 + e;
+    const int slot = 8 * b + (a ^ (half << 2)), t = 2 * q + half, e = 2 * ec + (r & 1);
+    return ((w * 8 + t) * 32 + slot) * 4 + e;
 }
 
 // Offset of row i in the packed strict upper triangle (row-major (0,1),(0,2),...).
@@ -59,6 +63,19 @@ __host__ __device__ inline int64_t packed_row_start(int64_t i, int64_t n) { retu
 // strips of a row block occupy consecutive row slots.
 struct Strip {
     int32_t I, j0, j1, row_slot;
+};
+
+// One unit of work of the chunked FP32C pair pass (chunk_kernel.cu): the
+// tiles [t0, t1) of the row-block-ordered tile sequence, (I0, J0) the blocks
+// of tile t0 and I1 the row block of tile t1 - 1.  A segment is the run of a
+// chunk's tiles in one row block (segment s of the chunk is row block I0 + s);
+// seg0 is the chunk's first segment in the global order of segments (chunk
+// by chunk), which sets its row-partial slots: warp w of segment g writes
+// slot 4 g + w.  The segments of one row block are consecutive in that order.
+struct Chunk {
+    int64_t t0, t1;
+    int32_t I0, J0, I1;
+    int32_t seg0;
 };
 
 // Scalar partial sums per strip, in this order.
@@ -113,6 +130,12 @@ struct PairArgs {
     int32_t *far_part;       // FP32C: per strip and warp, the warp blocks (64 x 8 pairs) of the last
                              // pass that skipped the Phi terms (diagnostics), or null
     unsigned *err;           // device error word (see ErrBits)
+    const Chunk *chunks;     // chunked FP32C pass: one chunk per CTA (n_strips chunks), else null
+    const float2 *xcol2;     // chunked FP32C pass: column layout {-xh_j, -xl_j} [(j * D + k)]
+    unsigned char *far_tile; // chunked FP32C pass: per tile and warp, the column pairs (0..2) that took
+                             // the far body, for the cost model of the chunking (or null)
+    unsigned long long *stamps;  // if not null: [0] earliest start and [1] latest end (%globaltimer ns)
+                                 // of the pass's warps after the dependency wait (min / max atomics)
     float far_d2;            // FP32C: (z_c sigma)^2; warp blocks at least this far apart skip the Phi
                              // terms (+inf: never)
     // FP32C constants (sigma folded in on the host), each duplicated {c, c}
@@ -122,6 +145,8 @@ struct PairArgs {
     float2 c_phi;            // -log2(e) / (2 sigma^2): 2^(c_phi delta^2) = exp(-z^2/2)
     float2 neg_inv_s2;       // -1/sigma^2
     float2 m_coef;           // 1/(sigma sqrt(2 pi))
+    float2 c_m2;             // chunked pass: -sigma / sqrt(2 pi), the Phi term of the gradient weight in
+                             // units of -1/sigma^2 (its partial sums carry the factor -sigma^2)
     // FP64 constants
     double sigma;
     double inv_sigma;
@@ -193,6 +218,11 @@ cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s);
 // smem_min: dynamic shared memory of each CTA at least this (the layout's
 // size otherwise): more only to cap the pass's CTAs per SM.
 cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true, int smem_min = 0);
+// The chunked FP32C pass (chunk_kernel.cu): a.chunks / a.n_strips chunks,
+// one CTA each.
+cudaError_t launch_pair_chunks_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true, int smem_min = 0);
+int pair_chunk_smem_bytes(int d);
+int pair_chunk_blocks_per_sm(int d);
 int pair_f32_smem_bytes(int d);
 cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s, bool pdl = true);
 
@@ -240,6 +270,7 @@ struct XState {
     const int32_t *inv;       // slot of item k in the tile layouts (locality order), or null (identity)
     float4 *xrow;             // FP32C split layouts (null on the FP64 path)
     float4 *xcol;
+    float2 *xcol2;            // FP32C column layout of the chunked pass {-xh, -xl} (or null)
     Split *split;             // FP32C quantum (device; grown by the end-of-trajectory reduction)
     unsigned *xmax_bits;      // FP32C: running max |x| (float bits, atomicMax)
 };
@@ -248,6 +279,10 @@ struct ReduceArgs {
     const void *row_part;
     const void *col_part;
     const void *scal_part;
+    double part_scale;        // the gradient is part_scale (sum of column partials - sum of row partials):
+                              // 1 for the strip passes, -1/sigma^2 for the chunked FP32C pass
+    unsigned long long *stamps;   // the pass's start / end stamps (PairArgs::stamps), or null: the
+    double *pass_ns;              // scalar CTA adds end - start to pass_ns[0], counts pass_ns[1], resets
     const int32_t *row_first_slot;  // [nt + 1]
     const int32_t *perm;      // item at slot s of the tile layouts, or null (identity)
     int32_t n_strips;

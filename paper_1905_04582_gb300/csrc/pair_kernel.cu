@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
         }
     }
     pdl_wait();
+    if (a.stamps && lane == 0) atomicMin(&a.stamps[0], global_ns());
     if (lane == 0) {
         for (int s = 0; s < kStages && s < nst; ++s)
             tma_load_1d(ring + s * L::kStageBytes + kWarpTileElems * 4, xsrc0 + s * kTile * D, kXjBytes, &bars[s]);
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
                           reinterpret_cast<float *>(a.row_part) + static_cast<int64_t>(st.row_slot) * kTile * D,
                           reinterpret_cast<float *>(a.scal_part) + static_cast<int64_t>(blockIdx.x) * kScalarParts,
                           a.err);
+    if (a.stamps && lane == 0) atomicMax(&a.stamps[1], global_ns());
 }
 
 // ---------------------------------------------------------------- FP64
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
         return;
     }
     pdl_wait();
+    if (a.stamps && lane == 0) atomicMin(&a.stamps[0], global_ns());
     const int64_t nt = a.nt, n = a.n;
     const bool ragged = (n % kTile) != 0;
     const int64_t t0 = tile_index(st.I, st.j0, nt);
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
             for (int k = 0; k < D; ++k) xj[k] = a.x64[citem * D + k];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 yv = ys[(2 * q + (c >> 1)) * 32 + lane];
+                const float4 yv = ys[(2 * q + (c >> 1)) * 32 + (lane ^ ((c >> 1) << 2))];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float yf = (c & 1) ? (h ? yv.w : yv.z) : (h ? yv.y : yv.x);
@@ -356,6 +359,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
         reinterpret_cast<double *>(a.scal_part)[static_cast<int64_t>(blockIdx.x) * kScalarParts + tid] = v;
         if (!isfinite(v)) atomicOr(a.err, kErrNonfinite);
     }
+    if (a.stamps && lane == 0) atomicMax(&a.stamps[1], global_ns());
 }
 
 template <int D>

@@ -351,7 +351,7 @@ __device__ __forceinline__ int tile_f32(const K &a, const float4 *ys, const floa
             ++n_far;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 yv = ys[(2 * q + cp) * 32 + lane];
+                const float4 yv = ys[(2 * q + cp) * 32 + (lane ^ (cp << 2))];
                 float4 xi[D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) xi[k] = xis[k * 32 + la + 8 * q];
@@ -361,7 +361,7 @@ __device__ __forceinline__ int tile_f32(const K &a, const float4 *ys, const floa
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 yv = ys[(2 * q + cp) * 32 + lane];
+                const float4 yv = ys[(2 * q + cp) * 32 + (lane ^ (cp << 2))];
                 float4 xi[D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) xi[k] = xis[k * 32 + la + 8 * q];

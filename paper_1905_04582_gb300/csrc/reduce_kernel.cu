@@ -121,6 +121,7 @@ __device__ __forceinline__ void write_split_slot(const XState &xs, int64_t k, in
     xr[k & 1] = h;
     xr[2 + (k & 1)] = l;
     xs.xcol[k * d + kk] = make_float4(-h, -h, -l, -l);
+    if (xs.xcol2) xs.xcol2[k * d + kk] = make_float2(-h, -l);
 }
 
 // The same for item `item` (at its slot of the tile layouts).
@@ -204,6 +205,18 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     // every input (partials, x, p) comes from the pass just before
     pdl_trigger();
     pdl_wait();
+    if (a.stamps && blockIdx.x == 0 && tid == 0) {
+        // the pass just before is complete: its span (first warp past the
+        // dependency wait to the last warp's end) into the running total, and
+        // the stamps reset for the next pass (which waits for this kernel)
+        const unsigned long long t0 = a.stamps[0], t1 = a.stamps[1];
+        if (t1 > t0) {
+            a.pass_ns[0] += static_cast<double>(t1 - t0);
+            a.pass_ns[1] += 1.0;
+        }
+        a.stamps[0] = ~0ull;
+        a.stamps[1] = 0ull;
+    }
 
     if (Jq < 0) {
         // scalar partials of all strips -> L, sum r, dL/dsigma (fixed order)
@@ -388,8 +401,17 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
             const Acc g = gsum[d];
             T gv;
             if constexpr (kF32) {
-                grad[it * D + d] = make_float2(g.hi, g.lo);
-                gv = df_float(g);
+                if (a.part_scale == 1.0) {
+                    grad[it * D + d] = make_float2(g.hi, g.lo);
+                    gv = df_float(g);
+                } else {
+                    // partial sums in other units (the chunked pass sums the
+                    // gradient weight times -sigma^2): scaled in FP64
+                    const double v = (static_cast<double>(g.hi) + static_cast<double>(g.lo)) * a.part_scale;
+                    const float hi = static_cast<float>(v);
+                    grad[it * D + d] = make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+                    gv = hi;
+                }
             } else {
                 grad[it * D + d] = g;
                 gv = g;
@@ -714,9 +736,9 @@ __global__ void sigma_draws_kernel(uint64_t seed, uint32_t chain, int64_t iter0,
 
 // Inverse of tile_offset(): (row, column) inside a tile of element `off`.
 __device__ __forceinline__ void tile_rc(int off, int &r, int &c) {
-    const int e = off & 3, lane = (off >> 2) & 31, wt = off >> 7;
+    const int e = off & 3, slot = (off >> 2) & 31, wt = off >> 7;
     const int t = wt & 7, w = wt >> 3;
-    const int a = lane & 7, b = lane >> 3, q = t >> 1, half = t & 1;
+    const int q = t >> 1, half = t & 1, a = (slot & 7) ^ (half << 2), b = slot >> 3;
     r = 2 * (a + 8 * q) + (e & 1);
     c = 16 * w + 4 * b + 2 * half + (e >> 1);
 }

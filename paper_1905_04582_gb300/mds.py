@@ -51,7 +51,7 @@ def _buf(a, writable=False):
 class MDS:
     """One MDS problem (N items, D latent dimensions) resident on the GPU."""
 
-    def __init__(self, n, d, precision="fp32c", strip=None, stream=None):
+    def __init__(self, n, d, precision="fp32c", strip=None, stream=None, chunks=None):
         flags = {"fp32c": capi.MDS_PREC_FP32C, "fp64": capi.MDS_PREC_FP64}[precision]
         self._lib = capi.lib()
         h = ctypes.c_void_p()
@@ -60,6 +60,12 @@ class MDS:
         self.n, self.d, self.precision = int(n), int(d), precision
         if strip is not None:
             self.set_strip(strip)
+        if chunks is not None:
+            # chunks per resident CTA slot, or ("count", k) for exactly k chunks
+            if isinstance(chunks, tuple):
+                self.set_pass_shape(capi.MDS_PASS_CHUNK_COUNT, chunks[1])
+            else:
+                self.set_pass_shape(capi.MDS_PASS_CHUNKS, chunks)
         if stream is not None:
             self.set_stream(stream)
 
@@ -128,6 +134,27 @@ class MDS:
         s = ctypes.c_int32()
         self._check(self._lib.mds_get_strip(self._h, ctypes.byref(s)))
         return s.value
+
+    def set_pass_shape(self, kind, param):
+        """kind capi.MDS_PASS_STRIPS (param: tiles per strip) or
+        capi.MDS_PASS_CHUNKS (param: chunks per resident CTA slot); param 0
+        returns to the autotuner (mds_set_pass_shape)."""
+        self._check(self._lib.mds_set_pass_shape(self._h, int(kind), int(param)))
+
+    def get_pass_shape(self):
+        """(kind, param, CTAs of the pass) in use."""
+        k, p, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.mds_get_pass_shape(self._h, ctypes.byref(k), ctypes.byref(p), ctypes.byref(g)))
+        return k.value, p.value, g.value
+
+    def set_pass_stamps(self, on=True):
+        self._check(self._lib.mds_set_pass_stamps(self._h, 1 if on else 0))
+
+    def get_pass_span(self):
+        """(passes, total milliseconds) of the pass spans since set_pass_stamps."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        self._check(self._lib.mds_get_pass_span(self._h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
 
     def reorder(self):
         """Arrange the tile layouts in the locality order of the current
