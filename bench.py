@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -40,24 +41,26 @@ WORKLOAD = "paper-scale N=5392 D=2, 6-component Gaussian mixture, sigma=0.3, FP3
 SM_MAX_MHZ = 2070.0
 
 
-def fp32_ops_per_pair(d, far_frac=0.0):
-    """FP32 lane operations per pair, an FMA counting once.  pair2_f32
-    (pair_math.cuh): per coordinate the exact-split differences (3), squares
-    (1), cross term (2) and the two gradient accumulations (2); fixed: d^2,
-    residual (2), half inverse, corrected e (2), exp argument, Mills ratio
-    P and D (3 + 3), D Phi, 1/Phi, phi/Phi, log-product, e^2, m delta, w (2),
-    w/delta: 8 D + 22.  pair2_far (warp blocks whose pairs all lie at
-    z >= 8, Phi terms dropped): the same per coordinate; fixed d^2, residual
-    (2), half inverse, corrected e (2), e^2, w (2): 8 D + 9.  far_frac is the
-    fraction of warp blocks that took pair2_far."""
-    return (1.0 - far_frac) * (8 * d + 22) + far_frac * (8 * d + 9)
+def fp32_ops_per_pair(d, far_frac=0.0, chunked=True):
+    """FP32 lane operations per pair that the pass executes, an FMA counting
+    once.  Chunked pass (chunk_kernel.cu): per coordinate the exact-split
+    differences (3), the square (1), the cross term (2) and the two gradient
+    accumulations (2); then d^2, the residual (2), the corrected e (2), e^2
+    and the gradient weight (1): 8 D + 7 where every pair of the warp's block
+    lies at z >= 8 (Phi terms skipped); with Phi: the exp argument, the Mills
+    ratio P and D (3 + 3), D Phi, 1/Phi, phi/Phi, the log-product, m delta and
+    one more for the weight: 8 D + 20.  The strip pass (pair_math.cuh) takes
+    8 D + 9 and 8 D + 22.  far_frac is the fraction of warp blocks that took
+    the far body."""
+    far, near = (8 * d + 7, 8 * d + 20) if chunked else (8 * d + 9, 8 * d + 22)
+    return (1.0 - far_frac) * near + far_frac * far
 
 
-PAIR_KERNEL_SOURCES = ("pair_kernel.cu", "pair_math.cuh", "mills_ratio_coeffs.h")
+PAIR_KERNEL_SOURCES = ("pair_kernel.cu", "chunk_kernel.cu", "pair_math.cuh", "mills_ratio_coeffs.h")
 # the part of mds_internal.h the pair kernel is compiled from: the tile
 # geometry through the end of its argument struct, and the error bits
 PAIR_KERNEL_INTERNAL = (("// Tile geometry of the pair pass.", "cudaError_t launch_pair_batch"),)
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_f32_kernel_N5392_D2_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_chunk_kernel_N5392_D2_traffic.txt")
 
 
 def pair_kernel_sha256():
@@ -75,10 +78,10 @@ def pair_kernel_sha256():
     return h.hexdigest()
 
 
-def kernel_traffic(n, d):
+def kernel_traffic(n, d, kind="chunks"):
     """DRAM bytes per launch of the pair pass from the committed ncu capture
     (`key: value` lines), if it was taken on the current kernel source at
-    this N and D; else None."""
+    this N, D and pass kind (strips / chunks); else None."""
     try:
         kv = {}
         with open(TRAFFIC_FILE) as f:
@@ -87,7 +90,7 @@ def kernel_traffic(n, d):
                     k, v = ln.split(":", 1)
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_sha256") == pair_kernel_sha256() and int(kv.get("n", -1)) == n \
-                and int(kv.get("d", -1)) == d:
+                and int(kv.get("d", -1)) == d and kv.get("shape", "").split(" ")[0] == kind:
             return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         pass
@@ -188,30 +191,6 @@ def barrier(world):
         dist.barrier()
 
 
-def pass_distribution(model, wl, flush_l2, stream, n_warm=100, n_cold=20):
-    """Pair-kernel launch times (CUDA events around the launch): p10 / p50 /
-    p90 over n_warm back-to-back evaluations (Y L2-resident) and over n_cold
-    evaluations each after an L2 flush (Y from HBM)."""
-    import torch
-    x_dev = torch.from_numpy(wl.x_eval.copy()).to(device=torch.device("cuda", torch.cuda.current_device()))
-
-    def run(n, cold):
-        out = []
-        for _ in range(n):
-            if cold:
-                flush_l2()
-            model.set_profiling(True)  # restarts the launch timer
-            model.set_locations(x_dev)  # invalidates the cached pass (Y untouched)
-            model.log_likelihood()
-            out.append(model.pass_time()[1])
-        model.set_profiling(False)
-        q = np.quantile(np.array(out) * 1e3, [0.1, 0.5, 0.9])
-        return {"p10": float(q[0]), "p50": float(q[1]), "p90": float(q[2]), "n": n}
-
-    torch.cuda.synchronize()
-    return {"warm": run(n_warm, False), "cold": run(n_cold, True)}
-
-
 def cpu_oracle_rate(wl, evals, nthreads=1):
     """Oracle (as it stands) likelihood + gradient on the host: pairs/s."""
     import oracle
@@ -257,6 +236,153 @@ def run_reference(args):
     return 0
 
 
+def eps_pilot(model, eps0, seed, target=0.65, rounds=8, iters=10):
+    """A short pilot that picks the leapfrog step for acceptance ~ target
+    (section 2.3 leaves it to the user): blocks of `iters` HMC iterations, the
+    step moved on a log scale by the acceptance of each block (the gain
+    shrinking), starting from the evaluation point (the pilot also burns
+    the chain in).  Returns the step and the (eps, acceptance) history."""
+    eps = eps0
+    hist = []
+    for r in range(rounds):
+        acc, _, _ = model.hmc(iters, N_LEAPFROG, eps, seed=seed + 7919 * (r + 1))
+        a = float(np.mean(acc))
+        hist.append({"eps": eps, "accept": a})
+        eps *= math.exp(2.0 * (a - target) / math.sqrt(r + 1))
+    return eps, hist
+
+
+def parity_entry(model, wl, nthreads):
+    """Errors of the benchmarked path against the FP64 oracle at the model's
+    current locations (the bench configuration: locality order, tuned pass
+    shape, Phi cut-off): relative errors of L, sum r and dL/dsigma, max and
+    p99.9 of the per-coordinate gradient error, and the coordinates that pass
+    only through the cancellation / rounding branches (stated tolerances)."""
+    import oracle
+    oracle.build()
+    x = model.get_locations(dtype=np.float64)  # the FP32 state, widened exactly
+    ll, g, ds = model.gradient()
+    _, sr = model.log_likelihood()
+    ll_r, sr_r = oracle.loglik(wl.y_packed, x, wl.sigma, nthreads=nthreads)
+    g_r, s_abs, s_sq = oracle.gradient(wl.y_packed, x, wl.sigma, nthreads=nthreads, with_abs=True, with_sq=True)
+    ds_r = oracle.dsigma(wl.y_packed, x, wl.sigma, nthreads=nthreads)
+    u, tol = 2.0 ** -24, 1e-5
+    err = np.abs(g - g_r)
+    rel = err / np.maximum(np.abs(g_r), 1e-300)
+    rel_ok = err <= tol * np.abs(g_r)
+    kappa = s_abs / np.maximum(np.abs(g_r), 1e-300)
+    cond_ok = (kappa > 1e3) & (err <= max(tol * 1e-3, u) * s_abs)
+    round_ok = err <= 8.0 * u * s_sq
+    esc = ~rel_ok & (cond_ok | round_ok)
+    # coordinates above the rounding line |g| > 2 * 8 u / tol * S2 must meet
+    # the relative tolerance (the escape branches serve the ones below it)
+    line = 2.0 * 8.0 * u / tol
+    above = np.abs(g_r) > line * s_sq
+    ratio = np.abs(g_r) / np.maximum(s_sq, 1e-300)
+    return {"n_coords": int(g.size), "L_rel": abs(ll - ll_r) / abs(ll_r), "sum_r_rel": abs(sr - sr_r) / abs(sr_r),
+            "dsigma_rel": abs(ds - ds_r) / abs(ds_r), "dsigma_abs": abs(ds - ds_r),
+            "grad_max_rel": float(rel.max()), "grad_p999_rel": float(np.quantile(rel, 0.999)),
+            "grad_median_rel": float(np.median(rel)),
+            "grad_max_rel_above_line": float(rel[above].max()) if np.any(above) else 0.0,
+            "n_above_line": int(np.sum(above)),
+            "escape_max_g_over_s2": float(ratio[esc].max()) if np.any(esc) else 0.0, "escape_line": line,
+            "n_kappa_branch": int(np.sum(~rel_ok & cond_ok)),
+            "n_rounding_branch": int(np.sum(~rel_ok & ~cond_ok & round_ok)),
+            "n_out_of_tolerance": int(np.sum(~(rel_ok | cond_ok | round_ok))),
+            "tolerances": {"L": 1e-6, "grad_coord": tol, "dsigma": tol},
+            "oracle_threads": nthreads}
+
+
+def sweep_entries(reps, order="locality", with_fp64=True):
+    """The scale sweep (N = 20000, 50000; D = 2, 6; 12-component mixtures;
+    FP32C, autotuned pass shape): per size the pass span (stamps, so only the
+    pass), pairs/s and the fraction of the measured HBM copy bandwidth for
+    4 B of Y per pair (Y is 0.8 / 5.0 GB, far larger than L2, so every pass
+    streams it from HBM); the FP64 pass at N = 20000, D = 2."""
+    import torch
+    from paper_1905_04582_gb300 import workloads as W
+    from paper_1905_04582_gb300.mds import MDS
+    hbm_peak, peak_kind = load_peaks()
+    out = []
+    for n, d in ((20000, 2), (20000, 6), (50000, 2), (50000, 6)):
+        t0 = time.perf_counter()
+        wl = W.scale_sweep(n, d)
+        gen_s = time.perf_counter() - t0
+        with MDS(wl.n, wl.d, "fp32c") as m:
+            m.set_data(wl.y_packed)
+            m.set_locations(wl.x_eval)
+            m.set_sigma(wl.sigma)
+            if order == "locality":
+                m.reorder()
+            far, total = m.far_blocks()
+            m.set_pass_stamps(True)
+            ms = m.time_pass(reps)
+            n_pass, span_ms = m.get_pass_span()
+            m.set_pass_stamps(False)
+            span = span_ms / max(n_pass, 1)
+            kind, param, ctas = m.get_pass_shape()
+        gbs = 4.0 * wl.m / (span / 1e3) / 1e9
+        e = {"workload": wl.name, "n": n, "d": d, "pairs": wl.m, "y_bytes": 4 * wl.m, "order": order,
+             "pass_shape": {"kind": ["strips", "chunks", "chunks"][kind], "param": param, "ctas": ctas},
+             "far_fraction": far / total, "pass_span_ms": span, "pass_and_reduction_ms": ms,
+             "pairs_per_s": wl.m / (span / 1e3),
+             "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                     "peak_kind": f"{peak_kind} hbm_gbs"},
+             "ops_per_pair": fp32_ops_per_pair(d, far / total, kind != 0), "gen_s": gen_s}
+        if with_fp64 and n == 20000 and d == 2:
+            with MDS(wl.n, wl.d, "fp64") as m64:
+                m64.set_data(wl.y_packed)
+                m64.set_locations(wl.x_eval)
+                m64.set_sigma(wl.sigma)
+                m64.set_pass_stamps(True)
+                ms64 = m64.time_pass(2)
+                n64, sp64 = m64.get_pass_span()
+            e["fp64_pass_span_ms"] = sp64 / max(n64, 1)
+            e["speedup_vs_fp64"] = e["fp64_pass_span_ms"] / span
+        out.append(e)
+        del wl
+        torch.cuda.synchronize()
+    return out
+
+
+def batch_entry(reps, steps):
+    """Batched datasets x chains (N = 1600, 1500, 1300, 992; 8 chains each):
+    pair evaluations per second of one batched pass for all 32 chains, and
+    HMC leapfrog steps per second over all chains."""
+    import torch
+    from paper_1905_04582_gb300 import workloads as W
+    from paper_1905_04582_gb300.mds import Batch, MDS
+    ds = W.batch_datasets()
+    chains = 8
+    b = Batch([w.n for w in ds], 2, [chains] * len(ds))
+    try:
+        for k, w in enumerate(ds):
+            b.set_data(k, w.y_packed)
+            b.set_sigma(k, w.sigma)
+            for j in range(chains):
+                b.set_locations(k, j, w.x_eval)
+        ms = b.time_pass(reps)
+        evals = sum(w.m for w in ds) * chains
+        b.hmc(2, N_LEAPFROG, [5e-4] * len(ds), seed=1)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        acc, dh = b.hmc(steps, N_LEAPFROG, [5e-4] * len(ds), seed=2)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        strip = b.get_strip()
+    finally:
+        b.close()
+    with MDS(128, 2, "fp32c") as mc:
+        mc.set_sigma(ds[0].sigma)
+        ceil_near = mc.pair_body_ceiling(far=False)
+    return {"datasets": [w.n for w in ds], "chains_per_dataset": chains, "order": "caller", "strip": strip,
+            "ms_per_pass": ms, "pair_evals_per_pass": evals, "pair_evals_per_s": evals / (ms / 1e3),
+            "measured_ceiling": {"near_pairs_per_s": ceil_near, "frac": evals / (ms / 1e3) / ceil_near,
+                                 "note": "the full per-pair body (Phi evaluated) on register operands"},
+            "hmc_iterations": steps, "leapfrog_steps_per_s_all_chains": steps * N_LEAPFROG * len(ds) * chains / wall,
+            "accept_rate": float(np.mean(acc))}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -283,7 +409,6 @@ def run_gpu(args):
         model.reorder()  # tile layouts in the locality order of the start point
     far_blocks, total_blocks = model.far_blocks()
     far_frac = far_blocks / total_blocks
-    eps = args.eps
     seed = 1234 + rank
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -292,15 +417,24 @@ def run_gpu(args):
         with torch.cuda.stream(stream):
             flush.fill_(float(np.random.rand()))
 
-    # warm-up (autotune, graph capture, clocks)
+    # warm-up (autotune, graph capture, clocks), then the step size: fixed by
+    # --eps, else a short pilot for acceptance ~0.65
     model.log_likelihood()
-    model.hmc(max(args.warmup, 1), N_LEAPFROG, eps, seed=seed)
+    model.hmc(max(args.warmup, 1), N_LEAPFROG, 2e-4, seed=seed)
+    if args.eps > 0:
+        eps, pilot = args.eps, None
+    else:
+        eps, pilot = eps_pilot(model, 1e-3, seed)
+    model.hmc(1, N_LEAPFROG, eps, seed=seed)  # graph for this step size
 
     # timed region: K HMC iterations queued back to back on the stream (no
     # host round trip between them), each bracketed by its own CUDA events,
-    # L2 flushed before each one outside the brackets
+    # L2 flushed before each one outside the brackets.  The pair pass's span
+    # inside each leapfrog step is taken by %globaltimer stamps (no events
+    # between the launches, so programmatic dependent launch stays intact).
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    model.set_pass_stamps(True)
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
@@ -313,71 +447,69 @@ def run_gpu(args):
         acc, dh, stats = model.hmc_collect()
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+    n_pass, span_total_ms = model.get_pass_span()
+    model.set_pass_stamps(False)
     acc_total = int(acc.sum())
     barrier(world)
     step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
     dev_ms = sum(step_ms)
     dev_ms_max = reduce_max(dev_ms, world)
 
-    # the same K iterations again with CUDA events bracketing every pair-pass
-    # launch inside the graph: the dominant kernel's average duration
-    model.set_profiling(True)
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush_l2()
-        model.hmc(1, N_LEAPFROG, eps, seed=seed)
-    torch.cuda.synchronize()
-    n_pass, pass_ms = model.pass_time()
-    model.set_profiling(False)
-
     pairs_per_step = N_LEAPFROG * wl.m
     value = replica_rate(args.steps * pairs_per_step, dev_ms / 1e3, world)
     lf_steps = world * args.steps * N_LEAPFROG / (dev_ms_max / 1e3)
 
-    # roofline of the dominant kernel (the fused pair pass), timed live.  It
-    # is bound by the FP32 pipe: FP32_OPS_PER_PAIR lane operations per pair
-    # (counted from the kernel source; an FMA counts once) against
-    # SMs x 128 FP32 lanes x the SM clock.  The HBM view (4 B of Y per pair
-    # against the measured copy bandwidth) is reported beside it.
+    # roofline of the dominant kernel (the fused pair pass): HBM-bound by
+    # design, 4 B of Y per pair per pass, against the measured copy bandwidth;
+    # its time is the pass's span inside the timed steps
     hbm_peak, peak_kind = load_peaks()
     m_pairs, y_bytes = model.problem_size()
-    pass_avg_ms = pass_ms / max(n_pass, 1)
+    span_ms = span_total_ms / max(n_pass, 1)
     alg_bytes = 4.0 * m_pairs  # one FP32 y_ij per pair per pass
-    achieved_gbs = alg_bytes / (pass_avg_ms / 1e3) / 1e9
+    achieved_gbs = alg_bytes / (span_ms / 1e3) / 1e9
+    kind, param, ctas = model.get_pass_shape()
+    kname = ["strips", "chunks", "chunks"][kind]
+    chunked = kind != 0
+    kernel_name = f"pair_chunk_kernel<{wl.d}>" if chunked else f"pair_f32_kernel<{wl.d}>"
+    traffic = kernel_traffic(wl.n, wl.d, kname)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk = clocks.summary()
     sm_mhz = (clk or {}).get("sm_max_mhz") or SM_MAX_MHZ
-    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12  # TFP32-op/s
-    ops = fp32_ops_per_pair(wl.d, far_frac)
-    alu_achieved = m_pairs * ops / (pass_avg_ms / 1e3) / 1e12
-    traffic = kernel_traffic(wl.n, wl.d)
+    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12  # T FP32 lane-op/s
+    ops = fp32_ops_per_pair(wl.d, far_frac, chunked)
+    kernel_rate = m_pairs / (span_ms / 1e3)
 
-    # the plain FP64 GPU path on the same data (one pass, timed alone)
+    # the plain FP64 GPU path on the same data (pass spans, timed alone)
     with MDS(wl.n, wl.d, "fp64", stream=stream) as m64:
         m64.set_data(wl.y_packed)
         m64.set_locations(wl.x_eval)
         m64.set_sigma(wl.sigma)
+        m64.set_pass_stamps(True)
         ms64 = m64.time_pass(5)
+        n64, sp64 = m64.get_pass_span()
+    model.set_pass_stamps(True)
     ms32 = model.time_pass(20)
+    n32, sp32 = model.get_pass_span()
+    model.set_pass_stamps(False)
     # the same FP32C pass with the items in the caller's (random) order: no
     # warp block is all far, every pair evaluates Phi
     with MDS(wl.n, wl.d, "fp32c", stream=stream) as m_u:
         m_u.set_data(wl.y_packed)
         m_u.set_locations(wl.x_eval)
         m_u.set_sigma(wl.sigma)
+        m_u.set_pass_stamps(True)
         ms32_unordered = m_u.time_pass(20)
-    pass_dist = pass_distribution(model, wl, flush_l2, stream)
-    # the measured ceiling of the pass's per-pair arithmetic: the same bodies
-    # with their operands in registers, no memory traffic or epilogue; far
-    # blocks take the body without the Phi terms
+        nu, spu = m_u.get_pass_span()
+    # the measured ceiling of the per-pair arithmetic: the bodies with their
+    # operands in registers, no memory traffic or epilogue; far blocks take
+    # the body without the Phi terms
     ceil_near = model.pair_body_ceiling(far=False)
     ceil_far = model.pair_body_ceiling(far=True)
     ceil_w = 1.0 / (far_frac / ceil_far + (1.0 - far_frac) / ceil_near)
-    kernel_rate = m_pairs / (pass_avg_ms / 1e3)
 
     # end to end through the C ABI with host buffers: X in, one HMC
     # iteration, X and the statistics out
-    x_host = torch.from_numpy(wl.x_eval.copy()).pin_memory()
+    x_host = torch.from_numpy(model.get_locations(dtype=np.float32).copy()).pin_memory()
     x_out = torch.empty_like(x_host).pin_memory()
     e2e_steps = max(3, args.steps)
     torch.cuda.synchronize()
@@ -390,16 +522,27 @@ def run_gpu(args):
     e2e_value = replica_rate(e2e_steps * pairs_per_step, time.perf_counter() - t0, world)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        rate, secs = cpu_oracle_rate(wl, args.cpu_evals)
-        cpu = {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_evals} serial evaluations of L and dL/dX at N=5392 ({secs:.1f} s)"}
+    parity = None
+    if rank == 0 and world == 1:
         ncores = os.cpu_count() or 1
-        rate_mt, secs_mt = cpu_oracle_rate(wl, args.cpu_evals, nthreads=ncores)
-        cpu["all_cores"] = {"value": rate_mt, "unit": "pairs/s", "cores": ncores, "kind": "oracle (OpenMP rows)",
-                            "sample": f"{args.cpu_evals} evaluations of L and dL/dX at N=5392 ({secs_mt:.1f} s)"}
+        parity = parity_entry(model, wl, ncores)
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            rate, secs = cpu_oracle_rate(wl, args.cpu_evals)
+            cpu = {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{args.cpu_evals} serial evaluations of L and dL/dX at N=5392 ({secs:.1f} s)"}
+            rate_mt, secs_mt = cpu_oracle_rate(wl, args.cpu_evals, nthreads=ncores)
+            cpu["all_cores"] = {"value": rate_mt, "unit": "pairs/s", "cores": ncores,
+                                "kind": "oracle (OpenMP rows)",
+                                "sample": f"{args.cpu_evals} evaluations of L and dL/dX at N=5392 ({secs_mt:.1f} s)"}
+    model.close()
+
+    sweep = None
+    if rank == 0 and world == 1 and not args.no_sweep:
+        with ClockSampler(local) as sclk:
+            sweep = {"scale": sweep_entries(3), "batched": batch_entry(5, 5)}
+        sweep["clocks"] = sclk.summary()
 
     if rank == 0:
         line = {
@@ -409,36 +552,43 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "n": wl.n, "d": wl.d, "pairs": m_pairs, "sigma": wl.sigma,
                        "precision": "FP32 per pair, compensated FP32 partials reduced in FP64",
                        "step": f"one HMC iteration: {N_LEAPFROG} leapfrog steps (fused L+grad pass each) + Metropolis",
-                       "eps": eps, "strip": model.get_strip(),
+                       "eps": eps, "eps_pilot": pilot,
+                       "pass_shape": {"kind": kname, "param": param, "ctas": ctas},
                        "order": ("locality order of the start point (mds_reorder)" if args.order == "locality"
                                  else "caller's item order"),
                        "l2": "flushed (512 MB write) between timed steps; Y (58 MB) stays L2-resident within a step",
                        "parallelism": f"replicas x{world}"},
             "leapfrog_steps_per_s": lf_steps,
             "accept_rate": acc_total / args.steps,
-            "hbm_fraction_of_pairs_rate": value * 4.0 / 1e9 / hbm_peak,
             "far_blocks": {"far": far_blocks, "total": total_blocks, "fraction": far_frac,
                            "note": "warp blocks of 64 x 8 pairs all at z >= 8: Phi terms skipped (start point)"},
-            "pass_alone": {"fp32c_ms": ms32, "fp64_ms": ms64, "fp32c_pairs_per_s": m_pairs / (ms32 / 1e3),
-                           "fp32c_caller_order_ms": ms32_unordered,
-                           "fp64_pairs_per_s": m_pairs / (ms64 / 1e3), "speedup_vs_fp64": ms64 / ms32,
-                           "pair_kernel_warm_us": pass_dist["warm"], "pair_kernel_cold_us": pass_dist["cold"]},
-            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFP32-op/s",
-                         "frac": alu_achieved / alu_peak, "traffic": traffic,
-                         "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
-                         "ops_per_pair": ops, "ops_per_pair_note": "8D+22 (Phi evaluated), 8D+9 (far blocks), "
-                                                                   "weighted by the far-block fraction",
-                         "kernel": f"pair_f32_kernel<{wl.d}>", "launches_timed": n_pass,
-                         "avg_launch_ms": pass_avg_ms, "pairs_per_launch": m_pairs,
-                         "hbm_view": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                                      "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                                      "algorithmic_bytes_per_launch": alg_bytes},
+            "pass_alone": {"fp32c_span_ms": sp32 / max(n32, 1), "fp32c_with_reduction_ms": ms32,
+                           "fp64_span_ms": sp64 / max(n64, 1), "fp64_with_reduction_ms": ms64,
+                           "fp32c_caller_order_span_ms": spu / max(nu, 1),
+                           "fp32c_pairs_per_s": m_pairs / (sp32 / max(n32, 1) / 1e3),
+                           "fp64_pairs_per_s": m_pairs / (sp64 / max(n64, 1) / 1e3),
+                           "speedup_vs_fp64": (sp64 / max(n64, 1)) / (sp32 / max(n32, 1))},
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                         "peak_kind": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                         "kernel": kernel_name, "algorithmic_bytes_per_launch": alg_bytes,
+                         "pass_span_ms": span_ms, "passes_timed": n_pass,
+                         "span_note": "per pass: the first warp past the dependency wait to the last warp's "
+                                      "end (%globaltimer), inside the timed HMC steps",
+                         "passes_x_span_ms_per_step": N_LEAPFROG * span_ms,
                          "measured_ceiling": {"near_pairs_per_s": ceil_near, "far_pairs_per_s": ceil_far,
                                               "weighted_pairs_per_s": ceil_w, "kernel_pairs_per_s": kernel_rate,
                                               "frac": kernel_rate / ceil_w,
-                                              "note": "mds_pair_body_ceiling: the pass's per-pair bodies on "
-                                                      "operands in registers at its occupancy, weighted by the "
-                                                      "far-block fraction"}},
+                                              "note": "mds_pair_body_ceiling: the strip pass's per-pair bodies "
+                                                      "on register operands at its occupancy, weighted by the "
+                                                      "far-block fraction"},
+                         "alu_view": {"ops_per_pair": ops, "achieved_tflops": kernel_rate * ops / 1e12,
+                                      "peak_tflops": alu_peak, "frac": kernel_rate * ops / 1e12 / alu_peak,
+                                      "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
+                                      "note": "FP32 lane operations the pass executes per pair (exact-split "
+                                              "arithmetic included), weighted by the far-block fraction"}},
+            "parity": parity,
+            "sweep": sweep,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": wl.n * wl.d * 4,
                     "d2h_bytes_per_step": wl.n * wl.d * 4 + 8 + 8 + 4,
@@ -446,11 +596,9 @@ def run_gpu(args):
             "gpu_launches": args.steps * (2 + 2 * N_LEAPFROG),
             "wall_s": wall,
         }
-        clk = clocks.summary()
         if clk is not None:
             line["clocks"] = clk
         print(json.dumps(line), flush=True)
-    model.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -470,115 +618,45 @@ def run_pass_only(args):
         wl = W.paper_scale(d=args.d)
     else:
         wl = W.make(f"mixture N={args.n} D={args.d}", args.n, args.d, 0.3, 5, 0.3, mixture=(6, 0.3))
-    with MDS(wl.n, wl.d, args.precision, strip=args.strip) as m:
+    with MDS(wl.n, wl.d, args.precision, strip=args.strip, chunks=args.chunks) as m:
         m.set_data(wl.y_packed)
         m.set_locations(wl.x_eval)
         m.set_sigma(wl.sigma)
         if args.order == "locality":
             m.reorder()
         far, total = m.far_blocks()
+        m.set_pass_stamps(True)
         ms = m.time_pass(args.reps)
+        n_pass, span = m.get_pass_span()
+        span /= max(n_pass, 1)
         print(json.dumps({"pass_only": True, "n": wl.n, "d": wl.d, "precision": args.precision,
-                          "order": args.order, "far_fraction": far / total,
-                          "strip": m.get_strip(), "ms_per_pass": ms, "pairs_per_s": wl.m / (ms / 1e3),
-                          "alg_gb_per_s": 4.0 * wl.m / (ms / 1e3) / 1e9}), flush=True)
+                          "order": args.order, "far_fraction": far / total, "pass_shape": m.get_pass_shape(),
+                          "pass_and_reduction_ms": ms, "pass_span_ms": span, "pairs_per_s": wl.m / (span / 1e3),
+                          "alg_gb_per_s": 4.0 * wl.m / (span / 1e3) / 1e9}), flush=True)
     return 0
 
 
-def _alu_peak_tflops():
-    import torch
-    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    return sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
-
-
 def run_sweep(args):
-    """The scale sweep (N = 20000, 50000; D = 2, 6; FP32C, autotuned strip):
-    one JSON line per size with the pass time and its HBM and ALU fractions,
-    Y (0.8 / 5.0 GB) far larger than L2, so every pass streams it from HBM."""
+    """The scale sweep alone: one JSON line per size (see sweep_entries)."""
     import torch
     from paper_1905_04582_gb300 import build as B
-    from paper_1905_04582_gb300 import workloads as W
-    from paper_1905_04582_gb300.mds import MDS
     B.build()
     torch.cuda.set_device(0)
-    hbm_peak, peak_kind = load_peaks()
-    alu_peak = _alu_peak_tflops()
-    for n, d in ((20000, 2), (20000, 6), (50000, 2), (50000, 6)):
-        wl = W.scale_sweep(n, d)
-        with MDS(wl.n, wl.d, "fp32c") as m:
-            m.set_data(wl.y_packed)
-            m.set_locations(wl.x_eval)
-            m.set_sigma(wl.sigma)
-            if args.order == "locality":
-                m.reorder()
-            far, total = m.far_blocks()
-            ms = m.time_pass(args.reps)
-            strip = m.get_strip()
-        ff = far / total
-        line = {"sweep": True, "workload": wl.name, "n": n, "d": d, "pairs": wl.m, "strip": strip,
-                "order": args.order, "far_fraction": ff,
-                "ms_per_pass": ms, "pairs_per_s": wl.m / (ms / 1e3),
-                "hbm": {"achieved_gbs": 4.0 * wl.m / (ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                        "frac": 4.0 * wl.m / (ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind},
-                "alu": {"achieved_tflops": wl.m * fp32_ops_per_pair(d, ff) / (ms / 1e3) / 1e12,
-                        "peak_tflops": alu_peak,
-                        "frac": wl.m * fp32_ops_per_pair(d, ff) / (ms / 1e3) / 1e12 / alu_peak}}
-        if n == 20000 and d == 2:
-            with MDS(wl.n, wl.d, "fp64") as m64:
-                m64.set_data(wl.y_packed)
-                m64.set_locations(wl.x_eval)
-                m64.set_sigma(wl.sigma)
-                ms64 = m64.time_pass(2)
-            line["fp64_ms_per_pass"] = ms64
-            line["speedup_vs_fp64"] = ms64 / ms
-        print(json.dumps(line), flush=True)
-        del wl
+    with ClockSampler(0) as clk:
+        entries = sweep_entries(args.reps, args.order)
+    for e in entries:
+        print(json.dumps(dict(e, sweep=True)), flush=True)
+    print(json.dumps({"sweep_clocks": clk.summary()}), flush=True)
     return 0
 
 
 def run_batch(args):
-    """Batched datasets x chains (N = 1600, 1500, 1300, 992; 8 chains each):
-    pair evaluations per second of one batched pass for all 32 chains, and
-    HMC leapfrog steps per second over all chains."""
+    """Batched datasets x chains alone (see batch_entry)."""
     import torch
     from paper_1905_04582_gb300 import build as B
-    from paper_1905_04582_gb300 import workloads as W
-    from paper_1905_04582_gb300.mds import Batch
     B.build()
     torch.cuda.set_device(0)
-    ds = W.batch_datasets()
-    chains = 8
-    b = Batch([w.n for w in ds], 2, [chains] * len(ds))
-    for k, w in enumerate(ds):
-        b.set_data(k, w.y_packed)
-        b.set_sigma(k, w.sigma)
-        for j in range(chains):
-            b.set_locations(k, j, w.x_eval)
-    ms = b.time_pass(args.reps)
-    evals = sum(w.m for w in ds) * chains
-    b.hmc(2, N_LEAPFROG, [5e-4] * len(ds), seed=1)  # warm-up (graph capture)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    acc, dh = b.hmc(args.steps, N_LEAPFROG, [5e-4] * len(ds), seed=2)
-    wall = time.perf_counter() - t0
-    alu_peak = _alu_peak_tflops()
-    # the measured ceiling of the full per-pair body (no far blocks in the
-    # batched pass): operands in registers, the first dataset's sigma
-    from paper_1905_04582_gb300.mds import MDS
-    with MDS(128, 2, "fp32c") as mc:
-        mc.set_sigma(ds[0].sigma)
-        ceil_near = mc.pair_body_ceiling(far=False)
-    print(json.dumps({"batch": True, "order": "caller", "datasets": [w.n for w in ds], "chains_per_dataset": chains,
-                      "strip": b.get_strip(), "ms_per_pass": ms, "pair_evals_per_pass": evals,
-                      "pair_evals_per_s": evals / (ms / 1e3),
-                      "alu": {"achieved_tflops": evals * fp32_ops_per_pair(2) / (ms / 1e3) / 1e12,
-                              "peak_tflops": alu_peak,
-                              "frac": evals * fp32_ops_per_pair(2) / (ms / 1e3) / 1e12 / alu_peak},
-                      "measured_ceiling": {"near_pairs_per_s": ceil_near,
-                                           "frac": evals / (ms / 1e3) / ceil_near},
-                      "hmc_iterations": args.steps, "leapfrog_steps_per_s_all_chains":
-                          args.steps * N_LEAPFROG * len(ds) * chains / wall,
-                      "accept_rate": float(np.mean(acc)), "wall_s": wall}), flush=True)
+    print(json.dumps(dict(batch_entry(args.reps, args.steps), batch=True)), flush=True)
     return 0
 
 
@@ -601,7 +679,8 @@ def run_tree(args):
     y = np.abs(pdist(x_true) + sigma * rng.standard_normal(f.n * (f.n - 1) // 2)).astype(np.float32)
     x_eval = (x_true + 0.02 * rng.standard_normal(x_true.shape)).astype(np.float32)
     stream = torch.cuda.Stream()
-    out = {"tree": True, "n": f.n, "trees": list(W.SUBTYPE_SIZES), "steps": N_LEAPFROG}
+    eps = args.eps if args.eps > 0 else 2e-4
+    out = {"tree": True, "n": f.n, "trees": list(W.SUBTYPE_SIZES), "steps": N_LEAPFROG, "eps": eps}
     for with_tree in (False, True):
         with MDS(f.n, 2, "fp32c", stream=stream) as m:
             m.set_data(y)
@@ -610,11 +689,11 @@ def run_tree(args):
             if with_tree:
                 m.set_tree_prior(f.parent, f.length, f.sigma_mat, f.mu, f.tau0, f.tau_u)
             m.reorder()
-            m.hmc(3, N_LEAPFROG, args.eps, seed=5)
+            m.hmc(3, N_LEAPFROG, eps, seed=5)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             ev0.record(stream)
-            m.hmc_enqueue(args.steps, N_LEAPFROG, args.eps, seed=6)
+            m.hmc_enqueue(args.steps, N_LEAPFROG, eps, seed=6)
             ev1.record(stream)
             acc, _, _ = m.hmc_collect()
             torch.cuda.synchronize()
@@ -784,14 +863,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--eps", type=float, default=2e-4)
+    ap.add_argument("--eps", type=float, default=0.0, help="leapfrog step (0: a short pilot for acceptance ~0.65)")
     ap.add_argument("--cpu-evals", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="leave the scale sweep and the batched case out")
     ap.add_argument("--pass-only", action="store_true", help="time the fused pass alone (profiling runs)")
     ap.add_argument("--n", type=int, default=5392)
     ap.add_argument("--d", type=int, default=2)
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--strip", type=int, default=None)
+    ap.add_argument("--chunks", type=int, default=None, help="chunked pass, chunks per resident CTA slot")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--kernel-hash", action="store_true", help="print the pair kernel's source hash and exit")
     ap.add_argument("--sweep", action="store_true", help="the N = 20000 / 50000 scale sweep (pass only)")
