@@ -65,6 +65,7 @@ extern "C" {
 #define MDS_ERR_TIMEOUT 5     /* a bounded device-side wait gave up */
 #define MDS_ERR_NONFINITE 6   /* a result was NaN/Inf (reported, not hidden) */
 #define MDS_ERR_UNSUPPORTED 7 /* no sm_100-family GPU, or a size beyond the limits */
+#define MDS_ERR_EXCHANGE 8    /* the all-gather of a sharded evaluation failed */
 
 /* mds_create flags: arithmetic of the pair pass. */
 #define MDS_PREC_FP32C 0u /* FP32 per-pair math, compensated FP32 partials reduced in FP64 */
@@ -408,6 +409,47 @@ int mds_problem_size(const mds_ctx *ctx, int64_t *pairs, int64_t *y_bytes);
  * the summation order (results stay within tolerance but not bit-identical). */
 int mds_set_strip(mds_ctx *ctx, int32_t strip);
 int mds_get_strip(const mds_ctx *ctx, int32_t *strip);
+
+/* ------------------------------------------------------------------------
+ * Sharded evaluation over several ranks (section 2.5 of arXiv:1905.04582:
+ * the pairwise sum is split over workers and their partial sums are reduced).
+ *
+ * mds_shard_range: the tiles of the pass (64 x 64 pairs, in row-block
+ * order) cut into n_ranks contiguous ranges of equal pair count to within one
+ * tile; rank `rank` gets tiles [*t0, *t1) (possibly empty for tiny N).  Host
+ * only; needs no device.
+ *
+ * mds_set_shard: make ctx rank `rank` of `n_ranks` (n_ranks 1: no sharding).
+ * Call before mds_set_data: the context then holds only its range's tiles of
+ * Y (about 4 M / n_ranks bytes) and its pair pass covers only them.  Every
+ * evaluation (mds_log_likelihood, mds_gradient, each leapfrog step of
+ * mds_leapfrog / mds_hmc) computes this rank's partials {L_r, dL/dsigma_r,
+ * sum r_r, dL/dX_r} (L_r = -M_r log sigma - sum r over the range's M_r pairs,
+ * so that all four add up over the ranks), hands them to `allgather`, sums
+ * the n_ranks vectors it gets back in rank order (FP64; every rank gets
+ * bitwise the same totals) and takes its leapfrog updates with the total
+ * gradient, so the chains of all ranks stay identical (replicated updates).
+ * allgather(user, send, recv, count, where) must place every rank's `count`
+ * doubles of send into recv (rank-major, n_ranks * count doubles) and return
+ * 0 (nonzero: the evaluation fails with MDS_ERR_EXCHANGE); send and recv are
+ * device memory when where_buffers is MDS_DEVICE (for NCCL), pinned host
+ * memory when MDS_HOST (for host transports); the call is made with the
+ * context's stream synchronised, and recv must be complete when it returns.
+ * count = 3 + N D.  All ranks must make the same sequence of calls (each
+ * evaluation is a collective).  A sharded context uses a fixed pass shape
+ * (no timing autotuner), runs HMC without CUDA graphs, and refuses
+ * mds_reorder, cross-validation folds, the tree prior, sigma updates and the
+ * random-walk sampler (STATE).  Errors: INVALID_ARG (rank, n_ranks, NULL
+ * allgather with n_ranks > 1), STATE (data already set), OOM.
+ *
+ * mds_shard_sum: the fixed-order sum of the exchange on the host:
+ * out[i] = gathered[i] + gathered[count + i] + ... (rank 0 first), the order
+ * the device combine uses. */
+typedef int (*mds_allgather_fn)(void *user, const double *send, double *recv, int64_t count, int32_t where);
+int mds_shard_range(int64_t n, int32_t n_ranks, int32_t rank, int64_t *t0, int64_t *t1);
+int mds_set_shard(mds_ctx *ctx, int32_t n_ranks, int32_t rank, mds_allgather_fn allgather, void *user,
+                  int32_t where_buffers);
+int mds_shard_sum(int32_t n_ranks, int64_t count, const double *gathered, double *out);
 
 /* Shape of the FP32C pair pass (section 2.5 of arXiv:1905.04582: the
  * pairwise transformation split into work units and the partial sums reduced;

@@ -22,6 +22,7 @@ MDS_ERR_OOM = 4
 MDS_ERR_TIMEOUT = 5
 MDS_ERR_NONFINITE = 6
 MDS_ERR_UNSUPPORTED = 7
+MDS_ERR_EXCHANGE = 8
 
 MDS_PREC_FP32C = 0
 MDS_PREC_FP64 = 1
@@ -38,8 +39,12 @@ MDS_PASS_CHUNK_COUNT = 2
 
 STATUS_NAMES = {
     0: "MDS_OK", 1: "MDS_ERR_INVALID_ARG", 2: "MDS_ERR_STATE", 3: "MDS_ERR_CUDA", 4: "MDS_ERR_OOM",
-    5: "MDS_ERR_TIMEOUT", 6: "MDS_ERR_NONFINITE", 7: "MDS_ERR_UNSUPPORTED",
+    5: "MDS_ERR_TIMEOUT", 6: "MDS_ERR_NONFINITE", 7: "MDS_ERR_UNSUPPORTED", 8: "MDS_ERR_EXCHANGE",
 }
+
+# int (*)(void *user, const double *send, double *recv, int64_t count, int32_t where)
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_int32)
 
 
 class mds_hmc_stats(ctypes.Structure):
@@ -98,6 +103,9 @@ SIGNATURES = {
     "mds_set_state": (_int, [_vp, _vp, _i64]),
     "mds_set_strip": (_int, [_vp, _i32]),
     "mds_get_strip": (_int, [_vp, _pi32]),
+    "mds_shard_range": (_int, [_i64, _i32, _i32, _pi64, _pi64]),
+    "mds_set_shard": (_int, [_vp, _i32, _i32, ALLGATHER_FN, _vp, _i32]),
+    "mds_shard_sum": (_int, [_i32, _i64, _vp, _vp]),
     "mds_set_pass_shape": (_int, [_vp, _i32, _i32]),
     "mds_get_pass_shape": (_int, [_vp, _pi32, _pi32, _pi32]),
     "mds_set_pass_stamps": (_int, [_vp, _int]),

@@ -66,6 +66,16 @@ struct mds_ctx {
     unsigned char *far_tile = nullptr;       // [tiles][4] far column pairs of the last chunked pass
     std::vector<float> tile_cost;            // cost model of the chunking (empty: uniform)
     float2 *xcol2 = nullptr;                 // FP32C column layout of the chunked pass
+    // shard (mds_set_shard): this context's pass covers the tiles [shard_t0,
+    // shard_t1) of a pass split over shard_n ranks; Y holds only those tiles
+    int32_t shard_n = 1, shard_rank = 0;
+    int64_t shard_t0 = 0, shard_t1 = 0;      // set to [0, tiles) in create_ctx
+    int64_t shard_pairs = 0;                 // pairs in the range
+    mds_allgather_fn shard_fn = nullptr;
+    void *shard_user = nullptr;
+    int32_t shard_where = MDS_DEVICE;        // memory of the buffers the exchange gets
+    double *shard_send = nullptr, *shard_recv = nullptr;    // device
+    double *shard_hsend = nullptr, *shard_hrecv = nullptr;  // pinned host (exchange on the host)
     bool stamping = false;                   // pass spans measured with %globaltimer
     unsigned long long *stamps = nullptr;    // [2]
     double *pass_ns = nullptr;               // [2]: total ns, passes
@@ -283,11 +293,16 @@ int build_strips(mds_ctx *c, int strip) {
     int32_t slot = 0;
     for (int64_t I = 0; I < nt; ++I) {
         first[I] = slot;
-        for (int64_t j0 = I; j0 < nt; j0 += strip) {
+        // the row block's tiles within this context's range (all of them
+        // unless the context is a shard)
+        const int64_t td = tile_index(I, I, nt);
+        const int64_t jlo = I + std::max<int64_t>(0, c->shard_t0 - td);
+        const int64_t jhi = I + std::min<int64_t>(nt - I, c->shard_t1 - td);
+        for (int64_t j0 = jlo; j0 < jhi; j0 += strip) {
             Strip s;
             s.I = static_cast<int32_t>(I);
             s.j0 = static_cast<int32_t>(j0);
-            s.j1 = static_cast<int32_t>(std::min<int64_t>(nt, j0 + strip));
+            s.j1 = static_cast<int32_t>(std::min<int64_t>(jhi, j0 + strip));
             s.row_slot = slot++;
             v.push_back(s);
         }
@@ -364,22 +379,42 @@ constexpr double kCostFar = 23.0, kCostNear = 36.0, kCostTile = 70.0, kCostSeg =
 // cost (c->tile_cost from the far counts of an earlier chunked pass, else
 // every block counted near), one CTA each.
 int build_chunks(mds_ctx *c, int mult) {
-    const int64_t nt = c->nt, T = c->tiles;
+    // the tiles [T0, T0 + T) of this context (a shard's range, or all)
+    const int64_t nt = c->nt, T0 = c->shard_t0, T = c->shard_t1 - c->shard_t0;
     int per_sm = pair_chunk_blocks_per_sm(c->d);
     if (per_sm < 1) per_sm = 1;
     // mult > 0: chunks per resident CTA slot; mult < 0: exactly -mult chunks
     const int64_t want = mult > 0 ? static_cast<int64_t>(c->sm_count) * per_sm * mult : -static_cast<int64_t>(mult);
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(T, want));
-    const bool have_cost = static_cast<int64_t>(c->tile_cost.size()) == T;
+    if (T <= 0) {
+        // a shard without tiles: no CTA, no partial slot
+        std::vector<int32_t> zero(nt + 1, 0);
+        CU(cudaMemcpyAsync(c->row_first, zero.data(), (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        c->chunks_host.clear();
+        c->n_strips = 0;
+        c->n_scal_parts = 0;
+        c->n_row_slots = 0;
+        c->pass_kind = kPassChunks;
+        c->chunk_mult = mult;
+        c->strip = 0;
+        c->gen++;
+        return MDS_OK;
+    }
+    const bool have_cost = static_cast<int64_t>(c->tile_cost.size()) == c->tiles;
+    // blocks of the first tile of the range
+    int64_t Ib = 0;
+    while (Ib + 1 < nt && tile_index(Ib + 1, Ib + 1, nt) <= T0) ++Ib;
+    const int64_t Jb = Ib + (T0 - tile_index(Ib, Ib, nt));
     std::vector<double> pre(static_cast<size_t>(T) + 1, 0.0);
     {
-        int64_t t = 0;
-        for (int64_t I = 0; I < nt; ++I)
-            for (int64_t J = I; J < nt; ++J, ++t) {
-                double cst = have_cost ? c->tile_cost[t] : kCostTile + 4.0 * 8.0 * kCostNear;
-                if (J == I) cst += kCostSeg;
-                pre[t + 1] = pre[t] + cst;
-            }
+        int64_t I = Ib, J = Jb;
+        for (int64_t t = 0; t < T; ++t) {
+            double cst = have_cost ? c->tile_cost[T0 + t] : kCostTile + 4.0 * 8.0 * kCostNear;
+            if (J == I || t == 0) cst += kCostSeg;
+            pre[t + 1] = pre[t] + cst;
+            if (++J == nt) J = ++I;
+        }
     }
     const double total = pre[T];
     std::vector<int64_t> cut(static_cast<size_t>(G) + 1, 0);
@@ -396,16 +431,16 @@ int build_chunks(mds_ctx *c, int mult) {
     // blocks of every tile boundary, segments, the first segment of each row block
     std::vector<Chunk> v(static_cast<size_t>(G));
     std::vector<int32_t> first(nt + 1, -1);
-    int64_t t = 0, I = 0, J = 0;
+    int64_t t = 0, I = Ib, J = Jb;
     int32_t seg = 0;
     for (int64_t g = 0; g < G; ++g) {
-        while (t < cut[g]) {  // advance (I, J) to tile cut[g]
+        while (t < cut[g]) {  // advance (I, J) to tile cut[g] of the range
             if (++J == nt) J = ++I;
             ++t;
         }
         Chunk ch{};
-        ch.t0 = cut[g];
-        ch.t1 = cut[g + 1];
+        ch.t0 = T0 + cut[g];
+        ch.t1 = T0 + cut[g + 1];
         ch.I0 = static_cast<int32_t>(I);
         ch.J0 = static_cast<int32_t>(J);
         // row block of the last tile: the largest I with tile_index(I, I) <= t1 - 1
@@ -419,8 +454,9 @@ int build_chunks(mds_ctx *c, int mult) {
         v[g] = ch;
     }
     first[nt] = 4 * seg;
-    for (int64_t r = 0; r < nt; ++r)
-        if (first[r] < 0) return fail(c, MDS_ERR_STATE, "chunking left row block %lld without a segment", (long long)r);
+    // row blocks outside the range (a shard) have no slots
+    for (int64_t r = nt - 1; r >= 0; --r)
+        if (first[r] < 0) first[r] = first[r + 1];
     CHECK(ensure_part_buffers(c, static_cast<size_t>(4) * seg, static_cast<size_t>(4 * G), static_cast<size_t>(4 * G)));
     const size_t cb = v.size() * sizeof(Chunk);
     if (cb > c->chunks_bytes) {
@@ -443,6 +479,73 @@ int build_chunks(mds_ctx *c, int mult) {
     c->gen++;
     return MDS_OK;
 }
+
+// Pairs i < j < n of the tiles [t0, t1) (row-block order).
+int64_t range_pairs(int64_t n, int64_t nt, int64_t t0, int64_t t1) {
+    int64_t m = 0;
+    for (int64_t I = 0; I < nt; ++I) {
+        const int64_t td = tile_index(I, I, nt);
+        const int64_t jlo = I + std::max<int64_t>(0, t0 - td);
+        const int64_t jhi = I + std::min<int64_t>(nt - I, t1 - td);
+        const int64_t r = std::min<int64_t>(kTile, n - I * kTile);
+        for (int64_t J = jlo; J < jhi; ++J) {
+            const int64_t cc = std::min<int64_t>(kTile, n - J * kTile);
+            m += J == I ? r * (r - 1) / 2 : r * cc;
+        }
+    }
+    return m;
+}
+
+// The shard ranges: tile boundaries b[0..g] with b[r] the first tile whose
+// prefix of pairs reaches r M / g (so every range holds M / g pairs to within
+// one tile).
+std::vector<int64_t> shard_bounds(int64_t n, int32_t g) {
+    const int64_t nt = (n + kTile - 1) / kTile, T = tile_count(nt);
+    const int64_t M = n * (n - 1) / 2;
+    std::vector<int64_t> b(static_cast<size_t>(g) + 1, T);
+    b[0] = 0;
+    int64_t t = 0, pre = 0;
+    int32_t r = 1;
+    for (int64_t I = 0; I < nt && r < g; ++I) {
+        const int64_t ri = std::min<int64_t>(kTile, n - I * kTile);
+        for (int64_t J = I; J < nt && r < g; ++J) {
+            // before tile t: pre pairs; assign every rank whose target is reached
+            while (r < g && static_cast<long double>(pre) >= static_cast<long double>(M) * r / g) b[r++] = t;
+            const int64_t cc = std::min<int64_t>(kTile, n - J * kTile);
+            pre += J == I ? ri * (ri - 1) / 2 : ri * cc;
+            ++t;
+        }
+    }
+    while (r < g) b[r++] = T;
+    return b;
+}
+
+// One exchange of a sharded evaluation: this rank's partials (the scalars
+// and gradient its reduction just wrote) out, every rank's in, summed in rank
+// order into the scalars and the gradient.
+int shard_exchange(mds_ctx *c, cudaStream_t s) {
+    const int64_t nd = c->n * c->d, count = 3 + nd;
+    cudaError_t e = launch_shard_pack(c->scal, c->grad, c->fp64, nd, c->shard_send, s);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "shard pack: %s", cudaGetErrorString(e));
+    int rc = 0;
+    if (c->shard_where == MDS_DEVICE) {
+        CU(cudaStreamSynchronize(s));
+        rc = c->shard_fn(c->shard_user, c->shard_send, c->shard_recv, count, MDS_DEVICE);
+    } else {
+        CU(cudaMemcpyAsync(c->shard_hsend, c->shard_send, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        rc = c->shard_fn(c->shard_user, c->shard_hsend, c->shard_hrecv, count, MDS_HOST);
+        if (rc == 0)
+            CU(cudaMemcpyAsync(c->shard_recv, c->shard_hrecv, static_cast<size_t>(c->shard_n) * count * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+    }
+    if (rc != 0) return fail(c, MDS_ERR_EXCHANGE, "the all-gather of the shard partials returned %d", rc);
+    e = launch_shard_combine(c->shard_recv, c->shard_n, count, c->scal, c->grad, c->fp64, s);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "shard combine: %s", cudaGetErrorString(e));
+    return MDS_OK;
+}
+
+bool sharded(const mds_ctx *c) { return c->shard_n > 1; }
 
 // Per-tile costs from the far counts of the last chunked pass.
 int read_tile_costs(mds_ctx *c) {
@@ -526,6 +629,7 @@ int set_split_from_xmax(mds_ctx *c) {
 PairArgs pair_args(const mds_ctx *c) {
     PairArgs a{};
     a.y = c->y;
+    a.y_t0 = c->shard_t0;
     a.xrow = c->xrow;
     a.xcol = c->xcol;
     a.x64 = c->fp64 ? static_cast<const double *>(c->x) : nullptr;
@@ -592,7 +696,7 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.sigma = c->sigma;
     r.log_sigma = std::log(c->sigma);
     r.inv_sigma = 1.0 / c->sigma;
-    r.m_pairs = 0.5 * static_cast<double>(c->n) * static_cast<double>(c->n - 1) - static_cast<double>(c->ho_count);
+    r.m_pairs = static_cast<double>(c->shard_pairs) - static_cast<double>(c->ho_count);
     r.lambda = c->lambda;
     r.eps = eps;
     r.grad = static_cast<double *>(c->grad);
@@ -691,6 +795,22 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_na
     if (c->profiling) {
         CHECK(record_prof(c, c->prof_b[pk], s));
         c->prof_used = pk + 1;
+    }
+    if (sharded(c)) {
+        // this rank's partials (an evaluation-mode reduction), the exchange,
+        // then the leapfrog update with the combined gradient
+        ReduceArgs r = reduce_args(c, kModeEval, 0.0);
+        e = launch_reduce(r, s);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(e));
+        CHECK(shard_exchange(c, s));
+        if (mode != kModeEval) {
+            ReduceArgs u = reduce_args(c, mode, eps);
+            u.use_grad = true;
+            u.stamps = nullptr;
+            e = launch_reduce(u, s);
+            if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "update launch: %s", cudaGetErrorString(e));
+        }
+        return MDS_OK;
     }
     ReduceArgs r = reduce_args(c, mode, eps);
     e = launch_reduce(r, s);
@@ -816,6 +936,12 @@ int time_shape(mds_ctx *c, int reps, float *ms) {
 }
 
 int autotune(mds_ctx *c) {
+    if (sharded(c)) {
+        // every rank must make the same passes (each is a collective): a
+        // fixed shape, no timing and no counted pass
+        if (c->fp64 || c->strip_req > 0) return apply_shape(c, kPassStrips, c->strip_req > 0 ? c->strip_req : 2);
+        return apply_shape(c, kPassChunks, c->chunk_req != 0 ? c->chunk_req : 1);
+    }
     if (c->strip_req > 0) return apply_shape(c, kPassStrips, c->strip_req);
     if (c->chunk_req != 0 && !c->fp64) {
         CHECK(apply_shape(c, kPassChunks, c->chunk_req));
@@ -1088,6 +1214,14 @@ int hmc_enqueue(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, 
         CHECK(hmc_spill(c));
         CHECK(ensure_out_cap(c, static_cast<size_t>(n_iter)));
     }
+    if (sharded(c)) {
+        // the exchange is a host call between kernels: iterations run eagerly
+        for (int t = 0; t < n_iter; ++t) {
+            CHECK(enqueue_trajectory(c, n_steps, eps, inj ? 2 : 1, inj ? 2 : 1, 1, seed, c->stream));
+            c->hmc_pending++;
+        }
+        return MDS_OK;
+    }
     // one HMC iteration as a CUDA graph, captured once per configuration
     const auto key = std::make_tuple(c->gen, n_steps, eps, inj ? 2 : 1, c->profiling ? 1 : 0, seed, c->strip);
     if (!c->graph || key != c->graph_key) {
@@ -1343,6 +1477,9 @@ int create_ctx(int64_t n, int32_t d, uint32_t flags, bool alloc_y, mds_ctx **out
     c->nt = (n + kTile - 1) / kTile;
     c->n_pad = c->nt * kTile;
     c->tiles = tile_count(c->nt);
+    c->shard_t0 = 0;
+    c->shard_t1 = c->tiles;
+    c->shard_pairs = n * (n - 1) / 2;
     auto cleanup = [&](int st) {
         g_create_error = c->last_error;
         mds_destroy(c);
@@ -1426,12 +1563,14 @@ int mds_destroy(mds_ctx *c) {
                     c->scal_part, c->strips,  c->row_first, c->scal,     c->counters,  c->err,
                     c->bad,      c->e_start,  c->e_end,     c->stage,    c->p_inj,     c->u_inj,
                     c->acc_out,  c->dh_out,    c->perm_d,    c->inv_d,     c->far_part,  c->chunks,
-                    c->far_tile, c->xcol2,     c->stamps,    c->pass_ns};
+                    c->far_tile, c->xcol2,     c->stamps,    c->pass_ns,   c->shard_send, c->shard_recv};
     for (void *b : bufs) dev_free(b);
     void *ho_bufs[] = {c->ho_off, c->ho_pairs, c->ho_y, c->tile_ho, c->lse_m, c->lse_s, c->lpd_part, c->sigma_draws};
     for (void *b : ho_bufs) dev_free(b);
     for (void *b : c->tree_bufs) dev_free(b);
     if (c->host_stage) cudaFreeHost(c->host_stage);
+    if (c->shard_hsend) cudaFreeHost(c->shard_hsend);
+    if (c->shard_hrecv) cudaFreeHost(c->shard_hrecv);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->tree_stream) {
         cudaStreamSynchronize(c->tree_stream);
@@ -1469,6 +1608,8 @@ int mds_set_data(mds_ctx *c, const void *y, int dtype, int layout, int64_t ld, i
     CU(cudaMemcpyAsync(c->bad, &none, sizeof(none), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     IngestArgs a{};
+    a.t_lo = c->shard_t0;
+    a.t_hi = c->shard_t1;
     a.src_f64 = f64;
     a.packed = layout == MDS_Y_PACKED_UPPER;
     a.ld = ld;
@@ -1486,13 +1627,27 @@ int mds_set_data(mds_ctx *c, const void *y, int dtype, int layout, int64_t ld, i
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "ingest: %s", cudaGetErrorString(e));
     } else {
         // host source: stage groups of row blocks through a device buffer
+        // (a shard uploads only the rows of its tiles' row blocks)
         const int64_t rows_per = kTile * std::max<int64_t>(1, (int64_t(64) << 20) / (kTile * n * eb));
         const size_t stage_bytes = static_cast<size_t>(std::min<int64_t>(rows_per, n)) * n * eb;
+        int64_t row_lo = 0, row_hi = n;
+        if (c->shard_n > 1) {
+            if (c->shard_t1 <= c->shard_t0) {
+                row_hi = 0;
+            } else {
+                int64_t I0 = 0, I1 = 0;
+                while (I0 + 1 < c->nt && tile_index(I0 + 1, I0 + 1, c->nt) <= c->shard_t0) ++I0;
+                I1 = I0;
+                while (I1 + 1 < c->nt && tile_index(I1 + 1, I1 + 1, c->nt) <= c->shard_t1 - 1) ++I1;
+                row_lo = I0 * kTile;
+                row_hi = std::min(n, (I1 + 1) * kTile);
+            }
+        }
         void *stg = nullptr;
         CHECK(dev_alloc(c, &stg, stage_bytes));
         int st = MDS_OK;
-        for (int64_t r0 = 0; r0 < n && st == MDS_OK; r0 += rows_per) {
-            const int64_t r1 = std::min(n, r0 + rows_per);
+        for (int64_t r0 = row_lo; r0 < row_hi && st == MDS_OK; r0 += rows_per) {
+            const int64_t r1 = std::min(row_hi, r0 + rows_per);
             const char *src;
             size_t bytes;
             if (a.packed) {
@@ -1733,6 +1888,7 @@ int mds_hmc_collect(mds_ctx *c, int64_t cap, int32_t *accepted, double *dh, int6
 
 int mds_set_heldout(mds_ctx *c, const int64_t *pairs, int64_t n_pairs) {
     CHECK(check_ctx(c));
+    if (sharded(c)) return fail(c, MDS_ERR_STATE, "cross-validation folds are not available on a sharded context");
     if (n_pairs < 0 || (n_pairs > 0 && !pairs)) return fail(c, MDS_ERR_INVALID_ARG, "need n_pairs >= 0 and pairs");
     if (n_pairs > 0 && !c->have_data) return fail(c, MDS_ERR_STATE, "no data: call mds_set_data first");
     if (c->hmc_pending > 0 || !c->acc_spill.empty())
@@ -1841,6 +1997,7 @@ int mds_get_sigma(const mds_ctx *c, double *sigma) {
 int mds_sigma_mh(mds_ctx *c, int n_iter, double step, double shape, double rate, uint64_t seed, const double *z_all,
                  const double *u_all, int32_t *accepted) {
     CHECK(check_ctx(c));
+    if (sharded(c)) return fail(c, MDS_ERR_STATE, "sigma updates are not available on a sharded context");
     if (n_iter < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_iter must be >= 0");
     if (!(step >= 0.0) || !std::isfinite(step) || !(shape > 0.0) || !(rate > 0.0) || !std::isfinite(shape) ||
         !std::isfinite(rate))
@@ -1995,6 +2152,9 @@ namespace {
 // batch builds its own strip list).
 int reorder_ctx(mds_ctx *c, bool order_strips) {
     CHECK(check_ctx(c));
+    if (sharded(c))
+        return fail(c, MDS_ERR_STATE, "a sharded context holds part of Y and cannot be reordered (permute X and Y "
+                                      "before mds_set_data instead)");
     if (!c->y_owned) return fail(c, MDS_ERR_STATE, "the chains of a batch share Y and cannot be reordered");
     if (!c->have_data || !c->have_x) return fail(c, MDS_ERR_STATE, "mds_reorder needs data and locations");
     if (c->ho_count > 0)
@@ -2094,6 +2254,7 @@ int mds_set_tail_cutoff(mds_ctx *c, double z) {
 int mds_set_tree_prior(mds_ctx *c, int64_t n_nodes, const int64_t *parent, const double *length,
                        const double *sigma_mat, const double *mu, double tau0, double tau_u) {
     CHECK(check_ctx(c));
+    if (sharded(c)) return fail(c, MDS_ERR_STATE, "the tree prior is not available on a sharded context");
     if (c->hmc_pending > 0 || !c->acc_spill.empty())
         return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
     const int64_t n = c->n;
@@ -2293,6 +2454,7 @@ int mds_tree_prior(mds_ctx *c, double *logp, void *grad, int dtype, int where) {
 int mds_rwmh(mds_ctx *c, int n_prop, double step, uint64_t seed, const int64_t *items, const double *z_all,
              const double *u_all, int32_t *accepted, double *dlogpi) {
     CHECK(check_ctx(c));
+    if (sharded(c)) return fail(c, MDS_ERR_STATE, "the random-walk sampler is not available on a sharded context");
     if (n_prop < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_prop must be >= 0");
     if (!(step > 0.0) || !std::isfinite(step)) return fail(c, MDS_ERR_INVALID_ARG, "step must be finite and > 0");
     const bool inj = items || z_all || u_all;
@@ -2513,7 +2675,7 @@ int mds_set_state(mds_ctx *c, const void *buf, int64_t bytes) {
 int mds_problem_size(const mds_ctx *c, int64_t *pairs, int64_t *y_bytes) {
     if (!c) return MDS_ERR_INVALID_ARG;
     if (pairs) *pairs = c->n * (c->n - 1) / 2;
-    if (y_bytes) *y_bytes = c->tiles * kTileElems * static_cast<int64_t>(sizeof(float));
+    if (y_bytes) *y_bytes = (c->shard_t1 - c->shard_t0) * kTileElems * static_cast<int64_t>(sizeof(float));
     return MDS_OK;
 }
 
@@ -2579,6 +2741,85 @@ int mds_set_pass_stamps(mds_ctx *c, int on) {
     CU(cudaStreamSynchronize(c->stream));
     if (c->stamping != (on != 0)) c->gen++;  // captured launches carry the stamp pointers
     c->stamping = on != 0;
+    return MDS_OK;
+}
+
+int mds_shard_range(int64_t n, int32_t n_ranks, int32_t rank, int64_t *t0, int64_t *t1) {
+    if (n < 2 || n_ranks < 1 || rank < 0 || rank >= n_ranks || !t0 || !t1) {
+        set_thread_error("mds_shard_range: need N >= 2, n_ranks >= 1, 0 <= rank < n_ranks, non-NULL t0, t1");
+        return MDS_ERR_INVALID_ARG;
+    }
+    const std::vector<int64_t> b = shard_bounds(n, n_ranks);
+    *t0 = b[rank];
+    *t1 = b[rank + 1];
+    return MDS_OK;
+}
+
+int mds_shard_sum(int32_t n_ranks, int64_t count, const double *gathered, double *out) {
+    if (n_ranks < 1 || count < 0 || (count > 0 && (!gathered || !out))) {
+        set_thread_error("mds_shard_sum: need n_ranks >= 1, count >= 0, non-NULL buffers");
+        return MDS_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        double v = gathered[i];
+        for (int32_t r = 1; r < n_ranks; ++r) v += gathered[static_cast<int64_t>(r) * count + i];
+        out[i] = v;
+    }
+    return MDS_OK;
+}
+
+int mds_set_shard(mds_ctx *c, int32_t n_ranks, int32_t rank, mds_allgather_fn allgather, void *user,
+                  int32_t where_buffers) {
+    CHECK(check_ctx(c));
+    if (n_ranks < 1 || rank < 0 || rank >= n_ranks)
+        return fail(c, MDS_ERR_INVALID_ARG, "need n_ranks >= 1 and 0 <= rank < n_ranks (got %d, %d)", n_ranks, rank);
+    if (n_ranks > 1 && !allgather) return fail(c, MDS_ERR_INVALID_ARG, "allgather must not be NULL for n_ranks > 1");
+    if (where_buffers != MDS_HOST && where_buffers != MDS_DEVICE)
+        return fail(c, MDS_ERR_INVALID_ARG, "where_buffers must be MDS_HOST or MDS_DEVICE");
+    if (c->have_data) return fail(c, MDS_ERR_STATE, "mds_set_shard must precede mds_set_data");
+    if (!c->y_owned) return fail(c, MDS_ERR_STATE, "the chains of a batch cannot be sharded");
+    if (c->reordered || c->ho_count > 0 || c->tree_on)
+        return fail(c, MDS_ERR_STATE, "a reordered context, a fold or a tree prior cannot be sharded");
+    const std::vector<int64_t> b = shard_bounds(c->n, n_ranks);
+    const int64_t t0 = b[rank], t1 = b[rank + 1];
+    // Y for the range only
+    dev_free(c->y);
+    c->y = nullptr;
+    if (t1 > t0) CHECK(dev_alloc_t(c, &c->y, static_cast<size_t>(t1 - t0) * kTileElems * sizeof(float)));
+    // column partials outside the range are never written: zero once
+    CU(cudaMemsetAsync(c->col_part, 0, static_cast<size_t>(c->tiles) * kTile * c->d * elem(c), c->stream));
+    const int64_t count = 3 + c->n * c->d;
+    dev_free(c->shard_send);
+    dev_free(c->shard_recv);
+    c->shard_send = c->shard_recv = nullptr;
+    if (c->shard_hsend) cudaFreeHost(c->shard_hsend);
+    if (c->shard_hrecv) cudaFreeHost(c->shard_hrecv);
+    c->shard_hsend = c->shard_hrecv = nullptr;
+    if (n_ranks > 1) {
+        CHECK(dev_alloc_t(c, &c->shard_send, count * sizeof(double)));
+        CHECK(dev_alloc_t(c, &c->shard_recv, static_cast<size_t>(n_ranks) * count * sizeof(double)));
+        if (where_buffers == MDS_HOST) {
+            if (cudaMallocHost(&c->shard_hsend, count * sizeof(double)) != cudaSuccess ||
+                cudaMallocHost(&c->shard_hrecv, static_cast<size_t>(n_ranks) * count * sizeof(double)) != cudaSuccess)
+                return fail(c, MDS_ERR_OOM, "pinned host buffers of the exchange");
+        }
+    }
+    c->shard_n = n_ranks;
+    c->shard_rank = rank;
+    c->shard_t0 = t0;
+    c->shard_t1 = t1;
+    c->shard_pairs = range_pairs(c->n, c->nt, t0, t1);
+    c->shard_fn = allgather;
+    c->shard_user = user;
+    c->shard_where = where_buffers;
+    c->tile_cost.clear();
+    c->grad_valid = false;
+    // the pass shape over the new range (fixed for shards: see autotune)
+    if (c->fp64 || c->strip_req > 0)
+        CHECK(build_strips(c, c->strip_req > 0 ? c->strip_req : (c->strip > 0 ? c->strip : 2)));
+    else
+        CHECK(build_chunks(c, c->chunk_req != 0 ? c->chunk_req : 1));
+    CU(cudaStreamSynchronize(c->stream));
     return MDS_OK;
 }
 

@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
     // prologue: the first stages' Y quarters (Y is constant) may stream in
     // while the previous kernel drains; locations and partial buffers belong
     // to it until pdl_wait() returns
-    const float *ynext = a.y + ch.t0 * kTileElems + warp * kWarpTileElems;  // Y of the next tile to load
+    const float *ynext = a.y + (ch.t0 - a.y_t0) * kTileElems + warp * kWarpTileElems;  // Y of the next tile to load
     if (lane == 0) {
         for (int s = 0; s < kChunkStages && s < ntile; ++s) {
             mbar_expect_tx(&bars[s], L::kYBytes + L::kXjBytes);

@@ -114,7 +114,8 @@ struct Split {
 
 // Arguments of the fused pair pass.
 struct PairArgs {
-    const float *y;          // tile-packed Y (FP32)
+    const float *y;          // tile-packed Y (FP32): tile t at y + (t - y_t0) * kTileElems
+    int64_t y_t0;            // first tile held (a shard holds only its range; 0 otherwise)
     const float4 *xrow;      // FP32C: row-pair split layout;  FP64: unused
     const float4 *xcol;      // FP32C: column split layout;   FP64: unused
     const double *x64;       // FP64: plain locations [n_pad][D]
@@ -281,6 +282,9 @@ struct ReduceArgs {
     const void *scal_part;
     double part_scale;        // the gradient is part_scale (sum of column partials - sum of row partials):
                               // 1 for the strip passes, -1/sigma^2 for the chunked FP32C pass
+    bool use_grad;            // sharded update: take the gradient from `grad` (all ranks' partials,
+                              // combined) instead of summing partials; the scalar CTA keeps L, sum r
+                              // and dL/dsigma as the combine left them
     unsigned long long *stamps;   // the pass's start / end stamps (PairArgs::stamps), or null: the
     double *pass_ns;              // scalar CTA adds end - start to pass_ns[0], counts pass_ns[1], resets
     const int32_t *row_first_slot;  // [nt + 1]
@@ -510,6 +514,8 @@ cudaError_t launch_rwmh_draws(const RwmhArgs &a, int d, int64_t *items, double *
 // atomicMin) and kErrBadInput is set.
 struct IngestArgs {
     const void *src;
+    int64_t t_lo, t_hi;       // tiles held by the destination (a shard's range; 0, tiles otherwise):
+                              // tile t is written at y + (t - t_lo) * kTileElems, others skipped
     bool src_f64;
     bool packed;
     int64_t ld;               // full layout: row stride (elements)
@@ -558,6 +564,16 @@ cudaError_t launch_lpd_accumulate(const void *x, bool fp64, int d, const int2 *p
 constexpr int kLpdParts = 1024;
 cudaError_t launch_lpd_sum(const double *lse_m, const double *lse_s, int64_t count, double draws, double *part,
                            double *out, cudaStream_t s);
+
+// Sharded evaluation (section 2.5: the pairwise sum split over workers, the
+// partial sums reduced).  pack: this shard's partials {L, dL/dsigma, sum r,
+// gradient [N][D] (item order)} into send (FP64); combine: the n_ranks
+// partial vectors of recv (rank-major, `count` doubles each) summed in rank
+// order into the context's scalars and gradient (FP32C: (hi, lo) pairs).
+cudaError_t launch_shard_pack(const double *scal, const void *grad, bool fp64, int64_t nd, double *send,
+                              cudaStream_t s);
+cudaError_t launch_shard_combine(const double *recv, int n_ranks, int64_t count, double *scal, void *grad, bool fp64,
+                                 cudaStream_t s);
 
 // Set the message mds_last_error(NULL) returns in the calling thread.
 void set_thread_error(const char *fmt, ...);

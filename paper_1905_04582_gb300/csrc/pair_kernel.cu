@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
     const int64_t t0 = tile_index(st.I, st.j0, nt);
 
     // this warp's quarter of the tile and its 16 columns of split locations
-    const float *ysrc0 = a.y + t0 * kTileElems + warp * kWarpTileElems;
+    const float *ysrc0 = a.y + (t0 - a.y_t0) * kTileElems + warp * kWarpTileElems;
     const float4 *xsrc0 = a.xcol + (static_cast<int64_t>(st.j0) * kTile + warp * kWarpCols) * D;
 
     // prologue: the first stages' Y quarters (Y is constant) may stream in
@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
         const bool masked = (J == st.I) || (ragged && J == nt - 1) || (a.tile_ho && a.tile_ho[t0 + jt]);
         const int row_rel = rowbase - J * kTile;
         const int64_t ncv = n - static_cast<int64_t>(J) * kTile;
-        const float4 *ys = reinterpret_cast<const float4 *>(a.y + (t0 + jt) * kTileElems + warp * kWarpTileElems);
+        const float4 *ys =
+            reinterpret_cast<const float4 *>(a.y + (t0 + jt - a.y_t0) * kTileElems + warp * kWarpTileElems);
         double colv[P];
 #pragma unroll
         for (int i = 0; i < P; ++i) colv[i] = 0.0;

@@ -218,6 +218,29 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         a.stamps[1] = 0ull;
     }
 
+    if (Jq < 0 && a.use_grad) {
+        // sharded update: L, sum r and dL/dsigma come from the combine; only
+        // the end of a trajectory's quantum growth is left for this CTA
+        if constexpr (kF32) {
+            if (tid == 0 && mode == kModeHalfKick) {
+                Split sp = *a.xs.split;
+                const float m = __uint_as_float(*a.xs.xmax_bits);
+                int rs = 0;
+                if (m > sp.bound) {
+                    Split ns;
+                    if (choose_split(m, D, ns)) {
+                        sp = ns;
+                        rs = 1;
+                    } else {
+                        atomicOr(a.err, kErrRange);
+                    }
+                }
+                sp.resplit = rs;
+                *a.xs.split = sp;
+            }
+        }
+        return;
+    }
     if (Jq < 0) {
         // scalar partials of all strips -> L, sum r, dL/dsigma (fixed order)
         const T *sp = reinterpret_cast<const T *>(a.scal_part);
@@ -332,7 +355,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     constexpr int kU = D <= 2 ? 8 : D <= 4 ? 4 : 2;
     const T *cp = reinterpret_cast<const T *>(a.col_part);
     const T *rpart = reinterpret_cast<const T *>(a.row_part);
-    for (int q = 0; s + q <= J || s0 + s + q < s1; q += kSplits * kU) {
+    for (int q = 0; !a.use_grad && (s + q <= J || s0 + s + q < s1); q += kSplits * kU) {
         T vc[kU][D], vr[kU][D];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -400,7 +423,13 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         for (int d = 0; d < D; ++d) {
             const Acc g = gsum[d];
             T gv;
-            if constexpr (kF32) {
+            if (a.use_grad) {
+                // the combined gradient of all shards, as the combine stored it
+                if constexpr (kF32)
+                    gv = GradT<T>::value(grad[it * D + d]);
+                else
+                    gv = grad[it * D + d];
+            } else if constexpr (kF32) {
                 if (a.part_scale == 1.0) {
                     grad[it * D + d] = make_float2(g.hi, g.lo);
                     gv = df_float(g);
@@ -732,6 +761,54 @@ __global__ void sigma_draws_kernel(uint64_t seed, uint32_t chain, int64_t iter0,
         default: return cudaErrorInvalidValue;                                              \
     }
 
+// ------------------------------------------------------------- shards
+
+// This shard's partials: {L, dL/dsigma, sum r, gradient} (FP64).
+__global__ void shard_pack_kernel(const double *scal, const void *grad, bool fp64, int64_t nd, double *send) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i0 == 0) {
+        send[0] = scal[kLogLik];
+        send[1] = scal[kDSigma];
+        send[2] = scal[kSumR];
+    }
+    for (int64_t i = i0; i < nd; i += stride) {
+        double v;
+        if (fp64) {
+            v = reinterpret_cast<const double *>(grad)[i];
+        } else {
+            const float2 g = reinterpret_cast<const float2 *>(grad)[i];
+            v = static_cast<double>(g.x) + static_cast<double>(g.y);
+        }
+        send[3 + i] = v;
+    }
+}
+
+// Sum of all ranks' partials in rank order (rank 0 first), FP64, into the
+// scalars and the gradient; the same order on every rank, so every rank
+// holds bitwise the same combined values.
+__global__ void shard_combine_kernel(const double *recv, int n_ranks, int64_t count, double *scal, void *grad,
+                                     bool fp64) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
+        double v = recv[i];
+        for (int r = 1; r < n_ranks; ++r) v += recv[static_cast<int64_t>(r) * count + i];
+        if (i == 0) {
+            scal[kLogLik] = v;
+            scal[kLogLikEnd] = v;
+        } else if (i == 1) {
+            scal[kDSigma] = v;
+        } else if (i == 2) {
+            scal[kSumR] = v;
+        } else if (fp64) {
+            reinterpret_cast<double *>(grad)[i - 3] = v;
+        } else {
+            const float hi = static_cast<float>(v);
+            reinterpret_cast<float2 *>(grad)[i - 3] = make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+        }
+    }
+}
+
 // ----------------------------------------------------------------- ingest
 
 // Inverse of tile_offset(): (row, column) inside a tile of element `off`.
@@ -749,8 +826,9 @@ __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
     const int64_t nt = a.nt;
     const int64_t b0 = a.r0 / kTile;
     const int64_t b1 = (a.r1 + kTile - 1) / kTile;
-    const int64_t t_begin = tile_index(b0, b0, nt);
-    const int64_t t_end = tile_index(b1 - 1, nt - 1, nt) + 1;
+    const int64_t t_begin = max(tile_index(b0, b0, nt), a.t_lo);
+    const int64_t t_end = min(tile_index(b1 - 1, nt - 1, nt) + 1, a.t_hi);
+    if (t_end <= t_begin) return;
     const int64_t total = (t_end - t_begin) * kTileElems;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -758,6 +836,7 @@ __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
         const int off = static_cast<int>(g % kTileElems);
         // row block I is the largest with tile_index(I, I) <= t
         int64_t lo = b0, hi = b1 - 1;
+        if (t < tile_index(b0, b0, nt)) continue;
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) / 2;
             if (tile_index(mid, mid, nt) <= t)
@@ -790,7 +869,7 @@ __global__ void ingest_kernel(const __grid_constant__ IngestArgs a) {
             }
             v = static_cast<float>(y);
         }
-        if (in_rows || i >= a.n) a.y[t * kTileElems + off] = v;  // rows past N: padding of the last block
+        if (in_rows || i >= a.n) a.y[(t - a.t_lo) * kTileElems + off] = v;  // rows past N: padding
     }
 }
 
@@ -976,6 +1055,18 @@ cudaError_t launch_sigma_draws(uint64_t seed, uint32_t chain, int64_t iter0, int
 cudaError_t launch_traj_end_batch(const AcceptArgs *cfg, int n_chains, int64_t max_nd, int d, cudaStream_t s) {
     const dim3 grid(grid_for(max_nd, kTrajThreads), n_chains);
     MDS_SWITCH_DB(traj_end_batch_kernel, grid, kTrajThreads, s, d, cfg)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_pack(const double *scal, const void *grad, bool fp64, int64_t nd, double *send,
+                              cudaStream_t s) {
+    shard_pack_kernel<<<grid_for(nd, 256), 256, 0, s>>>(scal, grad, fp64, nd, send);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_combine(const double *recv, int n_ranks, int64_t count, double *scal, void *grad, bool fp64,
+                                 cudaStream_t s) {
+    shard_combine_kernel<<<grid_for(count, 256), 256, 0, s>>>(recv, n_ranks, count, scal, grad, fp64);
     return cudaGetLastError();
 }
 

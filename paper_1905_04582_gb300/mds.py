@@ -99,6 +99,7 @@ class MDS:
             ptr = stream.cuda_stream
         else:
             ptr = int(stream)
+        self._stream = stream  # the caller's stream object stays alive with the context
         self._check(self._lib.mds_set_stream(self._h, ctypes.c_void_p(ptr)))
 
     def set_data(self, y, layout="packed", ld=None):
@@ -146,6 +147,20 @@ class MDS:
         k, p, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         self._check(self._lib.mds_get_pass_shape(self._h, ctypes.byref(k), ctypes.byref(p), ctypes.byref(g)))
         return k.value, p.value, g.value
+
+    def set_shard(self, n_ranks, rank, allgather, where=capi.MDS_HOST):
+        """Make this context rank `rank` of `n_ranks` of a sharded evaluation
+        (mds_set_shard; before set_data).  allgather(send, recv, count, where)
+        gets raw addresses (ints) of the context's buffers: `count` doubles to
+        send, n_ranks * count doubles to fill in rank order (host memory for
+        MDS_HOST, device memory for MDS_DEVICE); it returns 0 on success."""
+        def _cb(user, send, recv, count, wh):
+            try:
+                return int(allgather(send, recv, count, wh))
+            except Exception:  # an exception must not cross the C boundary
+                return -1
+        self._shard_cb = capi.ALLGATHER_FN(_cb)  # kept alive with the context
+        self._check(self._lib.mds_set_shard(self._h, int(n_ranks), int(rank), self._shard_cb, None, int(where)))
 
     def set_pass_stamps(self, on=True):
         self._check(self._lib.mds_set_pass_stamps(self._h, 1 if on else 0))

@@ -1,10 +1,12 @@
 """The replica aggregation of bench.py over two gloo ranks on the CPU.
 
-The fused pass does not shard (every pair reads every location), so a run on
-N GPUs is N independent replicas: no data-path collective, whole-job
-throughput = all ranks' pairs / the slowest rank's time.  This checks the
-max-over-ranks reduction and the aggregate with unequal per-rank times, and
-that the reference arm's ranks other than 0 exit without work.
+bench.py on N GPUs advances N independent chains, one per rank (replicas:
+no data-path collective; whole-job throughput = all ranks' pairs / the
+slowest rank's time).  The sharded evaluation, which splits one chain's pass
+over ranks with an exchange of partial sums, is tested in test_shard_cpu.py
+and test_shard_gpu.py.  This checks the max-over-ranks reduction and the
+aggregate with unequal per-rank times, and that the reference arm's ranks
+other than 0 exit without work.
 """
 import json
 import os
