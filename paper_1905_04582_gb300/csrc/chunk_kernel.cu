@@ -18,10 +18,11 @@
 //    running across row-block boundaries; at a boundary it writes its row
 //    sums to its own partial slot and goes on.  No CTA barrier runs inside
 //    the loop.
-//  - the row block's split locations are double-buffered in shared memory and
+//  - the row block's split locations sit in three shared-memory buffers
 //    shared by the CTA's warps: the last warp to finish a segment (a count in
-//    shared memory) issues the bulk copy of the segment after next into the
-//    buffer it frees, so the copy lands long before it is needed.
+//    shared memory) issues the bulk copy of the segment three ahead into the
+//    buffer it frees, so even a run of one-tile segments (the last row blocks)
+//    finds its locations landed.
 //  - the gradient weight is summed without its factor -1/sigma^2:
 //    w' = -sigma^2 w = (e - sigma phi'/sqrt(2 pi)) ... (one FMA fewer per
 //    pair); the reduction multiplies the partial sums by -1/sigma^2 in FP64.
@@ -37,6 +38,7 @@ namespace mds {
 namespace {
 
 constexpr int kChunkStages = 3;  // per-warp ring depth
+constexpr int kXisBufs = 3;      // row-block location buffers of a CTA (two segments of lead)
 
 __host__ __device__ constexpr int align128(int b) { return (b + 127) / 128 * 128; }
 
@@ -47,11 +49,11 @@ struct ChunkLayout {
     static constexpr int kStageBytes = align128(kYBytes + kXjBytes);
     static constexpr int kXiBytes = 32 * D * 16;         // a row block: 32 row pairs x D float4
     static constexpr int kXiOffset = kPairWarps * kChunkStages * kStageBytes;
-    static constexpr int kBarOffset = kXiOffset + 2 * align128(kXiBytes);
-    // mbarriers: [warp][stage], then the two row-block buffers
-    static constexpr int kCntOffset = kBarOffset + (kPairWarps * kChunkStages + 2) * 8;
-    // done[2] (warps that finished a segment on each buffer), issued[2] (copies into it)
-    static constexpr int kBoxOffset = kCntOffset + 4 * 4;
+    static constexpr int kBarOffset = kXiOffset + kXisBufs * align128(kXiBytes);
+    // mbarriers: [warp][stage], then the row-block buffers
+    static constexpr int kCntOffset = kBarOffset + (kPairWarps * kChunkStages + kXisBufs) * 8;
+    // done[kXisBufs] (warps that finished a segment on each buffer), issued[kXisBufs] (copies into it)
+    static constexpr int kBoxOffset = kCntOffset + 2 * kXisBufs * 4;
     static constexpr int kBytes = kBoxOffset + kPairWarps * 2 * D * 4;
 };
 
@@ -404,8 +406,11 @@ __device__ __forceinline__ void issue_rows(const PairArgs &a, int I, void *dst, 
     tma_load_1d(dst, a.xrow + static_cast<int64_t>(I) * 32 * D, kB, bar);
 }
 
+// Three CTAs per SM for D <= 2: the register budget (up to 168 per thread)
+// lets the compiler interleave more of a tile's 16 bodies per warp, which
+// measured faster than four CTAs at 128 registers (more warps, less ILP).
 template <int D, bool HELDOUT>
-__global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
+__global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
     pair_chunk_kernel(const __grid_constant__ PairArgs a) {
     using L = ChunkLayout<D>;
     // tall mapping (16 rows x 2 columns per lane) for D <= 2; 8 x 4 beyond,
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBarOffset) + warp * kChunkStages;
     uint64_t *xbar = reinterpret_cast<uint64_t *>(smem + L::kBarOffset) + kPairWarps * kChunkStages;
     unsigned *done = reinterpret_cast<unsigned *>(smem + L::kCntOffset);
-    unsigned *issued = done + 2;
+    unsigned *issued = done + kXisBufs;
     float *box = reinterpret_cast<float *>(smem + L::kBoxOffset) + warp * 2 * D;
     auto xbuf = [&](int b) { return smem + L::kXiOffset + b * align128(L::kXiBytes); };
 
@@ -436,10 +441,12 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
 #pragma unroll
         for (int s = 0; s < kChunkStages; ++s) mbar_init(&bars[s], 1);
         if (warp == 0) {
-            mbar_init(&xbar[0], 1);
-            mbar_init(&xbar[1], 1);
-            done[0] = done[1] = 0u;
-            issued[0] = issued[1] = 0u;
+#pragma unroll
+            for (int b = 0; b < kXisBufs; ++b) {
+                mbar_init(&xbar[b], 1);
+                done[b] = 0u;
+                issued[b] = 0u;
+            }
         }
         fence_mbar_init();
     }
@@ -468,11 +475,9 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
             next_tile(Ip, Jp, nt);
         }
         if (warp == 0) {
-            issued[0] = 1u;
-            issue_rows<D>(a, ch.I0, xbuf(0), &xbar[0]);
-            if (ch.I1 > ch.I0) {
-                issued[1] = 1u;
-                issue_rows<D>(a, ch.I0 + 1, xbuf(1), &xbar[1]);
+            for (int b = 0; b < kXisBufs && ch.I0 + b <= ch.I1; ++b) {
+                issued[b] = 1u;
+                issue_rows<D>(a, ch.I0 + b, xbuf(b), &xbar[b]);
             }
         }
     } else {
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
             if (seg >= 0) {
                 // the previous segment is done: its row sums out, its row
                 // buffer released (the last warp to release it refills it
-                // with the segment after next)
+                // with the segment kXisBufs ahead)
                 float *rp = rowp_base + static_cast<int64_t>(4 * (ch.seg0 + seg) + warp) * kTile * D;
                 if constexpr (kTall)
                     flush_rows_tall<D>(racc, lane, rp);
@@ -519,22 +524,24 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
                     flush_rows<D>(racc, lane, rp);
                 __syncwarp();
                 if (lane == 0) {
-                    const int b = seg & 1;
+                    const int b = seg % kXisBufs;
                     __threadfence_block();
                     const unsigned old = atomicAdd(&done[b], 1u);
-                    if ((old + 1u) % kPairWarps == 0u && ch.I0 + seg + 2 <= ch.I1) {
+                    if ((old + 1u) % kPairWarps == 0u && ch.I0 + seg + kXisBufs <= ch.I1) {
                         fence_proxy_async();
                         issued[b] += 1u;
-                        issue_rows<D>(a, ch.I0 + seg + 2, xbuf(b), &xbar[b]);
+                        issue_rows<D>(a, ch.I0 + seg + kXisBufs, xbuf(b), &xbar[b]);
                     }
                 }
             }
             ++seg;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&xbar[seg & 1], (seg >> 1) & 1, a.err))) {
+            if (!__all_sync(0xffffffffu,
+                            mbar_wait_bounded(&xbar[seg % kXisBufs], static_cast<uint32_t>(seg / kXisBufs) & 1u,
+                                              a.err))) {
                 ok = false;
                 break;
             }
-            xis = reinterpret_cast<const float4 *>(xbuf(seg & 1));
+            xis = reinterpret_cast<const float4 *>(xbuf(seg % kXisBufs));
             float b[2 * D];
             row_box<D>(xis, lane, b);
             if (lane == 0)
@@ -611,7 +618,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2))
                     ph ^= 1u;
                 }
             }
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < kXisBufs; ++b) {
                 const unsigned c = *reinterpret_cast<volatile unsigned *>(&issued[b]);
                 if (c > 0u) mbar_wait_bounded(&xbar[b], (c - 1u) & 1u, a.err);
             }
