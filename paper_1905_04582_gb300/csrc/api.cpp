@@ -686,6 +686,10 @@ ReduceArgs reduce_args(const mds_ctx *c, int mode, double eps) {
     r.perm = c->reordered ? c->perm_d : nullptr;
     r.n_strips = c->n_scal_parts;
     r.part_scale = (!c->fp64 && c->pass_kind == kPassChunks) ? -1.0 / (c->sigma * c->sigma) : 1.0;
+    {
+        const float h = static_cast<float>(r.part_scale);
+        r.part_scale_df = make_float2(h, static_cast<float>(r.part_scale - static_cast<double>(h)));
+    }
     r.stamps = c->stamping ? c->stamps : nullptr;
     r.pass_ns = c->pass_ns;
     r.nt = static_cast<int32_t>(c->nt);

@@ -282,6 +282,7 @@ struct ReduceArgs {
     const void *scal_part;
     double part_scale;        // the gradient is part_scale (sum of column partials - sum of row partials):
                               // 1 for the strip passes, -1/sigma^2 for the chunked FP32C pass
+    float2 part_scale_df;     // part_scale as a double-float (hi, lo) for the FP32C reduction
     bool use_grad;            // sharded update: take the gradient from `grad` (all ranks' partials,
                               // combined) instead of summing partials; the scalar CTA keeps L, sum r
                               // and dL/dsigma as the combine left them

@@ -61,6 +61,18 @@ __device__ __forceinline__ void df_add(DF &a, const DF &b) {
 }
 
 __device__ __forceinline__ float df_float(const DF &a) { return __fadd_rn(a.hi, a.lo); }
+
+// Double-float product a * (b.x + b.y): the exact product of the leading
+// parts by an FMA (Dekker's two-product), the cross terms added to its
+// error, then a fast two-sum (|p| >= |t|) into (hi, lo); relative error
+// about 2^-44, the precision of the double-float sums themselves.
+__device__ __forceinline__ DF df_mul(const DF &a, float2 b) {
+    const float p = __fmul_rn(a.hi, b.x);
+    const float e = __fmaf_rn(a.hi, b.x, -p);
+    const float t = __fmaf_rn(a.hi, b.y, __fmaf_rn(a.lo, b.x, e));
+    const float hi = __fadd_rn(p, t);
+    return DF{hi, __fsub_rn(t, __fsub_rn(hi, p))};
+}
 __device__ __forceinline__ double df_double(const DF &a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
 
 __device__ __forceinline__ DF df_shfl_xor(const DF &a, int o) {
@@ -113,8 +125,8 @@ __device__ __forceinline__ float block_max(float v, float *sm) {
 // ------------------------------------------------------------ locations
 
 // Rewrite slot k, coordinate kk of the FP32C split layouts from value v.
-__device__ __forceinline__ void write_split_slot(const XState &xs, int64_t k, int d, int kk, float v) {
-    const Split sp = *xs.split;
+__device__ __forceinline__ void write_split_slot(const XState &xs, const Split &sp, int64_t k, int d, int kk,
+                                                 float v) {
     const float h = __fsub_rn(__fadd_rn(v, sp.magic), sp.magic);  // nearest multiple of q
     const float l = __fsub_rn(v, h);                               // exact
     float *xr = reinterpret_cast<float *>(xs.xrow + (((k >> 6) * d + kk) * 32 + ((k >> 1) & 31)));
@@ -122,6 +134,10 @@ __device__ __forceinline__ void write_split_slot(const XState &xs, int64_t k, in
     xr[2 + (k & 1)] = l;
     xs.xcol[k * d + kk] = make_float4(-h, -h, -l, -l);
     if (xs.xcol2) xs.xcol2[k * d + kk] = make_float2(-h, -l);
+}
+
+__device__ __forceinline__ void write_split_slot(const XState &xs, int64_t k, int d, int kk, float v) {
+    write_split_slot(xs, *xs.split, k, d, kk, v);
 }
 
 // The same for item `item` (at its slot of the tile layouts).
@@ -136,11 +152,12 @@ __device__ __forceinline__ void store_x(const XState &xs, int64_t k, int d, int 
     if constexpr (std::is_same<T, float>::value) write_split(xs, k, d, kk, v);
 }
 
-// The same, for item k whose slot is known.
+// The same, for item k whose slot is known, with the split quantum in hand.
 template <typename T>
-__device__ __forceinline__ void store_x_at(const XState &xs, int64_t k, int64_t slot, int d, int kk, T v) {
+__device__ __forceinline__ void store_x_at(const XState &xs, const Split &sp, int64_t k, int64_t slot, int d, int kk,
+                                           T v) {
     reinterpret_cast<T *>(xs.x)[k * d + kk] = v;
-    if constexpr (std::is_same<T, float>::value) write_split_slot(xs, slot, d, kk, v);
+    if constexpr (std::is_same<T, float>::value) write_split_slot(xs, sp, slot, d, kk, v);
 }
 
 // Gradient storage: FP32C keeps (hi, lo) float pairs, FP64 doubles.
@@ -197,11 +214,13 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         s0 = a.row_first_slot[Jq / kRedQuarters];
         s1 = a.row_first_slot[Jq / kRedQuarters + 1];
     }
-    // the split's bound changes only at a trajectory's end (not in a
-    // kick-drift launch)
-    float xbound = 0.f;
+    // the split quantum changes only at a trajectory's end (never in a
+    // kick-drift launch): read before the wait, so that writing the split
+    // layouts after it costs no dependent L2 load
+    Split sp_kd{};
     if constexpr (kF32)
-        if (mode == kModeKickDrift) xbound = a.xs.split->bound;
+        if (mode == kModeKickDrift) sp_kd = *a.xs.split;
+    const float xbound = sp_kd.bound;
     // every input (partials, x, p) comes from the pass just before
     pdl_trigger();
     pdl_wait();
@@ -435,11 +454,11 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
                     gv = df_float(g);
                 } else {
                     // partial sums in other units (the chunked pass sums the
-                    // gradient weight times -sigma^2): scaled in FP64
-                    const double v = (static_cast<double>(g.hi) + static_cast<double>(g.lo)) * a.part_scale;
-                    const float hi = static_cast<float>(v);
-                    grad[it * D + d] = make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
-                    gv = hi;
+                    // gradient weight times -sigma^2): scaled as a
+                    // double-float product (FP64 latency is long here)
+                    const DF v = df_mul(g, a.part_scale_df);
+                    grad[it * D + d] = make_float2(v.hi, v.lo);
+                    gv = v.hi;
                 }
             } else {
                 grad[it * D + d] = g;
@@ -454,7 +473,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
                     const T pn = pv0[d] + static_cast<T>(a.eps) * tg;
                     const T xn = xv + static_cast<T>(a.eps) * pn;
                     p[it * D + d] = pn;
-                    store_x_at<T>(a.xs, it, k, D, d, xn);
+                    store_x_at<T>(a.xs, sp_kd, it, k, D, d, xn);
                     // the running max |x| only matters once it passes the
                     // split's bound (the end-of-trajectory reduction then
                     // grows the quantum), so only such values are recorded
