@@ -514,10 +514,15 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
     }
 }
 
+// CTA b reduces quarter-block last - 1 - b: the blocks with the most
+// partials (the last column blocks gather one per row block) start first,
+// which measured faster than the natural order (0.524 against 0.528 ms per
+// HMC iteration at N = 5392).  The scalar CTA is the last one.
 template <typename T, int D>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const __grid_constant__ ReduceArgs a) {
     const int last = a.nt * kRedQuarters;
-    reduce_body<T, D>(a, a.mode, blockIdx.x == static_cast<unsigned>(last) ? -1 : static_cast<int>(blockIdx.x));
+    const int b = static_cast<int>(blockIdx.x);
+    reduce_body<T, D>(a, a.mode, b == last ? -1 : last - 1 - b);
 }
 
 // Batched: job (problem index, quarter-block index J * kReduceQuarters + q,
