@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) pair_batch_kernel(const __gri
                 const float4 *ys = reinterpret_cast<const float4 *>(ybuf + jt * kTileElems + warp * kWarpTileElems);
                 const float4 *xjs =
                     reinterpret_cast<const float4 *>(smem + L.off_xj(b)) + (jt * kTile + warp * kWarpCols) * D;
-                float *colp = ch.col_part + ((t0 + jt) * kTile + warp * kWarpCols) * D;
+                float *colp = ch.col_part + (col_slot(st.I, J) * kTile + warp * kWarpCols) * D;
                 const int row_rel = (st.I - J) * kTile;
                 const int64_t ncv = ds.n - static_cast<int64_t>(J) * kTile;
                 float2 e2 = make_float2(0.f, 0.f), mdv = make_float2(0.f, 0.f), prod = make_float2(1.f, 1.f);

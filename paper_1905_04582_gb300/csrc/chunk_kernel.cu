@@ -500,12 +500,13 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
 
     const int64_t n = a.n;
     const bool ragged = (n % kTile) != 0;
-    float *colp = reinterpret_cast<float *>(a.col_part) + (ch.t0 * kTile + warp * kWarpCols) * D;
+    float *const colp_base = reinterpret_cast<float *>(a.col_part) + warp * kWarpCols * D;
     float *rowp_base = reinterpret_cast<float *>(a.row_part);
     unsigned char *far_tile = a.far_tile ? a.far_tile + ch.t0 * kPairWarps + warp : nullptr;
     bool ok = true;
     int n_far = 0;
     int I = ch.I0, J = ch.J0;
+    int cslot = static_cast<int>(col_slot(I, J));  // column-partial slot of tile (I, J), kept in step
     int seg = -1;
     const float4 *xis = nullptr;
     int stage = 0;
@@ -557,6 +558,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
         const float4 *ys = reinterpret_cast<const float4 *>(sbuf);
         const float2 *xjs = reinterpret_cast<const float2 *>(sbuf + L::kYBytes);
         const bool masked = (J == I) || (ragged && J == nt - 1) || (HELDOUT && a.tile_ho[ch.t0 + k]);
+        float *const colp = colp_base + static_cast<int64_t>(cslot) * (kTile * D);
         float2 e2 = f2(0.f, 0.f), mdv = f2(0.f, 0.f), prod = f2(1.f, 1.f);
         const int row_rel = (I - J) * kTile;
         const int64_t ncv = n - static_cast<int64_t>(J) * kTile;
@@ -594,7 +596,6 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
             stage = 0;
             phase ^= 1u;
         }
-        colp += kTile * D;
         // per-tile sums into the Kahan pairs (packed: e^2 and m' delta together)
         {
             const float2 v = f2(e2.x + e2.y, mdv.x + mdv.y);
@@ -604,6 +605,13 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
             es = tk;
         }
         kahan_add(gs, gc, lg2_approx(prod.x) + lg2_approx(prod.y));
+        // col_slot(I, J + 1) = col_slot(I, J) + J + 1; a new row block
+        // starts at its diagonal tile
+        if (J + 1 < nt) {
+            cslot += J + 1;
+        } else {
+            cslot = (I + 1) * (I + 2) / 2 + I + 1;
+        }
         next_tile(I, J, nt);
     }
     if (!ok) {

@@ -47,6 +47,11 @@ __host__ __device__ inline int64_t tile_index(int64_t I, int64_t J, int64_t nt) 
 
 __host__ __device__ inline int64_t tile_count(int64_t nt) { return nt * (nt + 1) / 2; }
 
+// Slot of tile (I, J), I <= J, in the column partials: column-block-major,
+// so that the partials one column block gathers (one per row block I <= J)
+// are contiguous for the reduction.
+__host__ __device__ inline int64_t col_slot(int64_t I, int64_t J) { return J * (J + 1) / 2 + I; }
+
 // Offset of (r, c) inside a tile (see above).
 __host__ __device__ inline int tile_offset(int r, int c) {
     const int w = c >> 4, b = (c >> 2) & 3, half = (c >> 1) & 1, ec = c & 1;

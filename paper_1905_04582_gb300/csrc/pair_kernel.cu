@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 2 ? 4 : D <= 4 ? 3 : 2)) p
         const int J = st.j0 + jt;
         const bool masked = (J == st.I) || (ragged && J == nt - 1) || (HELDOUT && a.tile_ho[t0 + jt]);
         float2 e2 = f2(0.f, 0.f), mdv = f2(0.f, 0.f), prod = f2(1.f, 1.f);
-        float *colp = colp_base + ((t0 + jt) * kTile + warp * kWarpCols) * D;
+        float *colp = colp_base + (col_slot(st.I, J) * kTile + warp * kWarpCols) * D;
         {
             const int row_rel = rowbase - J * kTile;
             const int64_t ncv = n - static_cast<int64_t>(J) * kTile;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_f64_kernel(const __grid_con
         bool writer;
         const int base = reduced_base<P, 3>(lane, 0, writer);
         constexpr int kHeld = P >= 8 ? P / 8 : 1;
-        double *cp = colp_base + ((t0 + jt) * kTile + warp * kWarpCols + 4 * lb) * D;
+        double *cp = colp_base + (col_slot(st.I, J) * kTile + warp * kWarpCols + 4 * lb) * D;
         if (writer) {
 #pragma unroll
             for (int i = 0; i < kHeld; ++i)

@@ -380,7 +380,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs &a, int mode, int J
         for (int u = 0; u < kU; ++u) {
             const int I = s + q + u * kSplits;
             const int slot = s0 + s + q + u * kSplits;
-            const T *c = cp + (tile_index(I, J, nt) * kTile + r) * D;
+            const T *c = cp + (col_slot(I, J) * kTile + r) * D;
             const T *rp = rpart + (static_cast<int64_t>(slot) * kTile + r) * D;
             load_coords<T, D>(c, I <= J, vc[u]);
             load_coords<T, D>(rp, slot < s1, vr[u]);
