@@ -375,7 +375,10 @@ def batch_entry(reps, steps):
     with MDS(128, 2, "fp32c") as mc:
         mc.set_sigma(ds[0].sigma)
         ceil_near = mc.pair_body_ceiling(far=False)
+    shape = (f"batched strip kernel, {strip} tiles per strip" if strip > 0 else
+             f"every chain's chunked pass (about {-strip} tiles per chunk) as concurrent graph branches")
     return {"datasets": [w.n for w in ds], "chains_per_dataset": chains, "order": "caller", "strip": strip,
+            "shape": shape,
             "ms_per_pass": ms, "pair_evals_per_pass": evals, "pair_evals_per_s": evals / (ms / 1e3),
             "measured_ceiling": {"near_pairs_per_s": ceil_near, "frac": evals / (ms / 1e3) / ceil_near,
                                  "note": "the full per-pair body (Phi evaluated) on register operands"},

@@ -534,10 +534,20 @@ int mds_batch_evaluate(mds_batch *b, double *loglik, double *dlogl_dsigma);
  * Synchronises. */
 int mds_batch_hmc(mds_batch *b, int n_iter, int n_steps, const double *eps, uint64_t seed, int32_t *accepted,
                   double *dh);
-/* Tiles per strip of the batched pass (0: autotune over 1..4 by timing). */
+/* Shape of the batched pass.  strip in [1, 8]: the batched strip kernel,
+ * strip tiles of one row block per CTA, each Y tile loaded into shared memory
+ * once for all chains of its dataset.  strip in [-256, -1]: every chain's own
+ * chunked pass (chunks of about -strip tiles), all chains' passes as
+ * concurrent branches between the same reduction steps; Y is read once per
+ * chain, from L2 where the datasets' Y fit.  0: autotune over both by timing
+ * (strips of 1-4 tiles, chunks of 2-16 tiles).
+ * mds_batch_get_strip returns the shape in use in the same encoding. */
 int mds_batch_set_strip(mds_batch *b, int32_t strip);
 int mds_batch_get_strip(const mds_batch *b, int32_t *strip);
-/* Mean milliseconds of one batched evaluation (pair pass + reduction) over reps. */
+/* Mean milliseconds of one batched evaluation (pair pass + reduction) over
+ * reps, timed as the HMC runs them: reps evaluations captured in one CUDA
+ * graph, launched once to warm up and once timed.  The autotuner (strip 0)
+ * times its candidates the same way. */
 int mds_batch_time_pass(mds_batch *b, int reps, double *ms_per_pass);
 /* Message of the last failed batch call (NULL: last failed mds_batch_create). */
 const char *mds_batch_last_error(const mds_batch *b);

@@ -2897,7 +2897,10 @@ struct mds_batch {
     std::string device_name;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    int32_t strip = 0, strip_req = 0;
+    int32_t strip = 0, strip_req = 0;  // > 0: the batched strip kernel; < 0: per-chain chunked passes
+                                       // of about -strip tiles per chunk
+    cudaEvent_t fork = nullptr;        // per-chain passes: fork from the batch stream ...
+    std::vector<cudaEvent_t> joins;    // ... and join back, one event per chain
     BatchDataset *ds_dev = nullptr;
     BatchChain *ch_dev = nullptr;
     BatchStrip *strips_dev = nullptr;
@@ -2982,8 +2985,14 @@ int batch_tables(mds_batch *b, int strip) {
     const int total = static_cast<int>(b->ctx.size());
     for (mds_ctx *c : b->ctx) {
         CHECK(bpass(b, c, ready(c)));
+        if (strip < 0) {
+            // each chain's own chunked pass: about -strip tiles per chunk
+            const int32_t G = static_cast<int32_t>(std::max<int64_t>(1, c->tiles / (-strip)));
+            if (c->pass_kind != kPassChunks || c->chunk_mult != -G) CHECK(bpass(b, c, build_chunks(c, -G)));
+            continue;
+        }
         c->strip_req = strip;
-        if (c->strip != strip) CHECK(bpass(b, c, build_strips(c, strip)));
+        if (c->pass_kind != kPassStrips || c->strip != strip) CHECK(bpass(b, c, build_strips(c, strip)));
     }
     std::vector<BatchDataset> ds(b->n_data);
     std::vector<BatchChain> ch(total);
@@ -3006,7 +3015,7 @@ int batch_tables(mds_batch *b, int strip) {
         x.c_phi = pa.c_phi;
         x.neg_inv_s2 = pa.neg_inv_s2;
         x.m_coef = pa.m_coef;
-        for (size_t i = 0; i < c0->strips_host.size(); ++i) {
+        for (size_t i = 0; strip > 0 && i < c0->strips_host.size(); ++i) {
             const Strip &s = c0->strips_host[i];
             st.push_back(BatchStrip{dd, s.I, s.j0, s.j1, s.row_slot, static_cast<int32_t>(i)});
         }
@@ -3047,6 +3056,7 @@ int batch_tables(mds_batch *b, int strip) {
     b->n_strips = static_cast<int32_t>(st.size());
     b->n_jobs = static_cast<int32_t>(jobs.size());
     b->strip = strip;
+    if (strip < 0) return MDS_OK;
     const int per_sm = pair_batch_blocks_per_sm(b->d, strip);
     if (per_sm <= 0) return bfail(b, MDS_ERR_CUDA, "batched pass does not fit on an SM (strip %d)", strip);
     b->grid = std::min(b->n_strips, per_sm * b->sm_count);
@@ -3065,7 +3075,21 @@ BatchPairArgs batch_pair_args(const mds_batch *b) {
 }
 
 int batch_enqueue_pass(mds_batch *b, int mode, cudaStream_t s) {
-    cudaError_t e = launch_pair_batch(batch_pair_args(b), b->d, b->grid, s);
+    cudaError_t e = cudaSuccess;
+    if (b->strip < 0) {
+        // every chain's chunked pass on its own stream (graph branches when
+        // captured), all after the work before on s, all before the reduction
+        e = cudaEventRecord(b->fork, s);
+        for (size_t g = 0; e == cudaSuccess && g < b->ctx.size(); ++g) {
+            mds_ctx *c = b->ctx[g];
+            e = cudaStreamWaitEvent(c->cap_stream, b->fork, 0);
+            if (e == cudaSuccess) e = launch_pair_chunks_f32(pair_args(c), static_cast<int>(b->d), c->cap_stream, false, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(b->joins[g], c->cap_stream);
+        }
+        for (size_t g = 0; e == cudaSuccess && g < b->ctx.size(); ++g) e = cudaStreamWaitEvent(s, b->joins[g], 0);
+    } else {
+        e = launch_pair_batch(batch_pair_args(b), b->d, b->grid, s);
+    }
     if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batched pair pass: %s", cudaGetErrorString(e));
     e = launch_reduce_batch(b->rcfg, b->jobs, b->n_jobs, b->d, mode, s);
     if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batched reduction: %s", cudaGetErrorString(e));
@@ -3084,25 +3108,45 @@ std::map<std::tuple<std::string, std::vector<int64_t>, int>, int> g_btune_cache;
 // Batch strip length: forced, cached, or timed over a few candidates.
 int batch_autotune(mds_batch *b) {
     int s = b->strip_req;
-    if (s <= 0) {
+    if (s == 0) {
         const auto key = std::make_tuple(b->device_name, b->n, static_cast<int>(b->d));
         {
             std::lock_guard<std::mutex> lk(g_btune_mu);
             auto it = g_btune_cache.find(key);
             if (it != g_btune_cache.end()) s = it->second;
         }
-        if (s <= 0) {
+        if (s == 0) {
             float best_ms = 1e30f;
-            for (int cand : {1, 2, 3, 4}) {
-                if (pair_batch_blocks_per_sm(b->d, cand) <= 0) continue;
+            // each candidate timed as the HMC runs it: a captured graph of
+            // five passes with their reductions (the per-chain shapes launch
+            // one kernel per chain, which eager launches would slow)
+            for (int cand : {1, 2, 3, 4, -2, -4, -6, -8, -16}) {
+                if (cand > 0 && pair_batch_blocks_per_sm(b->d, cand) <= 0) continue;
                 CHECK(batch_tables(b, cand));
-                for (int w = 0; w < 2; ++w) CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
-                BCU(cudaEventRecord(b->ev0, b->stream));
-                for (int w = 0; w < 5; ++w) CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
-                BCU(cudaEventRecord(b->ev1, b->stream));
-                BCU(cudaEventSynchronize(b->ev1));
+                CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
+                cudaGraph_t g = nullptr;
+                BCU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+                int st = MDS_OK;
+                for (int w = 0; w < 5 && st == MDS_OK; ++w) st = batch_enqueue_pass(b, kModeEval, b->cap_stream);
+                cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+                if (st != MDS_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return st;
+                }
+                if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batch autotune capture: %s", cudaGetErrorString(e));
+                cudaGraphExec_t ge = nullptr;
+                e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batch autotune graph: %s", cudaGetErrorString(e));
                 float ms = 0.f;
-                BCU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+                e = cudaGraphLaunch(ge, b->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(b->ev0, b->stream);
+                if (e == cudaSuccess) e = cudaGraphLaunch(ge, b->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(b->ev1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b->ev1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+                cudaGraphExecDestroy(ge);
+                if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batch autotune timing: %s", cudaGetErrorString(e));
                 if (ms < best_ms) {
                     best_ms = ms;
                     s = cand;
@@ -3176,8 +3220,13 @@ int mds_batch_create(int32_t n_data, const int64_t *n, int32_t d, const int32_t 
     if ((st = bdev_alloc(b, &b->rcfg, total * sizeof(ReduceArgs)))) return cleanup(st);
     if ((st = bdev_alloc(b, &b->tcfg, total * sizeof(TrajArgs)))) return cleanup(st);
     if ((st = bdev_alloc(b, &b->acfg, total * sizeof(AcceptArgs)))) return cleanup(st);
-    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+    bool ev_ok = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreate(&b->ev0) == cudaSuccess && cudaEventCreate(&b->ev1) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    b->joins.assign(b->ctx.size(), nullptr);
+    for (size_t g = 0; ev_ok && g < b->ctx.size(); ++g)
+        ev_ok = cudaEventCreateWithFlags(&b->joins[g], cudaEventDisableTiming) == cudaSuccess;
+    if (!ev_ok) {
         b->last_error = "stream/event creation failed";
         return cleanup(MDS_ERR_CUDA);
     }
@@ -3198,6 +3247,9 @@ int mds_batch_destroy(mds_batch *b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t e : b->joins)
+        if (e) cudaEventDestroy(e);
     delete b;
     return MDS_OK;
 }
@@ -3368,7 +3420,9 @@ int mds_batch_hmc(mds_batch *b, int n_iter, int n_steps, const double *eps, uint
 
 int mds_batch_set_strip(mds_batch *b, int32_t strip) {
     if (!b) return MDS_ERR_INVALID_ARG;
-    if (strip < 0 || strip > 8) return bfail(b, MDS_ERR_INVALID_ARG, "batch strip must be in [0, 8]");
+    if (strip < -256 || strip > 8)
+        return bfail(b, MDS_ERR_INVALID_ARG, "batch strip must be in [1, 8] (strip kernel), [-256, -1] (per-chain "
+                                             "chunked passes of about -strip tiles per chunk) or 0 (autotune)");
     b->strip_req = strip;
     return MDS_OK;
 }
@@ -3384,12 +3438,30 @@ int mds_batch_time_pass(mds_batch *b, int reps, double *ms_per_pass) {
     BCU(cudaSetDevice(b->device));
     CHECK(batch_autotune(b));
     CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
-    BCU(cudaEventRecord(b->ev0, b->stream));
-    for (int r = 0; r < reps; ++r) CHECK(batch_enqueue_pass(b, kModeEval, b->stream));
-    BCU(cudaEventRecord(b->ev1, b->stream));
-    BCU(cudaEventSynchronize(b->ev1));
+    // timed as the HMC runs the passes: `reps` of them in one captured graph
+    cudaGraph_t g = nullptr;
+    BCU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int st = MDS_OK;
+    for (int r = 0; r < reps && st == MDS_OK; ++r) st = batch_enqueue_pass(b, kModeEval, b->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (st != MDS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batch time_pass capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batch time_pass graph: %s", cudaGetErrorString(e));
     float ms = 0.f;
-    BCU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    e = cudaGraphLaunch(ge, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev0, b->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b->ev1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return bfail(b, MDS_ERR_CUDA, "batch time_pass: %s", cudaGetErrorString(e));
     *ms_per_pass = ms / reps;
     for (mds_ctx *c : b->ctx) c->grad_valid = true;
     return batch_check_errors(b, "batch time_pass");

@@ -33,7 +33,7 @@ def build(datasets, chains, strip=None):
     return b, xs
 
 
-@pytest.mark.parametrize("strip", [1, 2, 4])
+@pytest.mark.parametrize("strip", [1, 2, 4, -8, -32])
 def test_batch_evaluate_matches_oracle(strip):
     datasets = [W.custom(300, 2, sigma=0.5, seed=41), W.custom(190, 2, sigma=0.3, seed=42),
                 W.custom(65, 2, sigma=0.7, seed=43)]
@@ -74,12 +74,15 @@ def test_batch_uneven_paper_datasets_sampled():
                 grad_check(b.get_gradient(k, j), g_ref, s_abs, tol["g"], s_sq=s_sq, u=tol["u"])
 
 
-def test_batch_hmc_matches_oracle_with_same_draws():
+@pytest.mark.parametrize("strip", [None, 2, -16])
+def test_batch_hmc_matches_oracle_with_same_draws(strip):
+    """Batched HMC (the strip kernel, or every chain's chunked pass as
+    concurrent graph branches) against the oracle's HMC with the same draws."""
     datasets = [W.custom(220, 2, sigma=0.5, seed=51), W.custom(130, 2, sigma=0.4, seed=52)]
     chains = [2, 2]
     eps = [1e-2, 1.2e-2]
     n_iter, n_steps, seed = 4, 8, 99
-    b, xs = build(datasets, chains)
+    b, xs = build(datasets, chains, strip=strip)
     with b:
         ll0, _ = b.evaluate()
         acc, dh = b.hmc(n_iter, n_steps, eps, seed=seed)
