@@ -361,6 +361,7 @@ def batch_entry(reps, steps):
             b.set_sigma(k, w.sigma)
             for j in range(chains):
                 b.set_locations(k, j, w.x_eval)
+        b.reorder()  # each dataset's locality order, shared by its chains
         ms = b.time_pass(reps)
         evals = sum(w.m for w in ds) * chains
         b.hmc(2, N_LEAPFROG, [5e-4] * len(ds), seed=1)  # warm-up (graph capture)
@@ -377,7 +378,8 @@ def batch_entry(reps, steps):
         ceil_near = mc.pair_body_ceiling(far=False)
     shape = (f"batched strip kernel, {strip} tiles per strip" if strip > 0 else
              f"every chain's chunked pass (about {-strip} tiles per chunk) as concurrent graph branches")
-    return {"datasets": [w.n for w in ds], "chains_per_dataset": chains, "order": "caller", "strip": strip,
+    return {"datasets": [w.n for w in ds], "chains_per_dataset": chains, "order": "locality (mds_batch_reorder)",
+            "strip": strip,
             "shape": shape,
             "ms_per_pass": ms, "pair_evals_per_pass": evals, "pair_evals_per_s": evals / (ms / 1e3),
             "measured_ceiling": {"near_pairs_per_s": ceil_near, "frac": evals / (ms / 1e3) / ceil_near,

@@ -543,6 +543,13 @@ int mds_batch_hmc(mds_batch *b, int n_iter, int n_steps, const double *eps, uint
  * (strips of 1-4 tiles, chunks of 2-16 tiles).
  * mds_batch_get_strip returns the shape in use in the same encoding. */
 int mds_batch_set_strip(mds_batch *b, int32_t strip);
+/* Locality order for every dataset of a batch (as mds_reorder, section 2.5's
+ * blocks of pairs made far enough apart that the Phi terms drop out): the
+ * order is computed from each dataset's first chain, its Y repacked once,
+ * and every chain of the dataset adopts the same slot order.  Every array of
+ * the batch API stays in the caller's item order.  Call after the data and
+ * all chains' locations are set (MDS_ERR_STATE otherwise). */
+int mds_batch_reorder(mds_batch *b);
 int mds_batch_get_strip(const mds_batch *b, int32_t *strip);
 /* Mean milliseconds of one batched evaluation (pair pass + reduction) over
  * reps, timed as the HMC runs them: reps evaluations captured in one CUDA

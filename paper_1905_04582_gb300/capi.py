@@ -124,6 +124,7 @@ SIGNATURES = {
     "mds_batch_evaluate": (_int, [_vp, _vp, _vp]),
     "mds_batch_hmc": (_int, [_vp, _int, _int, _vp, _u64, _vp, _vp]),
     "mds_batch_set_strip": (_int, [_vp, _i32]),
+    "mds_batch_reorder": (_int, [_vp]),
     "mds_batch_get_strip": (_int, [_vp, _pi32]),
     "mds_batch_time_pass": (_int, [_vp, _int, _pdbl]),
     "mds_batch_last_error": (ctypes.c_char_p, [_vp]),

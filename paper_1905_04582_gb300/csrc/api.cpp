@@ -1396,6 +1396,30 @@ int repack_to(mds_ctx *c, const std::vector<int32_t> &order, bool from_identity)
 // Y was just ingested in the caller's order: bring it to the context's slot order.
 int apply_order(mds_ctx *c, const std::vector<int32_t> &order) { return repack_to(c, order, true); }
 
+// A chain of a batch takes the slot order its dataset's first chain chose
+// (their shared Y, already repacked, at y): the order tables, then the split
+// locations rewritten at their new slots.  The state stays in item order.
+int adopt_order(mds_ctx *c, const std::vector<int32_t> &order, const std::vector<int32_t> &inv, float *y) {
+    const int64_t np = c->n_pad;
+    c->y = y;
+    if (!c->perm_d) {
+        CHECK(dev_alloc_t(c, &c->perm_d, np * sizeof(int32_t)));
+        CHECK(dev_alloc_t(c, &c->inv_d, np * sizeof(int32_t)));
+    }
+    CU(cudaMemcpyAsync(c->perm_d, order.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->inv_d, inv.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    c->perm_h = order;
+    c->inv_h = inv;
+    c->reordered = true;
+    c->tile_cost.clear();
+    c->gen++;
+    c->grad_valid = false;
+    cudaError_t e = launch_resplit(xstate(c), np, c->d, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "batch order: %s", cudaGetErrorString(e));
+    return MDS_OK;
+}
+
 }  // namespace
 
 // Recursive bisection: split the range along its widest coordinate (ties
@@ -3268,6 +3292,7 @@ int mds_batch_set_data(mds_batch *b, int32_t dataset, const void *y, int dtype, 
     for (int c = 0; c < b->chains[dataset]; ++c) {
         mds_ctx *x = b->ctx[b->chain0[dataset] + c];
         x->have_data = c0->have_data;
+        x->y = c0->y;  // the first chain may have repacked Y into a new buffer (its slot order)
         x->grad_valid = false;
     }
     return bpass(b, c0, st);
@@ -3424,6 +3449,22 @@ int mds_batch_set_strip(mds_batch *b, int32_t strip) {
         return bfail(b, MDS_ERR_INVALID_ARG, "batch strip must be in [1, 8] (strip kernel), [-256, -1] (per-chain "
                                              "chunked passes of about -strip tiles per chunk) or 0 (autotune)");
     b->strip_req = strip;
+    return MDS_OK;
+}
+
+int mds_batch_reorder(mds_batch *b) {
+    if (!b) return MDS_ERR_INVALID_ARG;
+    BCU(cudaSetDevice(b->device));
+    for (int dd = 0; dd < b->n_data; ++dd) {
+        mds_ctx *c0 = b->ctx[b->chain0[dd]];
+        BCHECK(c0, reorder_ctx(c0, false));
+        for (int j = 1; j < b->chains[dd]; ++j) {
+            mds_ctx *c = b->ctx[b->chain0[dd] + j];
+            if (!c->have_x) return bfail(b, MDS_ERR_STATE, "dataset %d chain %d has no locations", dd, j);
+            BCHECK(c, adopt_order(c, c0->perm_h, c0->inv_h, c0->y));
+        }
+    }
+    b->gen++;
     return MDS_OK;
 }
 

@@ -524,6 +524,11 @@ class Batch:
                                             dh.ctypes.data_as(ctypes.c_void_p)))
         return acc.astype(bool), dh
 
+    def reorder(self):
+        """Locality order for every dataset (mds_batch_reorder); the arrays of
+        the API stay in the caller's order."""
+        self._check(self._lib.mds_batch_reorder(self._h))
+
     def get_strip(self):
         s = ctypes.c_int32()
         self._check(self._lib.mds_batch_get_strip(self._h, ctypes.byref(s)))
