@@ -85,6 +85,8 @@ struct mds_ctx {
     double sigma = 0.0;
     double lambda = 0.0;
     bool have_data = false, have_x = false, have_sigma = false, grad_valid = false;
+    bool eval_unchecked = false;  // a start-point evaluation was queued without a wait (its error
+                                  // bits come back with the next HMC read-back)
     uint64_t gen = 1;         // bumps whenever captured kernel arguments would change
     int start_grid = 0;
 
@@ -1045,6 +1047,30 @@ int evaluate(mds_ctx *c) {
     return MDS_OK;
 }
 
+// The gradient and L at a new start point of HMC, queued ahead of the
+// trajectories without a wait: the evaluation's error bits reach the host
+// with the read-back of the HMC results.  With pass profiling or an injected
+// fault the evaluation waits and checks as a plain evaluation does.
+int queue_start_eval(mds_ctx *c) {
+    CHECK(autotune(c));
+    if (c->grad_valid) return MDS_OK;
+    if (c->profiling || std::getenv("MDS_FAULT")) return evaluate(c);
+    CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
+    CU(cudaGetLastError());
+    c->grad_valid = true;
+    c->eval_unchecked = true;
+    return MDS_OK;
+}
+
+// A queued start-point evaluation followed by no iteration: check it now.
+int finish_start_eval(mds_ctx *c, const char *what) {
+    if (!c->eval_unchecked) return MDS_OK;
+    c->eval_unchecked = false;
+    const int st = check_device_err(c, what);
+    if (st != MDS_OK) c->grad_valid = false;
+    return st;
+}
+
 // src_kind: 0 f32, 1 f64, 2 float2 (hi, lo) pairs
 int copy_out(mds_ctx *c, const void *dev_src, int src_kind, void *dst, int dtype, int where, int64_t count) {
     const bool dst_f64 = dtype == MDS_F64;
@@ -1055,9 +1081,14 @@ int copy_out(mds_ctx *c, const void *dev_src, int src_kind, void *dst, int dtype
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "convert: %s", cudaGetErrorString(e));
         return MDS_OK;
     }
-    cudaError_t e = launch_convert(dev_src, src_kind == 1, c->stage, dst_f64, cnt, c->stream);
-    if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "convert: %s", cudaGetErrorString(e));
-    CU(cudaMemcpyAsync(dst, c->stage, count * eb, cudaMemcpyDeviceToHost, c->stream));
+    if ((src_kind == 0 && !dst_f64) || (src_kind == 1 && dst_f64)) {
+        // same element type: straight to the host
+        CU(cudaMemcpyAsync(dst, dev_src, count * eb, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        cudaError_t e = launch_convert(dev_src, src_kind == 1, c->stage, dst_f64, cnt, c->stream);
+        if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "convert: %s", cudaGetErrorString(e));
+        CU(cudaMemcpyAsync(dst, c->stage, count * eb, cudaMemcpyDeviceToHost, c->stream));
+    }
     CU(cudaStreamSynchronize(c->stream));
     return MDS_OK;
 }
@@ -1315,8 +1346,11 @@ int hmc_collect(mds_ctx *c, int64_t cap, int32_t *accepted, double *dh, int64_t 
         stats->last_dh = hs[kLastDH];
         stats->last_loglik = hs[kLogLik];
     }
+    c->eval_unchecked = false;
     const unsigned h = *he;
     if (h == 0) return MDS_OK;
+    // the start-point evaluation may be the failed step: evaluate afresh next time
+    c->grad_valid = false;
     CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return err_status(c, h, what);
@@ -1731,20 +1765,29 @@ int mds_set_locations(mds_ctx *c, const void *x, int dtype, int where) {
     CHECK(stage_in(c, x, dtype, where, c->n * c->d, &dev));
     CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     if (!c->fp64) {
-        // quantum of the exact-difference split from the incoming values
+        // max |x| of the incoming values; the set_x kernel derives the
+        // quantum of the exact-difference split from it on the device
         CU(cudaMemsetAsync(c->xmax_bits, 0, sizeof(unsigned), c->stream));
         cudaError_t e = launch_xmax(dev, dtype == MDS_F64, c->n * c->d, c->xmax_bits, c->stream);
         if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_locations: %s", cudaGetErrorString(e));
-        CHECK(set_split_from_xmax(c));
     }
     cudaError_t e = launch_set_x(dev, dtype == MDS_F64, c->n, c->n_pad, c->d, c->fp64, xstate(c), c->err, c->stream);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "set_locations: %s", cudaGetErrorString(e));
+    // the one wait of the call: the error word (non-finite entry, range)
     unsigned h = 0;
     CU(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     if (h) {
+        unsigned bits = 0;
+        if (!c->fp64) CU(cudaMemcpyAsync(&bits, c->xmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
         CU(cudaStreamSynchronize(c->stream));
+        if (h & kErrRange) {
+            // nothing was written: the previous locations stay in place
+            float m;
+            std::memcpy(&m, &bits, sizeof(m));
+            return fail(c, MDS_ERR_INVALID_ARG, "locations out of the FP32C range (max |x| = %g)", m);
+        }
         c->have_x = false;
         return fail(c, MDS_ERR_INVALID_ARG, "X has a NaN or Inf entry");
     }
@@ -1862,9 +1905,8 @@ int mds_hmc(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t seed, cons
     if (c->hmc_pending > 0 || !c->acc_spill.empty())
         return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
     CHECK(ready(c));
-    if (!c->grad_valid) CHECK(evaluate(c));
-    CHECK(autotune(c));
-    if (n_iter == 0) return MDS_OK;
+    CHECK(queue_start_eval(c));
+    if (n_iter == 0) return finish_start_eval(c, "hmc");
     const int inj = p_all != nullptr;
     if (inj) {
         const int64_t nd = c->n * c->d;
@@ -1899,9 +1941,8 @@ int mds_hmc_enqueue(mds_ctx *c, int n_iter, int n_steps, double eps, uint64_t se
     if (n_iter < 0 || n_steps < 0) return fail(c, MDS_ERR_INVALID_ARG, "n_iter and n_steps must be >= 0");
     if (!std::isfinite(eps)) return fail(c, MDS_ERR_INVALID_ARG, "eps must be finite");
     CHECK(ready(c));
-    if (!c->grad_valid) CHECK(evaluate(c));
-    CHECK(autotune(c));
-    if (n_iter == 0) return MDS_OK;
+    CHECK(queue_start_eval(c));
+    if (n_iter == 0) return finish_start_eval(c, "hmc");
     return hmc_enqueue(c, n_iter, n_steps, eps, seed, 0);
 }
 

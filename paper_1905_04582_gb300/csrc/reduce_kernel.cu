@@ -937,19 +937,36 @@ __global__ void repack_kernel(const float *old_y, float *new_y, const int32_t *m
 
 // --------------------------------------------------------------- set x
 
+// Locations from the caller.  FP32C: the split quantum follows from max |x|
+// of the incoming values (xmax_kernel ran just before on the same stream);
+// every thread derives the same quantum by the host/device rule
+// (choose_split) and CTA 0 stores it.  Outside the FP32C range nothing is
+// written and the range bit is raised, so the previous state stays intact.
 template <typename T, typename S>
 __global__ void set_x_kernel(const S *src, int64_t n, int64_t n_pad, int d, XState xs, unsigned *err) {
+    Split sp{};
+    if constexpr (std::is_same<T, float>::value) {
+        if (!choose_split(__uint_as_float(*xs.xmax_bits), d, sp)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrRange);
+            return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) *xs.split = sp;
+    }
     const int64_t total = n_pad * d;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t k = e / d;
+        const int kk = static_cast<int>(e % d);
         T v = T(0);
         if (k < n) {
             const double sv = static_cast<double>(src[e]);
             if (!isfinite(sv)) atomicOr(err, kErrBadInput);
             v = static_cast<T>(sv);
         }
-        store_x<T>(xs, k, d, static_cast<int>(e % d), v);
+        if constexpr (std::is_same<T, float>::value)
+            store_x_at<T>(xs, sp, k, xs.inv ? xs.inv[k] : k, d, kk, v);
+        else
+            store_x<T>(xs, k, d, kk, v);
     }
 }
 
