@@ -78,6 +78,11 @@ def pair_kernel_sha256():
     return h.hexdigest()
 
 
+# mds_get_pass_shape kinds: strips, chunks per slot, a chunk count, and the
+# chunks of one CTA per SM run as groups of four warps
+PASS_KINDS = ["strips", "chunks", "chunks", "sm-chunks"]
+
+
 def kernel_traffic(n, d, kind="chunks"):
     """DRAM bytes per launch of the pair pass from the committed ncu capture
     (`key: value` lines), if it was taken on the current kernel source at
@@ -323,7 +328,7 @@ def sweep_entries(reps, order="locality", with_fp64=True):
             kind, param, ctas = m.get_pass_shape()
         gbs = 4.0 * wl.m / (span / 1e3) / 1e9
         e = {"workload": wl.name, "n": n, "d": d, "pairs": wl.m, "y_bytes": 4 * wl.m, "order": order,
-             "pass_shape": {"kind": ["strips", "chunks", "chunks"][kind], "param": param, "ctas": ctas},
+             "pass_shape": {"kind": PASS_KINDS[kind], "param": param, "ctas": ctas},
              "far_fraction": far / total, "pass_span_ms": span, "pass_and_reduction_ms": ms,
              "pairs_per_s": wl.m / (span / 1e3),
              "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
@@ -473,7 +478,7 @@ def run_gpu(args):
     alg_bytes = 4.0 * m_pairs  # one FP32 y_ij per pair per pass
     achieved_gbs = alg_bytes / (span_ms / 1e3) / 1e9
     kind, param, ctas = model.get_pass_shape()
-    kname = ["strips", "chunks", "chunks"][kind]
+    kname = PASS_KINDS[kind]
     chunked = kind != 0
     kernel_name = f"pair_chunk_kernel<{wl.d}>" if chunked else f"pair_f32_kernel<{wl.d}>"
     traffic = kernel_traffic(wl.n, wl.d, kname)

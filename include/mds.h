@@ -459,7 +459,11 @@ int mds_shard_sum(int32_t n_ranks, int64_t count, const double *gathered, double
  * chunks of equal estimated cost, one CTA each (the estimate uses the
  * per-tile counts of pairs whose Phi terms were skipped in an earlier pass);
  * kind MDS_PASS_CHUNK_COUNT: the same with exactly `param` chunks (at most
- * one per tile; param >= 1).
+ * one per tile; param >= 1);
+ * kind MDS_PASS_SM_CHUNKS: the chunks of MDS_PASS_CHUNKS (`param` per
+ * resident slot), with one CTA per SM that runs the SM's slots as groups of
+ * four warps (the CTAs sharing an SM progress unequally, the groups of one
+ * CTA alike).  While a tree prior is set the same chunks run one per CTA.
  * param 0 returns to the autotuner, which times the candidates once per
  * (GPU name, N, D, precision, item order) and keeps the result in memory and
  * in the file named by MDS_TUNE_CACHE (default: tune_cache.txt beside the
@@ -470,6 +474,7 @@ int mds_shard_sum(int32_t n_ranks, int64_t count, const double *gathered, double
 #define MDS_PASS_STRIPS 0
 #define MDS_PASS_CHUNKS 1
 #define MDS_PASS_CHUNK_COUNT 2
+#define MDS_PASS_SM_CHUNKS 3
 int mds_set_pass_shape(mds_ctx *ctx, int32_t kind, int32_t param);
 int mds_get_pass_shape(const mds_ctx *ctx, int32_t *kind, int32_t *param, int32_t *ctas);
 

@@ -36,6 +36,7 @@ MDS_MAX_D = 8
 MDS_PASS_STRIPS = 0
 MDS_PASS_CHUNKS = 1
 MDS_PASS_CHUNK_COUNT = 2
+MDS_PASS_SM_CHUNKS = 3
 
 STATUS_NAMES = {
     0: "MDS_OK", 1: "MDS_ERR_INVALID_ARG", 2: "MDS_ERR_STATE", 3: "MDS_ERR_CUDA", 4: "MDS_ERR_OOM",

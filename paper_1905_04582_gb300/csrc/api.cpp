@@ -32,6 +32,9 @@ thread_local std::string g_create_error = "no error";
 // Shapes of the FP32C pair pass (mds_ctx::pass_kind).
 constexpr int kPassStrips = 0;
 constexpr int kPassChunks = 1;
+// Shape kind of the tuner and of mds_set_pass_shape for the chunked pass in
+// its grouped form (pass_kind kPassChunks with chunk_grouped set).
+constexpr int kPassChunksSM = MDS_PASS_SM_CHUNKS;
 
 struct DevBuf {
     void *ptr = nullptr;
@@ -56,10 +59,14 @@ struct mds_ctx {
     int32_t n_scal_parts = 0; // scalar partial records the pass writes
     int32_t n_row_slots = 0;
     // the FP32C pass's shape: kPassStrips (one CTA per strip of `strip` tiles)
-    // or kPassChunks (one CTA per chunk, chunk_mult chunks per resident CTA slot)
+    // or kPassChunks (chunk_mult chunks per resident chunk slot, one group of
+    // four warps each: one CTA per chunk, or with chunk_grouped one CTA per
+    // SM holding pair_chunk_groups(d) of them)
     int32_t pass_kind = 0;
     int32_t chunk_mult = 0;       // in use (chunked pass)
+    bool chunk_grouped = false;   // in use (chunked pass)
     int32_t chunk_req = 0;        // > 0: chunked pass forced with this multiple
+    bool chunk_grouped_req = false;
     Chunk *chunks = nullptr;
     size_t chunks_bytes = 0;
     std::vector<Chunk> chunks_host;
@@ -380,10 +387,10 @@ constexpr double kCostFar = 23.0, kCostNear = 36.0, kCostTile = 70.0, kCostSeg =
 // G = (SMs x resident CTAs of the pass) x mult chunks of equal estimated
 // cost (c->tile_cost from the far counts of an earlier chunked pass, else
 // every block counted near), one CTA each.
-int build_chunks(mds_ctx *c, int mult) {
+int build_chunks(mds_ctx *c, int mult, bool grouped) {
     // the tiles [T0, T0 + T) of this context (a shard's range, or all)
     const int64_t nt = c->nt, T0 = c->shard_t0, T = c->shard_t1 - c->shard_t0;
-    int per_sm = pair_chunk_blocks_per_sm(c->d);
+    int per_sm = pair_chunk_blocks_per_sm(c->d, grouped);
     if (per_sm < 1) per_sm = 1;
     // mult > 0: chunks per resident CTA slot; mult < 0: exactly -mult chunks
     const int64_t want = mult > 0 ? static_cast<int64_t>(c->sm_count) * per_sm * mult : -static_cast<int64_t>(mult);
@@ -399,6 +406,7 @@ int build_chunks(mds_ctx *c, int mult) {
         c->n_row_slots = 0;
         c->pass_kind = kPassChunks;
         c->chunk_mult = mult;
+        c->chunk_grouped = grouped;
         c->strip = 0;
         c->gen++;
         return MDS_OK;
@@ -477,6 +485,7 @@ int build_chunks(mds_ctx *c, int mult) {
     c->n_row_slots = 4 * seg;
     c->pass_kind = kPassChunks;
     c->chunk_mult = mult;
+    c->chunk_grouped = grouped;
     c->strip = 0;
     c->gen++;
     return MDS_OK;
@@ -574,7 +583,7 @@ int order_strips_by_cost(mds_ctx *c) {
     if (c->pass_kind == kPassChunks) {
         // the chunked pass: cut the tiles again by the measured far counts
         CHECK(read_tile_costs(c));
-        CHECK(build_chunks(c, c->chunk_mult));
+        CHECK(build_chunks(c, c->chunk_mult, c->chunk_grouped));
         c->grad_valid = false;
         return MDS_OK;
     }
@@ -782,7 +791,9 @@ int enqueue_pass(mds_ctx *c, int mode, double eps, cudaStream_t s, bool plant_na
     if (c->fp64)
         e = launch_pair_pass_f64(a, c->d, s, pdl);
     else if (c->pass_kind == kPassChunks)
-        e = launch_pair_chunks_f32(a, c->d, s, pdl, capped ? c->tree_pass_smem : 0);
+        // the grouped form leaves no room for a traversal CTA: with a tree
+        // prior the same chunks run one per CTA
+        e = launch_pair_chunks_f32(a, c->d, s, pdl, capped ? c->tree_pass_smem : 0, c->chunk_grouped && !c->tree_on);
     else
         e = launch_pair_pass_f32(a, c->d, s, pdl, capped ? c->tree_pass_smem : 0);
     if (e != cudaSuccess) return fail(c, MDS_ERR_CUDA, "pair pass launch: %s", cudaGetErrorString(e));
@@ -898,7 +909,7 @@ void tune_load() {
         TuneKey k{fld[0], atoll(fld[1].c_str()), atoi(fld[2].c_str()), fld[3] == "fp64", fld[4] == "locality"};
         TuneVal v{atoi(fld[5].c_str()), atoi(fld[6].c_str()), atof(fld[7].c_str())};
         if ((v.kind == kPassStrips && v.param >= 1 && v.param <= kMaxStrip) ||
-            (v.kind == kPassChunks && v.param >= 1 && v.param <= 8))
+            ((v.kind == kPassChunks || v.kind == kPassChunksSM) && v.param >= 1 && v.param <= 8))
             g_tune_cache[k] = v;
     }
     fclose(f);
@@ -921,8 +932,10 @@ void tune_save() {
 }
 
 int apply_shape(mds_ctx *c, int kind, int param) {
-    if (kind == kPassChunks) {
-        if (c->pass_kind != kPassChunks || c->chunk_mult != param) CHECK(build_chunks(c, param));
+    if (kind == kPassChunks || kind == kPassChunksSM) {
+        const bool grouped = kind == kPassChunksSM;
+        if (c->pass_kind != kPassChunks || c->chunk_mult != param || c->chunk_grouped != grouped)
+            CHECK(build_chunks(c, param, grouped));
     } else if (c->pass_kind != kPassStrips || c->strip != param) {
         CHECK(build_strips(c, param));
     }
@@ -950,13 +963,13 @@ int autotune(mds_ctx *c) {
     }
     if (c->strip_req > 0) return apply_shape(c, kPassStrips, c->strip_req);
     if (c->chunk_req != 0 && !c->fp64) {
-        CHECK(apply_shape(c, kPassChunks, c->chunk_req));
+        CHECK(apply_shape(c, c->chunk_grouped_req ? kPassChunksSM : kPassChunks, c->chunk_req));
         if (c->tile_cost.empty()) {
             // cut by measured costs: one counted pass, then the chunks again
             CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
             CHECK(check_device_err(c, "chunk costs"));
             CHECK(read_tile_costs(c));
-            CHECK(build_chunks(c, c->chunk_req));
+            CHECK(build_chunks(c, c->chunk_req, c->chunk_grouped_req));
         }
         return MDS_OK;
     }
@@ -975,12 +988,12 @@ int autotune(mds_ctx *c) {
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             CHECK(apply_shape(c, it->second.kind, it->second.param));
-            if (it->second.kind == kPassChunks && c->tile_cost.empty()) {
+            if (it->second.kind != kPassStrips && c->tile_cost.empty()) {
                 // cut by measured costs: one counted pass, then the chunks again
                 CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
                 CHECK(check_device_err(c, "autotune"));
                 CHECK(read_tile_costs(c));
-                CHECK(build_chunks(c, it->second.param));
+                CHECK(build_chunks(c, it->second.param, it->second.kind == kPassChunksSM));
             }
             return MDS_OK;
         }
@@ -998,6 +1011,13 @@ int autotune(mds_ctx *c) {
         const int per_sm = std::max(1, pair_chunk_blocks_per_sm(c->d));
         for (int m : {1, 2, 3})
             if (static_cast<int64_t>(c->sm_count) * per_sm * m <= c->tiles || m == 1) cands.emplace_back(kPassChunks, m);
+        // the grouped form (not beside a tree prior's traversal, which it
+        // leaves no room for)
+        const int per_sm_g = pair_chunk_blocks_per_sm(c->d, true);
+        if (!c->tree_on && per_sm_g >= 1)
+            for (int m : {1, 2, 3})
+                if (static_cast<int64_t>(c->sm_count) * per_sm_g * m <= c->tiles || m == 1)
+                    cands.emplace_back(kPassChunksSM, m);
     }
     std::pair<int, int> best = cands[0];
     float best_ms = 1e30f;
@@ -1006,11 +1026,11 @@ int autotune(mds_ctx *c) {
     if (cands.size() > 1) {
         for (const auto &cd : cands) {
             CHECK(apply_shape(c, cd.first, cd.second));
-            if (cd.first == kPassChunks) {
+            if (cd.first != kPassStrips) {
                 // one counted pass, then cut by its far counts
                 CHECK(enqueue_pass(c, kModeEval, 0.0, c->stream));
                 CHECK(read_tile_costs(c));
-                CHECK(build_chunks(c, cd.second));
+                CHECK(build_chunks(c, cd.second, cd.first == kPassChunksSM));
             }
             float ms = 0.f;
             CHECK(time_shape(c, 5, &ms));
@@ -2754,6 +2774,7 @@ int mds_set_strip(mds_ctx *c, int32_t strip) {
     if (strip > kMaxStrip) return fail(c, MDS_ERR_INVALID_ARG, "strip %d exceeds the limit %d", strip, kMaxStrip);
     c->strip_req = strip;
     c->chunk_req = 0;
+    c->chunk_grouped_req = false;
     if (strip > 0) CHECK(apply_shape(c, kPassStrips, strip));
     return MDS_OK;
 }
@@ -2766,25 +2787,29 @@ int mds_get_strip(const mds_ctx *c, int32_t *strip) {
 
 int mds_set_pass_shape(mds_ctx *c, int32_t kind, int32_t param) {
     CHECK(check_ctx(c));
-    if (kind != MDS_PASS_STRIPS && kind != MDS_PASS_CHUNKS && kind != MDS_PASS_CHUNK_COUNT)
-        return fail(c, MDS_ERR_INVALID_ARG, "kind must be MDS_PASS_STRIPS, MDS_PASS_CHUNKS or MDS_PASS_CHUNK_COUNT");
+    if (kind != MDS_PASS_STRIPS && kind != MDS_PASS_CHUNKS && kind != MDS_PASS_CHUNK_COUNT &&
+        kind != MDS_PASS_SM_CHUNKS)
+        return fail(c, MDS_ERR_INVALID_ARG,
+                    "kind must be MDS_PASS_STRIPS, MDS_PASS_CHUNKS, MDS_PASS_CHUNK_COUNT or MDS_PASS_SM_CHUNKS");
     if (param < 0) return fail(c, MDS_ERR_INVALID_ARG, "param must be >= 0");
     if (c->hmc_pending > 0 || !c->acc_spill.empty())
         return fail(c, MDS_ERR_STATE, "queued HMC iterations: collect them first (mds_hmc_collect)");
     if (kind == MDS_PASS_STRIPS) {
         if (param > kMaxStrip) return fail(c, MDS_ERR_INVALID_ARG, "strip %d exceeds the limit %d", param, kMaxStrip);
         c->chunk_req = 0;
+        c->chunk_grouped_req = false;
         c->strip_req = param;
         if (param > 0) CHECK(apply_shape(c, kPassStrips, param));
     } else {
         if (c->fp64) return fail(c, MDS_ERR_INVALID_ARG, "the FP64 context has the strip pass only");
-        if (kind == MDS_PASS_CHUNKS && param > 8)
-            return fail(c, MDS_ERR_INVALID_ARG, "chunks per CTA slot must be <= 8, got %d", param);
+        if ((kind == MDS_PASS_CHUNKS || kind == MDS_PASS_SM_CHUNKS) && param > 8)
+            return fail(c, MDS_ERR_INVALID_ARG, "chunks per slot must be <= 8, got %d", param);
         if (kind == MDS_PASS_CHUNK_COUNT && param == 0)
             return fail(c, MDS_ERR_INVALID_ARG, "MDS_PASS_CHUNK_COUNT needs a chunk count >= 1");
         c->strip_req = 0;
         c->chunk_req = kind == MDS_PASS_CHUNK_COUNT ? -param : param;
-        if (param > 0) CHECK(apply_shape(c, kPassChunks, c->chunk_req));
+        c->chunk_grouped_req = kind == MDS_PASS_SM_CHUNKS && param > 0;
+        if (param > 0) CHECK(apply_shape(c, c->chunk_grouped_req ? kPassChunksSM : kPassChunks, c->chunk_req));
     }
     c->grad_valid = false;
     return MDS_OK;
@@ -2793,9 +2818,15 @@ int mds_set_pass_shape(mds_ctx *c, int32_t kind, int32_t param) {
 int mds_get_pass_shape(const mds_ctx *c, int32_t *kind, int32_t *param, int32_t *ctas) {
     if (!c) return MDS_ERR_INVALID_ARG;
     const bool counted = c->pass_kind == kPassChunks && c->chunk_mult < 0;
-    if (kind) *kind = counted ? MDS_PASS_CHUNK_COUNT : c->pass_kind;
+    const bool grouped = c->pass_kind == kPassChunks && c->chunk_grouped;
+    if (kind) *kind = counted ? MDS_PASS_CHUNK_COUNT : grouped ? MDS_PASS_SM_CHUNKS : c->pass_kind;
     if (param) *param = c->pass_kind == kPassChunks ? (counted ? -c->chunk_mult : c->chunk_mult) : c->strip;
-    if (ctas) *ctas = c->n_strips;
+    if (ctas) {
+        // the grouped form launches one CTA per pair_chunk_groups(d) chunks
+        // (one group alone beside a tree prior)
+        const int g = grouped && !c->tree_on ? pair_chunk_groups(c->d) : 1;
+        *ctas = (c->n_strips + g - 1) / g;
+    }
     return MDS_OK;
 }
 
@@ -2887,7 +2918,7 @@ int mds_set_shard(mds_ctx *c, int32_t n_ranks, int32_t rank, mds_allgather_fn al
     if (c->fp64 || c->strip_req > 0)
         CHECK(build_strips(c, c->strip_req > 0 ? c->strip_req : (c->strip > 0 ? c->strip : 2)));
     else
-        CHECK(build_chunks(c, c->chunk_req != 0 ? c->chunk_req : 1));
+        CHECK(build_chunks(c, c->chunk_req != 0 ? c->chunk_req : 1, false));
     CU(cudaStreamSynchronize(c->stream));
     return MDS_OK;
 }
@@ -3053,7 +3084,8 @@ int batch_tables(mds_batch *b, int strip) {
         if (strip < 0) {
             // each chain's own chunked pass: about -strip tiles per chunk
             const int32_t G = static_cast<int32_t>(std::max<int64_t>(1, c->tiles / (-strip)));
-            if (c->pass_kind != kPassChunks || c->chunk_mult != -G) CHECK(bpass(b, c, build_chunks(c, -G)));
+            if (c->pass_kind != kPassChunks || c->chunk_mult != -G || c->chunk_grouped)
+                CHECK(bpass(b, c, build_chunks(c, -G, false)));
             continue;
         }
         c->strip_req = strip;

@@ -406,29 +406,49 @@ __device__ __forceinline__ void issue_rows(const PairArgs &a, int I, void *dst, 
     tma_load_1d(dst, a.xrow + static_cast<int64_t>(I) * 32 * D, kB, bar);
 }
 
-// Three CTAs per SM for D <= 2: the register budget (up to 168 per thread)
-// lets the compiler interleave more of a tile's 16 bodies per warp, which
-// measured faster than four CTAs at 128 registers (more warps, less ILP).
-template <int D, bool HELDOUT>
-__global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
+// CTAs of the pass that fit one SM: three for D <= 4 (the register budget of
+// up to 168 per thread lets the compiler interleave more of a tile's 16
+// bodies per warp, which measured faster than four CTAs at 128 registers),
+// two beyond.
+template <int D>
+constexpr int chunk_slots_per_sm() {
+    return D <= 4 ? 3 : 2;
+}
+
+// One chunk per group of four warps.  G = 1: one group per CTA, several
+// CTAs per SM.  G = chunk_slots_per_sm<D>(): one CTA per SM whose G groups
+// each run a chunk in their own slice of shared memory.  CTAs that share an
+// SM do not progress alike (the first resident one runs ahead: the three
+// chunks of an SM ended at 12, 15 and 18 us at N = 5392), while the groups of
+// one CTA do (17.6, 17.5, 17.2 us), so the grouped form ends with the SM's
+// work instead of its slowest CTA.  Its groups cannot be replaced one by
+// one, which favours the one-group form when there are several chunks per
+// slot.
+template <int D, bool HELDOUT, int G>
+__global__ void __launch_bounds__(kPairThreads * G, (G > 1 ? 1 : chunk_slots_per_sm<D>()))
     pair_chunk_kernel(const __grid_constant__ PairArgs a) {
     using L = ChunkLayout<D>;
     // tall mapping (16 rows x 2 columns per lane) for D <= 2; 8 x 4 beyond,
     // where 16 rows of row sums would not fit the registers
     constexpr bool kTall = D <= 2;
     constexpr int kRP = kTall ? 8 : 4;  // row pairs per lane
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ __align__(128) unsigned char smem_cta[];
+    // group, warp within it, thread within it, and the group's chunk
+    const int lane = static_cast<int>(threadIdx.x) & 31;
+    const int grp = static_cast<int>(threadIdx.x >> 5) / kPairWarps;
+    const int warp = static_cast<int>(threadIdx.x >> 5) % kPairWarps;
+    const int tid = static_cast<int>(threadIdx.x) % kPairThreads;
+    const unsigned vb = blockIdx.x * G + static_cast<unsigned>(grp);
+    unsigned char *const smem = smem_cta + grp * align128(L::kBytes);
     pdl_trigger();
-    if (blockIdx.x >= static_cast<unsigned>(a.n_strips)) return;
-    const Chunk ch = a.chunks[blockIdx.x];  // the chunk table is fixed between passes
+    const bool active = vb < static_cast<unsigned>(a.n_strips);
+    Chunk ch{};
+    if (active) ch = a.chunks[vb];  // the chunk table is fixed between passes
     const int nt = a.nt;
     const int ntile = static_cast<int>(ch.t1 - ch.t0);
-    if (ntile < 1 || ch.t1 - ch.t0 > 0x7fffffff || ch.I0 < 0 || ch.I0 > ch.J0 || ch.J0 >= nt || ch.I1 < ch.I0 ||
-        ch.I1 >= nt || tile_index(ch.I0, ch.J0, nt) != ch.t0) {
-        if (tid == 0) atomicOr(a.err, kErrBadArgs);
-        return;
-    }
+    const bool bad = active && (ntile < 1 || ch.t1 - ch.t0 > 0x7fffffff || ch.I0 < 0 || ch.I0 > ch.J0 ||
+                                ch.J0 >= nt || ch.I1 < ch.I0 || ch.I1 >= nt || tile_index(ch.I0, ch.J0, nt) != ch.t0);
+    if (bad && tid == 0) atomicOr(a.err, kErrBadArgs);
     unsigned char *ring = smem + warp * kChunkStages * L::kStageBytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBarOffset) + warp * kChunkStages;
     uint64_t *xbar = reinterpret_cast<uint64_t *>(smem + L::kBarOffset) + kPairWarps * kChunkStages;
@@ -450,7 +470,8 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
         }
         fence_mbar_init();
     }
-    __syncthreads();
+    __syncthreads();  // the only CTA-wide barrier: every group passes it before any leaves
+    if (!active || bad) return;
 
     // prologue: the first stages' Y quarters (Y is constant) may stream in
     // while the previous kernel drains; locations and partial buffers belong
@@ -640,7 +661,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
         else
             flush_rows<D>(racc, lane, rp);
     }
-    if (a.far_part && lane == 0) a.far_part[blockIdx.x * kPairWarps + warp] = n_far;
+    if (a.far_part && lane == 0) a.far_part[vb * kPairWarps + warp] = n_far;
     // this warp's scalar sums (lane order fixed)
     float sv[3] = {es.x - ec.x, es.y - ec.y, gs - gc};
 #pragma unroll
@@ -649,7 +670,7 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
         for (int o = 16; o >= 1; o >>= 1) sv[i] += __shfl_xor_sync(0xffffffffu, sv[i], o);
     if (lane == 0) {
         float *sp = reinterpret_cast<float *>(a.scal_part) +
-                    static_cast<int64_t>(blockIdx.x * kPairWarps + warp) * kScalarParts;
+                    static_cast<int64_t>(vb * kPairWarps + warp) * kScalarParts;
         sp[kSumE2] = sv[0];
         sp[kSumMDelta] = sv[1];
         sp[kSumLogPhi] = sv[2];
@@ -659,26 +680,55 @@ __global__ void __launch_bounds__(kPairThreads, (D <= 4 ? 3 : 2))
     }
 }
 
-template <int D>
-cudaError_t launch_d(const PairArgs &a, cudaStream_t s, bool pdl, int smem_min) {
-    using L = ChunkLayout<D>;
-    const int smem = smem_min > L::kBytes ? smem_min : L::kBytes;
-    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false>), smem);
-    if (e == cudaSuccess) e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, true>), smem);
-    if (e != cudaSuccess) return e;
-    if (a.n_strips <= 0) return cudaSuccess;
-    e = a.tile_ho ? launch_maybe_pdl(pdl, pair_chunk_kernel<D, true>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a)
-                  : launch_maybe_pdl(pdl, pair_chunk_kernel<D, false>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a);
-    return e != cudaSuccess ? e : cudaGetLastError();
+// Shared memory of a CTA with G groups.
+template <int D, int G>
+constexpr int chunk_cta_smem() {
+    return G > 1 ? G * align128(ChunkLayout<D>::kBytes) : ChunkLayout<D>::kBytes;
 }
 
 template <int D>
-int blocks_per_sm_d() {
-    using L = ChunkLayout<D>;
-    if (raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false>), L::kBytes) != cudaSuccess)
-        return 0;
+cudaError_t launch_d(const PairArgs &a, cudaStream_t s, bool pdl, int smem_min, bool grouped) {
+    constexpr int G = chunk_slots_per_sm<D>();
+    if (grouped && !a.tile_ho) {
+        // held-out passes keep the one-group form (the chunk table serves both:
+        // the same chunk slots per SM)
+        const int smem = smem_min > chunk_cta_smem<D, G>() ? smem_min : chunk_cta_smem<D, G>();
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, G>), smem);
+        if (e != cudaSuccess) return e;
+        if (a.n_strips <= 0) return cudaSuccess;
+        e = launch_maybe_pdl(pdl, pair_chunk_kernel<D, false, G>, dim3((a.n_strips + G - 1) / G),
+                             dim3(kPairThreads * G), smem, s, a);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    const int smem = smem_min > chunk_cta_smem<D, 1>() ? smem_min : chunk_cta_smem<D, 1>();
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, 1>), smem);
+    if (e == cudaSuccess) e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, true, 1>), smem);
+    if (e != cudaSuccess) return e;
+    if (a.n_strips <= 0) return cudaSuccess;
+    e = a.tile_ho
+            ? launch_maybe_pdl(pdl, pair_chunk_kernel<D, true, 1>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a)
+            : launch_maybe_pdl(pdl, pair_chunk_kernel<D, false, 1>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Chunk slots per SM (groups of four warps that are resident at once): the
+// CTAs per SM of the one-group form, or G per CTA of the grouped form.
+template <int D>
+int blocks_per_sm_d(bool grouped) {
+    constexpr int G = chunk_slots_per_sm<D>();
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_chunk_kernel<D, false>, kPairThreads, L::kBytes) !=
+    if (grouped) {
+        constexpr int smem = chunk_cta_smem<D, G>();
+        if (raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, G>), smem) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_chunk_kernel<D, false, G>, kPairThreads * G,
+                                                          smem) != cudaSuccess)
+            return 0;
+        return nb * G;
+    }
+    constexpr int smem = chunk_cta_smem<D, 1>();
+    if (raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, 1>), smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_chunk_kernel<D, false, 1>, kPairThreads, smem) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -700,30 +750,32 @@ int pair_chunk_smem_bytes(int d) {
     }
 }
 
-int pair_chunk_blocks_per_sm(int d) {
+int pair_chunk_blocks_per_sm(int d, bool grouped) {
     switch (d) {
-        case 1: return blocks_per_sm_d<1>();
-        case 2: return blocks_per_sm_d<2>();
-        case 3: return blocks_per_sm_d<3>();
-        case 4: return blocks_per_sm_d<4>();
-        case 5: return blocks_per_sm_d<5>();
-        case 6: return blocks_per_sm_d<6>();
-        case 7: return blocks_per_sm_d<7>();
-        case 8: return blocks_per_sm_d<8>();
+        case 1: return blocks_per_sm_d<1>(grouped);
+        case 2: return blocks_per_sm_d<2>(grouped);
+        case 3: return blocks_per_sm_d<3>(grouped);
+        case 4: return blocks_per_sm_d<4>(grouped);
+        case 5: return blocks_per_sm_d<5>(grouped);
+        case 6: return blocks_per_sm_d<6>(grouped);
+        case 7: return blocks_per_sm_d<7>(grouped);
+        case 8: return blocks_per_sm_d<8>(grouped);
         default: return 0;
     }
 }
 
-cudaError_t launch_pair_chunks_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl, int smem_min) {
+int pair_chunk_groups(int d) { return d <= 4 ? chunk_slots_per_sm<1>() : chunk_slots_per_sm<8>(); }
+
+cudaError_t launch_pair_chunks_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl, int smem_min, bool grouped) {
     switch (d) {
-        case 1: return launch_d<1>(a, s, pdl, smem_min);
-        case 2: return launch_d<2>(a, s, pdl, smem_min);
-        case 3: return launch_d<3>(a, s, pdl, smem_min);
-        case 4: return launch_d<4>(a, s, pdl, smem_min);
-        case 5: return launch_d<5>(a, s, pdl, smem_min);
-        case 6: return launch_d<6>(a, s, pdl, smem_min);
-        case 7: return launch_d<7>(a, s, pdl, smem_min);
-        case 8: return launch_d<8>(a, s, pdl, smem_min);
+        case 1: return launch_d<1>(a, s, pdl, smem_min, grouped);
+        case 2: return launch_d<2>(a, s, pdl, smem_min, grouped);
+        case 3: return launch_d<3>(a, s, pdl, smem_min, grouped);
+        case 4: return launch_d<4>(a, s, pdl, smem_min, grouped);
+        case 5: return launch_d<5>(a, s, pdl, smem_min, grouped);
+        case 6: return launch_d<6>(a, s, pdl, smem_min, grouped);
+        case 7: return launch_d<7>(a, s, pdl, smem_min, grouped);
+        case 8: return launch_d<8>(a, s, pdl, smem_min, grouped);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -226,9 +226,13 @@ cudaError_t launch_wait_probe(unsigned *err, cudaStream_t s);
 cudaError_t launch_pair_pass_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true, int smem_min = 0);
 // The chunked FP32C pass (chunk_kernel.cu): a.chunks / a.n_strips chunks,
 // one CTA each.
-cudaError_t launch_pair_chunks_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true, int smem_min = 0);
+// grouped: one CTA per SM whose groups of four warps each run a chunk
+// (pair_chunk_groups(d) groups); otherwise one chunk per CTA.
+cudaError_t launch_pair_chunks_f32(const PairArgs &a, int d, cudaStream_t s, bool pdl = true, int smem_min = 0,
+                                   bool grouped = false);
 int pair_chunk_smem_bytes(int d);
-int pair_chunk_blocks_per_sm(int d);
+int pair_chunk_blocks_per_sm(int d, bool grouped = false);  // chunk slots resident per SM
+int pair_chunk_groups(int d);
 int pair_f32_smem_bytes(int d);
 cudaError_t launch_pair_pass_f64(const PairArgs &a, int d, cudaStream_t s, bool pdl = true);
 

@@ -61,9 +61,11 @@ class MDS:
         if strip is not None:
             self.set_strip(strip)
         if chunks is not None:
-            # chunks per resident CTA slot, or ("count", k) for exactly k chunks
+            # chunks per resident CTA slot, ("count", k) for exactly k chunks,
+            # or ("sm", m) for m per slot in the one-CTA-per-SM grouped form
             if isinstance(chunks, tuple):
-                self.set_pass_shape(capi.MDS_PASS_CHUNK_COUNT, chunks[1])
+                kind = {"count": capi.MDS_PASS_CHUNK_COUNT, "sm": capi.MDS_PASS_SM_CHUNKS}[chunks[0]]
+                self.set_pass_shape(kind, chunks[1])
             else:
                 self.set_pass_shape(capi.MDS_PASS_CHUNKS, chunks)
         if stream is not None:
@@ -137,9 +139,11 @@ class MDS:
         return s.value
 
     def set_pass_shape(self, kind, param):
-        """kind capi.MDS_PASS_STRIPS (param: tiles per strip) or
-        capi.MDS_PASS_CHUNKS (param: chunks per resident CTA slot); param 0
-        returns to the autotuner (mds_set_pass_shape)."""
+        """kind capi.MDS_PASS_STRIPS (param: tiles per strip),
+        capi.MDS_PASS_CHUNKS (param: chunks per resident CTA slot),
+        capi.MDS_PASS_CHUNK_COUNT (param: chunks) or capi.MDS_PASS_SM_CHUNKS
+        (param: chunks per slot, one CTA per SM running its slots as groups);
+        param 0 returns to the autotuner (mds_set_pass_shape)."""
         self._check(self._lib.mds_set_pass_shape(self._h, int(kind), int(param)))
 
     def get_pass_shape(self):

@@ -4,7 +4,9 @@ sizes with ragged tails and several dimensions, with chunks that hold one
 tile, several row blocks, or a whole problem (segments that start and end
 inside a chunk), in the caller's order and in the locality order (far
 blocks, measured-cost cuts), at the paper-scale size, with a
-cross-validation fold, along HMC trajectories, and the pass-span stamps."""
+cross-validation fold, along HMC trajectories, and the pass-span stamps;
+the same in the grouped form (one CTA per SM whose groups of four warps run
+the chunks), which sums in the same order as the one-group form."""
 import math
 
 import numpy as np
@@ -37,18 +39,18 @@ SIZES = [(2, 2), (3, 1), (65, 3), (130, 2), (333, 6), (700, 2), (257, 8), (129, 
 
 
 @pytest.mark.parametrize("n,d", SIZES)
-@pytest.mark.parametrize("chunks", [("count", 1), ("count", 3), ("count", 7), 1])
+@pytest.mark.parametrize("chunks", [("count", 1), ("count", 3), ("count", 7), 1, ("sm", 1)])
 def test_chunked_parity_small_sizes(n, d, chunks):
     wl = W.custom(n, d, sigma=0.5, seed=100 + n + d)
     with chunked(wl, chunks) as m:
         kind, param, ctas = m.get_pass_shape()
-        assert kind in (capi.MDS_PASS_CHUNKS, capi.MDS_PASS_CHUNK_COUNT)
+        assert kind in (capi.MDS_PASS_CHUNKS, capi.MDS_PASS_CHUNK_COUNT, capi.MDS_PASS_SM_CHUNKS)
         info = compare(m, wl, "fp32c")
     print(n, d, chunks, ctas, info)
 
 
 @pytest.mark.parametrize("n,d", [(700, 2), (1000, 3), (333, 6), (2000, 2)])
-@pytest.mark.parametrize("chunks", [("count", 5), 1])
+@pytest.mark.parametrize("chunks", [("count", 5), 1, ("sm", 1), ("sm", 2)])
 def test_chunked_parity_locality_order(n, d, chunks):
     wl = W.custom(n, d, sigma=0.25, seed=900 + n + d, mixture=(5, 0.3))
     with chunked(wl, chunks, reorder=True) as m:
@@ -64,7 +66,7 @@ def paper_workload():
 
 
 @pytest.mark.parametrize("reorder", [False, True])
-@pytest.mark.parametrize("chunks", [1, 2])
+@pytest.mark.parametrize("chunks", [1, 2, ("sm", 1)])
 def test_chunked_parity_paper_scale(paper_workload, reorder, chunks):
     wl, ref = paper_workload
     with chunked(wl, chunks, reorder=reorder) as m:
@@ -91,22 +93,24 @@ def test_chunked_and_strip_passes_agree_and_repeat():
 
 
 @pytest.mark.parametrize("n,d,k", [(200, 2, 400), (700, 2, 5000), (257, 3, 50)])
-def test_chunked_fold_matches_oracle(n, d, k):
+@pytest.mark.parametrize("chunks", [("count", 4), ("sm", 1)])
+def test_chunked_fold_matches_oracle(n, d, k, chunks):
     wl = W.custom(n, d, sigma=0.5, seed=500 + n)
     fold = make_fold(n, k, n)
-    with chunked(wl, ("count", 4)) as m:
+    with chunked(wl, chunks) as m:
         m.set_heldout(fold)
         check_fold(m, wl, "fp32c", fold)
 
 
 @pytest.mark.parametrize("eps", [1.5e-2, 3.5e-2])
-def test_chunked_hmc_injected_draws_match_oracle(eps):
+@pytest.mark.parametrize("chunks", [("count", 3), ("sm", 1)])
+def test_chunked_hmc_injected_draws_match_oracle(eps, chunks):
     wl = W.small()
     n_iter, n_steps = 10, 10
     p_all, u_all = W.momenta(22, n_iter, wl.n, wl.d)
     x64 = wl.x_eval.astype(np.float64)
     xr, acc_r, dh_r = oracle.hmc(wl.y_packed, x64, wl.sigma, eps, n_steps, p_all, u_all)
-    with chunked(wl, ("count", 3)) as m:
+    with chunked(wl, chunks) as m:
         ll0, _ = m.log_likelihood()
         acc, dh, stats = m.hmc(n_iter, n_steps, eps, p_all=p_all, u_all=u_all)
         x = m.get_locations()
@@ -139,14 +143,37 @@ def test_pass_shape_arguments():
     from paper_1905_04582_gb300.mds import MDS
     with MDS(wl.n, wl.d, "fp32c") as m, MDS(wl.n, wl.d, "fp64") as m64:
         for kind, param in ((7, 1), (capi.MDS_PASS_STRIPS, -1), (capi.MDS_PASS_CHUNKS, 9),
-                            (capi.MDS_PASS_CHUNK_COUNT, 0)):
+                            (capi.MDS_PASS_CHUNK_COUNT, 0), (capi.MDS_PASS_SM_CHUNKS, 9)):
             with pytest.raises(MDSError) as ei:
                 m.set_pass_shape(kind, param)
             assert ei.value.status == MDS_ERR_INVALID_ARG
-        with pytest.raises(MDSError) as ei:
-            m64.set_pass_shape(capi.MDS_PASS_CHUNKS, 1)
-        assert ei.value.status == MDS_ERR_INVALID_ARG
+        for kind in (capi.MDS_PASS_CHUNKS, capi.MDS_PASS_SM_CHUNKS):
+            with pytest.raises(MDSError) as ei:
+                m64.set_pass_shape(kind, 1)
+            assert ei.value.status == MDS_ERR_INVALID_ARG
+        # 300 items: 5 row blocks, 15 tiles, one chunk each; the grouped form
+        # runs them as groups of CTAs that each hold one SM's chunk slots
+        m.set_pass_shape(capi.MDS_PASS_SM_CHUNKS, 1)
+        kind, param, ctas = m.get_pass_shape()
+        assert (kind, param) == (capi.MDS_PASS_SM_CHUNKS, 1)
+        assert 1 <= ctas <= 15, ctas
         m.set_pass_shape(capi.MDS_PASS_CHUNK_COUNT, 4)
         assert m.get_pass_shape() == (capi.MDS_PASS_CHUNK_COUNT, 4, 4)
         m.set_pass_shape(capi.MDS_PASS_STRIPS, 2)
         assert m.get_pass_shape()[:2] == (capi.MDS_PASS_STRIPS, 2)
+
+
+@pytest.mark.parametrize("n,d", [(700, 2), (1000, 3), (333, 6), (5392, 2)])
+def test_grouped_form_sums_in_the_one_group_order(n, d):
+    """The grouped form runs the chunks of the one-group form (the same chunk
+    slots per SM, so the same cut) with each group writing its chunk's
+    partial slots: the results are bitwise those of the one-group form."""
+    wl = W.paper_scale() if n == 5392 else W.custom(n, d, sigma=0.3, seed=40 + n, mixture=(5, 0.3))
+    with chunked(wl, 1, reorder=True) as a, chunked(wl, ("sm", 1), reorder=True) as b:
+        la, ga, da = a.gradient()
+        lb, gb, db = b.gradient()
+        ka, kb = a.get_pass_shape(), b.get_pass_shape()
+        assert ka[0] == capi.MDS_PASS_CHUNKS and kb[0] == capi.MDS_PASS_SM_CHUNKS
+        assert kb[2] < ka[2], (ka, kb)  # fewer, larger CTAs
+    assert la == lb and da == db, (la, lb, da, db)
+    assert np.array_equal(ga, gb)
