@@ -628,7 +628,8 @@ def run_pass_only(args):
         wl = W.paper_scale(d=args.d)
     else:
         wl = W.make(f"mixture N={args.n} D={args.d}", args.n, args.d, 0.3, 5, 0.3, mixture=(6, 0.3))
-    with MDS(wl.n, wl.d, args.precision, strip=args.strip, chunks=args.chunks) as m:
+    chunks = ("sm", args.sm_chunks) if args.sm_chunks else args.chunks
+    with MDS(wl.n, wl.d, args.precision, strip=args.strip, chunks=chunks) as m:
         m.set_data(wl.y_packed)
         m.set_locations(wl.x_eval)
         m.set_sigma(wl.sigma)
@@ -883,6 +884,8 @@ def main():
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--strip", type=int, default=None)
     ap.add_argument("--chunks", type=int, default=None, help="chunked pass, chunks per resident CTA slot")
+    ap.add_argument("--sm-chunks", type=int, default=None,
+                    help="chunked pass in its grouped form (one CTA per SM), chunks per slot")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--kernel-hash", action="store_true", help="print the pair kernel's source hash and exit")
     ap.add_argument("--sweep", action="store_true", help="the N = 20000 / 50000 scale sweep (pass only)")

@@ -426,17 +426,35 @@ int build_chunks(mds_ctx *c, int mult, bool grouped) {
             if (++J == nt) J = ++I;
         }
     }
-    const double total = pre[T];
+    // out[0 .. parts]: the boundaries of `parts` pieces of [lo, hi) of equal
+    // estimated cost, each of at least min_tiles tiles
+    auto cut_range = [&](int64_t lo, int64_t hi, int64_t parts, int64_t min_tiles, int64_t *out) {
+        out[0] = lo;
+        out[parts] = hi;
+        const double c0 = pre[lo], span = pre[hi] - pre[lo];
+        for (int64_t g = 1; g < parts; ++g) {
+            const double target = c0 + span * static_cast<double>(g) / static_cast<double>(parts);
+            // first tile boundary whose prefix reaches the target
+            int64_t b = std::lower_bound(pre.begin() + lo, pre.begin() + hi + 1, target) - pre.begin();
+            if (b > lo && target - pre[b - 1] < pre[b] - target) --b;
+            b = std::max(b, out[g - 1] + min_tiles);
+            b = std::min(b, hi - min_tiles * (parts - g));
+            out[g] = b;
+        }
+    };
     std::vector<int64_t> cut(static_cast<size_t>(G) + 1, 0);
-    cut[G] = T;
-    for (int64_t g = 1; g < G; ++g) {
-        const double target = total * static_cast<double>(g) / static_cast<double>(G);
-        // first tile boundary whose prefix reaches the target
-        int64_t b = std::lower_bound(pre.begin(), pre.end(), target) - pre.begin();
-        if (b > 0 && target - pre[b - 1] < pre[b] - target) --b;
-        b = std::max(b, cut[g - 1] + 1);
-        b = std::min(b, T - (G - g));
-        cut[g] = b;
+    const int64_t groups = grouped ? pair_chunk_groups(c->d) : 1;
+    if (groups > 1 && G % groups == 0 && T >= G) {
+        // the grouped form: each SM's total decides the end of the pass (its
+        // groups share it), so equal-cost pieces per CTA first, where a tile
+        // is a smaller part of the share than of one chunk, then each piece
+        // into its groups' chunks
+        const int64_t P = G / groups;
+        std::vector<int64_t> piece(static_cast<size_t>(P) + 1, 0);
+        cut_range(0, T, P, groups, piece.data());
+        for (int64_t p = 0; p < P; ++p) cut_range(piece[p], piece[p + 1], groups, 1, cut.data() + p * groups);
+    } else {
+        cut_range(0, T, G, 1, cut.data());
     }
     // blocks of every tile boundary, segments, the first segment of each row block
     std::vector<Chunk> v(static_cast<size_t>(G));
