@@ -137,11 +137,13 @@ def _tree_workload(n_sizes, lone, seed):
     return f, y, x_eval, sigma
 
 
-@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+@pytest.mark.parametrize("prec,chunks", [("fp32c", None), ("fp64", None), ("fp32c", ("sm", 1))])
 @pytest.mark.parametrize("reorder", [False, True])
-def test_hmc_with_tree_prior_matches_oracle(prec, reorder):
+def test_hmc_with_tree_prior_matches_oracle(prec, chunks, reorder):
     """HMC on log pi = L + log p(X | tree) with injected momenta and uniforms:
-    the same decisions, energy differences and end point as the oracle."""
+    the same decisions, energy differences and end point as the oracle.
+    With the grouped chunked shape forced, the same chunks run one per CTA
+    beside the traversal."""
     import math
     from paper_1905_04582_gb300.mds import MDS
     f, y, x_eval, sigma = _tree_workload((70, 50), 6, 41)
@@ -149,7 +151,7 @@ def test_hmc_with_tree_prior_matches_oracle(prec, reorder):
     n_iter, n_steps, eps = 5, 8, 2e-3
     p_all, u_all = W.momenta(42, n_iter, f.n, 2)
     xr, acc_r, dh_r = TP.hmc(y, x_eval.astype(np.float64), sigma, eps, n_steps, p_all, u_all, tree)
-    with MDS(f.n, 2, prec) as m:
+    with MDS(f.n, 2, prec, chunks=chunks) as m:
         m.set_data(y)
         m.set_locations(x_eval)
         m.set_sigma(sigma)
