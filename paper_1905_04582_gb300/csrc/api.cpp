@@ -65,6 +65,7 @@ struct mds_ctx {
     int32_t pass_kind = 0;
     int32_t chunk_mult = 0;       // in use (chunked pass)
     bool chunk_grouped = false;   // in use (chunked pass)
+    bool chunk_long_runs = false; // some chunk runs more than max_seg_tiles(d) tiles in one row block
     int32_t chunk_req = 0;        // > 0: chunked pass forced with this multiple
     bool chunk_grouped_req = false;
     Chunk *chunks = nullptr;
@@ -461,6 +462,7 @@ int build_chunks(mds_ctx *c, int mult, bool grouped) {
     std::vector<int32_t> first(nt + 1, -1);
     int64_t t = 0, I = Ib, J = Jb;
     int32_t seg = 0;
+    bool long_runs = false;
     for (int64_t g = 0; g < G; ++g) {
         while (t < cut[g]) {  // advance (I, J) to tile cut[g] of the range
             if (++J == nt) J = ++I;
@@ -475,10 +477,16 @@ int build_chunks(mds_ctx *c, int mult, bool grouped) {
         int64_t Il = I;
         while (Il + 1 < nt && tile_index(Il + 1, Il + 1, nt) <= ch.t1 - 1) ++Il;
         ch.I1 = static_cast<int32_t>(Il);
+        // segments: the chunk's run in each row block, cut every max_seg_tiles
         ch.seg0 = seg;
-        for (int64_t r = I; r <= Il; ++r)
-            if (first[r] < 0) first[r] = 4 * (seg + static_cast<int32_t>(r - I));
-        seg += static_cast<int32_t>(Il - I + 1);
+        const int64_t cap = max_seg_tiles(c->d);
+        for (int64_t r = I; r <= Il; ++r) {
+            const int64_t r0 = tile_index(r, r, nt);
+            const int64_t len = std::min<int64_t>(ch.t1, r0 + nt - r) - std::max<int64_t>(ch.t0, r0);
+            if (first[r] < 0) first[r] = 4 * seg;
+            seg += static_cast<int32_t>((len + cap - 1) / cap);
+            long_runs = long_runs || len > cap;
+        }
         v[g] = ch;
     }
     first[nt] = 4 * seg;
@@ -504,6 +512,7 @@ int build_chunks(mds_ctx *c, int mult, bool grouped) {
     c->pass_kind = kPassChunks;
     c->chunk_mult = mult;
     c->chunk_grouped = grouped;
+    c->chunk_long_runs = long_runs;
     c->strip = 0;
     c->gen++;
     return MDS_OK;
@@ -678,6 +687,7 @@ PairArgs pair_args(const mds_ctx *c) {
         a.chunks = c->chunks;
         a.xcol2 = c->xcol2;
         a.far_tile = c->far_tile;
+        a.long_runs = c->chunk_long_runs ? 1 : 0;
     }
     const double s = c->sigma;
     // far warp blocks: every pair at z >= z_c (the squared-distance bound in
@@ -1027,7 +1037,9 @@ int autotune(mds_ctx *c) {
     if (cands.empty()) cands.emplace_back(kPassStrips, 1);
     if (!c->fp64 && c->tiles >= 2) {
         const int per_sm = std::max(1, pair_chunk_blocks_per_sm(c->d));
-        for (int m : {1, 2, 3})
+        // more chunks per slot also keep every chunk's row-block runs within
+        // max_seg_tiles at large N, where the uncut loop is the faster build
+        for (int m : {1, 2, 3, 4, 6})
             if (static_cast<int64_t>(c->sm_count) * per_sm * m <= c->tiles || m == 1) cands.emplace_back(kPassChunks, m);
         // the grouped form (not beside a tree prior's traversal, which it
         // leaves no room for)

@@ -11,18 +11,19 @@
 //
 // What differs from the strip pass:
 //  - work split: the tiles, in row-block order, are cut into one contiguous
-//    chunk per CTA, of equal estimated cost (far and near tiles weighted by
-//    the per-tile far counts of an earlier pass), so that the pass is one
-//    wave of CTAs that end together.  Each warp keeps its 3-stage TMA ring
-//    (its 4 KB quarter of every Y tile and its 16 columns of locations)
-//    running across row-block boundaries; at a boundary it writes its row
-//    sums to its own partial slot and goes on.  No CTA barrier runs inside
-//    the loop.
+//    chunk per group of four warps, of equal estimated cost (far and near
+//    tiles weighted by the per-tile far counts of an earlier pass), so that
+//    the pass is one wave of chunks that end together.  Each warp keeps its
+//    3-stage TMA ring (its 4 KB quarter of every Y tile and its 16 columns of
+//    locations) running across row-block boundaries; at a boundary, and
+//    after every max_seg_tiles(D) tiles of one row block, it writes its row sums
+//    to its own partial slot and goes on.  No barrier of the group runs
+//    inside the loop.
 //  - the row block's split locations sit in three shared-memory buffers
-//    shared by the CTA's warps: the last warp to finish a segment (a count in
-//    shared memory) issues the bulk copy of the segment three ahead into the
-//    buffer it frees, so even a run of one-tile segments (the last row blocks)
-//    finds its locations landed.
+//    shared by the group's warps: the last warp to finish a row block (a
+//    count in shared memory) issues the bulk copy of the row block three
+//    ahead into the buffer it frees, so even a run of one-tile row blocks
+//    (the last ones of the triangle) finds its locations landed.
 //  - the gradient weight is summed without its factor -1/sigma^2:
 //    w' = -sigma^2 w = (e - sigma phi'/sqrt(2 pi)) ... (one FMA fewer per
 //    pair); the reduction multiplies the partial sums by -1/sigma^2 in FP64.
@@ -38,7 +39,7 @@ namespace mds {
 namespace {
 
 constexpr int kChunkStages = 3;  // per-warp ring depth
-constexpr int kXisBufs = 3;      // row-block location buffers of a CTA (two segments of lead)
+constexpr int kXisBufs = 3;      // row-block location buffers of a group (two row blocks of lead)
 
 __host__ __device__ constexpr int align128(int b) { return (b + 127) / 128 * 128; }
 
@@ -52,7 +53,7 @@ struct ChunkLayout {
     static constexpr int kBarOffset = kXiOffset + kXisBufs * align128(kXiBytes);
     // mbarriers: [warp][stage], then the row-block buffers
     static constexpr int kCntOffset = kBarOffset + (kPairWarps * kChunkStages + kXisBufs) * 8;
-    // done[kXisBufs] (warps that finished a segment on each buffer), issued[kXisBufs] (copies into it)
+    // done[kXisBufs] (warps that finished a row block on each buffer), issued[kXisBufs] (copies into it)
     static constexpr int kBoxOffset = kCntOffset + 2 * kXisBufs * 4;
     static constexpr int kBytes = kBoxOffset + kPairWarps * 2 * D * 4;
 };
@@ -423,8 +424,11 @@ constexpr int chunk_slots_per_sm() {
 // one CTA do (17.6, 17.5, 17.2 us), so the grouped form ends with the SM's
 // work instead of its slowest CTA.  Its groups cannot be replaced one by
 // one, which favours the one-group form when there are several chunks per
-// slot.
-template <int D, bool HELDOUT, int G>
+// slot.  CAP: some chunk runs more than max_seg_tiles(D) tiles in one row
+// block, so segments are cut every max_seg_tiles(D) tiles (without it the
+// loop keeps only the row-block boundaries, which is the same cut for shorter
+// runs, and compiles to faster code).
+template <int D, bool HELDOUT, int G, bool CAP>
 __global__ void __launch_bounds__(kPairThreads * G, (G > 1 ? 1 : chunk_slots_per_sm<D>()))
     pair_chunk_kernel(const __grid_constant__ PairArgs a) {
     using L = ChunkLayout<D>;
@@ -528,48 +532,97 @@ __global__ void __launch_bounds__(kPairThreads * G, (G > 1 ? 1 : chunk_slots_per
     int n_far = 0;
     int I = ch.I0, J = ch.J0;
     int cslot = static_cast<int>(col_slot(I, J));  // column-partial slot of tile (I, J), kept in step
-    int seg = -1;
+    int seg = -1;  // segment of the chunk (row-partial slot 4 (seg0 + seg) + warp)
+    int rb = -1;   // CAP: row block of the chunk, I - I0 (location buffer rb % kXisBufs)
+    int run = 0;   // CAP: tiles of the current segment
     const float4 *xis = nullptr;
     int stage = 0;
     uint32_t phase = 0;
     int k = 0;
     for (; k < ntile; ++k) {
-        if (k == 0 || J == I) {
-            if (seg >= 0) {
-                // the previous segment is done: its row sums out, its row
-                // buffer released (the last warp to release it refills it
-                // with the segment kXisBufs ahead)
-                float *rp = rowp_base + static_cast<int64_t>(4 * (ch.seg0 + seg) + warp) * kTile * D;
-                if constexpr (kTall)
-                    flush_rows_tall<D>(racc, lane, rp);
-                else
-                    flush_rows<D>(racc, lane, rp);
-                __syncwarp();
-                if (lane == 0) {
-                    const int b = seg % kXisBufs;
-                    __threadfence_block();
-                    const unsigned old = atomicAdd(&done[b], 1u);
-                    if ((old + 1u) % kPairWarps == 0u && ch.I0 + seg + kXisBufs <= ch.I1) {
-                        fence_proxy_async();
-                        issued[b] += 1u;
-                        issue_rows<D>(a, ch.I0 + seg + kXisBufs, xbuf(b), &xbar[b]);
+        if constexpr (!CAP) {
+            if (k == 0 || J == I) {
+                if (seg >= 0) {
+                    // the previous segment (a row block) is done: its row sums
+                    // out, its row buffer released (the last warp to release
+                    // it refills it with the row block kXisBufs ahead)
+                    float *rp = rowp_base + static_cast<int64_t>(4 * (ch.seg0 + seg) + warp) * kTile * D;
+                    if constexpr (kTall)
+                        flush_rows_tall<D>(racc, lane, rp);
+                    else
+                        flush_rows<D>(racc, lane, rp);
+                    __syncwarp();
+                    if (lane == 0) {
+                        const int b = seg % kXisBufs;
+                        __threadfence_block();
+                        const unsigned old = atomicAdd(&done[b], 1u);
+                        if ((old + 1u) % kPairWarps == 0u && ch.I0 + seg + kXisBufs <= ch.I1) {
+                            fence_proxy_async();
+                            issued[b] += 1u;
+                            issue_rows<D>(a, ch.I0 + seg + kXisBufs, xbuf(b), &xbar[b]);
+                        }
                     }
                 }
-            }
-            ++seg;
-            if (!__all_sync(0xffffffffu,
-                            mbar_wait_bounded(&xbar[seg % kXisBufs], static_cast<uint32_t>(seg / kXisBufs) & 1u,
-                                              a.err))) {
-                ok = false;
-                break;
-            }
-            xis = reinterpret_cast<const float4 *>(xbuf(seg % kXisBufs));
-            float b[2 * D];
-            row_box<D>(xis, lane, b);
-            if (lane == 0)
+                ++seg;
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait_bounded(&xbar[seg % kXisBufs], static_cast<uint32_t>(seg / kXisBufs) & 1u,
+                                                  a.err))) {
+                    ok = false;
+                    break;
+                }
+                xis = reinterpret_cast<const float4 *>(xbuf(seg % kXisBufs));
+                float b[2 * D];
+                row_box<D>(xis, lane, b);
+                if (lane == 0)
 #pragma unroll
-                for (int i = 0; i < 2 * D; ++i) box[i] = b[i];
-            __syncwarp();
+                    for (int i = 0; i < 2 * D; ++i) box[i] = b[i];
+                __syncwarp();
+            }
+        } else {
+            const bool new_rb = k == 0 || J == I;
+            if (new_rb || run == max_seg_tiles(D)) {
+                if (seg >= 0) {
+                    // the previous segment is done: its row sums out
+                    float *rp = rowp_base + static_cast<int64_t>(4 * (ch.seg0 + seg) + warp) * kTile * D;
+                    if constexpr (kTall)
+                        flush_rows_tall<D>(racc, lane, rp);
+                    else
+                        flush_rows<D>(racc, lane, rp);
+                    __syncwarp();
+                }
+                ++seg;
+                run = 0;
+            }
+            if (new_rb) {
+                if (rb >= 0 && lane == 0) {
+                    // the previous row block is done: its buffer released (the
+                    // last warp to release it refills it with the row block
+                    // kXisBufs ahead)
+                    const int b = rb % kXisBufs;
+                    __threadfence_block();
+                    const unsigned old = atomicAdd(&done[b], 1u);
+                    if ((old + 1u) % kPairWarps == 0u && ch.I0 + rb + kXisBufs <= ch.I1) {
+                        fence_proxy_async();
+                        issued[b] += 1u;
+                        issue_rows<D>(a, ch.I0 + rb + kXisBufs, xbuf(b), &xbar[b]);
+                    }
+                }
+                ++rb;
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait_bounded(&xbar[rb % kXisBufs], static_cast<uint32_t>(rb / kXisBufs) & 1u,
+                                                  a.err))) {
+                    ok = false;
+                    break;
+                }
+                xis = reinterpret_cast<const float4 *>(xbuf(rb % kXisBufs));
+                float b[2 * D];
+                row_box<D>(xis, lane, b);
+                if (lane == 0)
+#pragma unroll
+                    for (int i = 0; i < 2 * D; ++i) box[i] = b[i];
+                __syncwarp();
+            }
+            ++run;
         }
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[stage], phase, a.err))) {
             ok = false;
@@ -686,6 +739,21 @@ constexpr int chunk_cta_smem() {
     return G > 1 ? G * align128(ChunkLayout<D>::kBytes) : ChunkLayout<D>::kBytes;
 }
 
+template <int D, bool HO, int G, bool CAP>
+cudaError_t launch_one(const PairArgs &a, cudaStream_t s, bool pdl, int smem) {
+    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, HO, G, CAP>), smem);
+    if (e != cudaSuccess) return e;
+    if (a.n_strips <= 0) return cudaSuccess;
+    e = launch_maybe_pdl(pdl, pair_chunk_kernel<D, HO, G, CAP>, dim3((a.n_strips + G - 1) / G),
+                         dim3(kPairThreads * G), smem, s, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int D, bool HO, int G>
+cudaError_t launch_cap(const PairArgs &a, cudaStream_t s, bool pdl, int smem) {
+    return a.long_runs ? launch_one<D, HO, G, true>(a, s, pdl, smem) : launch_one<D, HO, G, false>(a, s, pdl, smem);
+}
+
 template <int D>
 cudaError_t launch_d(const PairArgs &a, cudaStream_t s, bool pdl, int smem_min, bool grouped) {
     constexpr int G = chunk_slots_per_sm<D>();
@@ -693,22 +761,10 @@ cudaError_t launch_d(const PairArgs &a, cudaStream_t s, bool pdl, int smem_min, 
         // held-out passes keep the one-group form (the chunk table serves both:
         // the same chunk slots per SM)
         const int smem = smem_min > chunk_cta_smem<D, G>() ? smem_min : chunk_cta_smem<D, G>();
-        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, G>), smem);
-        if (e != cudaSuccess) return e;
-        if (a.n_strips <= 0) return cudaSuccess;
-        e = launch_maybe_pdl(pdl, pair_chunk_kernel<D, false, G>, dim3((a.n_strips + G - 1) / G),
-                             dim3(kPairThreads * G), smem, s, a);
-        return e != cudaSuccess ? e : cudaGetLastError();
+        return launch_cap<D, false, G>(a, s, pdl, smem);
     }
     const int smem = smem_min > chunk_cta_smem<D, 1>() ? smem_min : chunk_cta_smem<D, 1>();
-    cudaError_t e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, 1>), smem);
-    if (e == cudaSuccess) e = raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, true, 1>), smem);
-    if (e != cudaSuccess) return e;
-    if (a.n_strips <= 0) return cudaSuccess;
-    e = a.tile_ho
-            ? launch_maybe_pdl(pdl, pair_chunk_kernel<D, true, 1>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a)
-            : launch_maybe_pdl(pdl, pair_chunk_kernel<D, false, 1>, dim3(a.n_strips), dim3(kPairThreads), smem, s, a);
-    return e != cudaSuccess ? e : cudaGetLastError();
+    return a.tile_ho ? launch_cap<D, true, 1>(a, s, pdl, smem) : launch_cap<D, false, 1>(a, s, pdl, smem);
 }
 
 // Chunk slots per SM (groups of four warps that are resident at once): the
@@ -719,17 +775,18 @@ int blocks_per_sm_d(bool grouped) {
     int nb = 0;
     if (grouped) {
         constexpr int smem = chunk_cta_smem<D, G>();
-        if (raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, G>), smem) != cudaSuccess)
-            return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_chunk_kernel<D, false, G>, kPairThreads * G,
-                                                          smem) != cudaSuccess)
+        const void *fn = reinterpret_cast<const void *>(pair_chunk_kernel<D, false, G, false>);
+        if (raise_dyn_smem(fn, smem) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_chunk_kernel<D, false, G, false>,
+                                                          kPairThreads * G, smem) != cudaSuccess)
             return 0;
         return nb * G;
     }
     constexpr int smem = chunk_cta_smem<D, 1>();
-    if (raise_dyn_smem(reinterpret_cast<const void *>(pair_chunk_kernel<D, false, 1>), smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_chunk_kernel<D, false, 1>, kPairThreads, smem) !=
-        cudaSuccess)
+    const void *fn = reinterpret_cast<const void *>(pair_chunk_kernel<D, false, 1, false>);
+    if (raise_dyn_smem(fn, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_chunk_kernel<D, false, 1, false>, kPairThreads,
+                                                      smem) != cudaSuccess)
         return 0;
     return nb;
 }

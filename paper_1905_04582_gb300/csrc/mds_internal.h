@@ -72,11 +72,16 @@ struct Strip {
 
 // One unit of work of the chunked FP32C pair pass (chunk_kernel.cu): the
 // tiles [t0, t1) of the row-block-ordered tile sequence, (I0, J0) the blocks
-// of tile t0 and I1 the row block of tile t1 - 1.  A segment is the run of a
-// chunk's tiles in one row block (segment s of the chunk is row block I0 + s);
-// seg0 is the chunk's first segment in the global order of segments (chunk
-// by chunk), which sets its row-partial slots: warp w of segment g writes
-// slot 4 g + w.  The segments of one row block are consecutive in that order.
+// of tile t0 and I1 the row block of tile t1 - 1.  A segment is a run of at
+// most max_seg_tiles(D) of a chunk's tiles in one row block: the chunk's run
+// in a row block of L tiles is ceil(L / max_seg_tiles(D)) segments.  seg0 is
+// the chunk's first segment in the global order of segments (chunk by
+// chunk), which sets its row-partial slots: warp w of segment g writes slot
+// 4 g + w.  The segments of one row block are consecutive in that order.
+// max_seg_tiles bounds the FP32 row sums a lane keeps in registers at 256
+// terms, as the strip pass's longest strip: 2 columns x 128 tiles in the
+// 16 x 2 lane mapping of D <= 2, 4 columns x 64 tiles in the 8 x 4 one.
+__host__ __device__ constexpr int max_seg_tiles(int d) { return d <= 2 ? 128 : 64; }
 struct Chunk {
     int64_t t0, t1;
     int32_t I0, J0, I1;
@@ -144,6 +149,9 @@ struct PairArgs {
                                  // of the pass's warps after the dependency wait (min / max atomics)
     float far_d2;            // FP32C: (z_c sigma)^2; warp blocks at least this far apart skip the Phi
                              // terms (+inf: never)
+    int32_t long_runs;       // chunked FP32C pass: some chunk runs more than max_seg_tiles(D) tiles in
+                             // one row block, so its segments are cut every max_seg_tiles(D) tiles (in the
+                             // padding before the float2 constants: the layout after it is unchanged)
     // FP32C constants (sigma folded in on the host), each duplicated {c, c}
     // so that it is a ready operand of the packed f32x2 instructions
     float2 mp[4];            // -P(delta/sigma)/sqrt(2 pi) coefficients in powers of delta

@@ -203,11 +203,14 @@ SCALE = [(20000, 2), (20000, 6), (50000, 2), (50000, 6)]
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("n,d", SCALE)
-def test_parity_scale_sweep_sampled(n, d):
+@pytest.mark.parametrize("n,d,chunks", [(n, d, None) for n, d in SCALE] +
+                         [(20000, 2, ("sm", 1)), (20000, 6, ("sm", 1)), (50000, 6, ("sm", 2))])
+def test_parity_scale_sweep_sampled(n, d, chunks):
     """Scale sweep: likelihood and dL/dsigma against the (threaded) oracle,
     gradient on 256 sampled rows computed one by one by the oracle, and the
-    translation invariance sum_i grad_i = 0 over all rows."""
+    translation invariance sum_i grad_i = 0 over all rows.  With `chunks`,
+    the shape the benchmark's autotuner picks there (the grouped chunked
+    pass) in the locality order, as the benchmark runs it."""
     from paper_1905_04582_gb300.mds import MDS
     wl = W.scale_sweep(n, d)
     x64 = wl.x_eval.astype(np.float64)
@@ -216,10 +219,12 @@ def test_parity_scale_sweep_sampled(n, d):
                                          with_sq=True)
     ll_ref, _ = oracle.loglik(wl.y_packed, x64, wl.sigma, nthreads=16)
     ds_ref = oracle.dsigma(wl.y_packed, x64, wl.sigma, nthreads=16)
-    with MDS(n, d, "fp32c") as m:
+    with MDS(n, d, "fp32c", chunks=chunks) as m:
         m.set_data(wl.y_packed)
         m.set_locations(wl.x_eval)
         m.set_sigma(wl.sigma)
+        if chunks is not None:
+            m.reorder()
         ll, g, ds = m.gradient()
     tol = TOL["fp32c"]
     scalar_check(ll, ll_ref, tol["ll"], what="log-likelihood")
