@@ -639,7 +639,7 @@ int order_strips_by_cost(mds_ctx *c) {
     return MDS_OK;
 }
 
-constexpr int kMaxStrip = 64;  // bounds the FP32 row sums of a lane (<= 256 terms)
+constexpr int kMaxStrip = 16;  // bounds the FP32 row sums of a lane (<= 64 terms, 4 columns a tile)
 
 // Choose the split quantum from max |x| of locations the caller sets and
 // rewrite the split layouts.  During trajectories the end-of-trajectory
@@ -1027,7 +1027,7 @@ int autotune(mds_ctx *c) {
         }
     }
     std::vector<std::pair<int, int>> cands;
-    for (int s : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
+    for (int s : {1, 2, 3, 4, 6, 8, 12, 16}) {
         if (s > kMaxStrip || s > c->nt) continue;
         const int64_t strips_est = (c->tiles + s - 1) / s;
         // keep enough CTAs for every SM, unless the problem is tiny anyway

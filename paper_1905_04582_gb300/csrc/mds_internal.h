@@ -78,10 +78,13 @@ struct Strip {
 // the chunk's first segment in the global order of segments (chunk by
 // chunk), which sets its row-partial slots: warp w of segment g writes slot
 // 4 g + w.  The segments of one row block are consecutive in that order.
-// max_seg_tiles bounds the FP32 row sums a lane keeps in registers at 256
-// terms, as the strip pass's longest strip: 2 columns x 128 tiles in the
-// 16 x 2 lane mapping of D <= 2, 4 columns x 64 tiles in the 8 x 4 one.
-__host__ __device__ constexpr int max_seg_tiles(int d) { return d <= 2 ? 128 : 64; }
+// max_seg_tiles bounds the FP32 row sums a lane keeps in registers at 64
+// terms, as the strip pass's longest strip: 2 columns x 32 tiles in the
+// 16 x 2 lane mapping of D <= 2, 4 columns x 16 tiles in the 8 x 4 one.  The
+// rounding of an FP32 partial sum grows faster than its length: at 256 terms
+// a lane, well-conditioned gradient coordinates of N = 20000, D = 2 reached
+// 1.25e-5 against the 1e-5 tolerance.
+__host__ __device__ constexpr int max_seg_tiles(int d) { return d <= 2 ? 32 : 16; }
 struct Chunk {
     int64_t t0, t1;
     int32_t I0, J0, I1;

@@ -7,12 +7,12 @@ Tolerances (stated for the hot path):
 A relative error is ill-conditioned where a coordinate's terms cancel, so a
 gradient coordinate also passes when
   (a) its condition number kappa = S / |g_ref| exceeds 1e3 (S = sum of the
-      absolute values of its terms, from the oracle) and its absolute error
-      is below max(tol * 1e-3, u) * S: terms summed in a precision of unit
-      roundoff u can be off by u * S in the worst case (each term rounded
-      once or twice on its way into a short partial sum), whatever the
-      grouping of the sum (the strip length, chosen by timing, sets it);
-      or
+      absolute values of its terms, from the oracle), or it lies below the
+      escape line defined next, and its absolute error is below
+      max(tol * 1e-3, u) * S: terms summed in a precision of unit roundoff u
+      can be off by u * S in the worst case (each term rounded once or twice
+      on its way into a short partial sum), whatever the grouping of the sum
+      (the pass shape, chosen by timing, sets it); or
   (b) its absolute error is below 8 u * S2, S2 = sqrt(sum of its squared
       terms) and u the unit roundoff of the path (2^-24 for FP32C, 2^-53 for
       FP64): the size of the rounding error that any evaluation of the
@@ -61,7 +61,14 @@ def grad_check(g, g_ref, s_abs, tol, what="gradient", s_sq=None, u=None):
     err = np.abs(g - g_ref)
     rel_ok = err <= tol * np.abs(g_ref)
     kappa = s_abs / np.maximum(np.abs(g_ref), 1e-300)
-    cond_ok = (kappa > KAPPA) & (err <= max(tol * 1e-3, u or 0.0) * s_abs)
+    # the cancellation branch: kappa above KAPPA, or (with S2 known) the
+    # coordinate below the escape line, where even a few ulps per term cannot
+    # promise the relative tolerance and the FP32 sums' own rounding, up to
+    # u S, decides
+    ill = kappa > KAPPA
+    if s_sq is not None and u is not None:
+        ill = ill | (np.abs(g_ref) <= ESCAPE_SLACK * ULPS * u / tol * np.asarray(s_sq, dtype=np.float64))
+    cond_ok = ill & (err <= max(tol * 1e-3, u or 0.0) * s_abs)
     if s_sq is not None and u is not None:
         round_ok = err <= ULPS * u * np.asarray(s_sq, dtype=np.float64)
     else:

@@ -194,3 +194,17 @@ def test_grouped_form_paper_scale_repeats_and_agrees(paper_workload):
         compare(b, wl, "fp32c", ref)
     assert lb == lb2 and db == db2 and np.array_equal(gb, gb2)
     scalar_check(lb, la, 2e-6, what="grouped vs one-group L")
+
+
+@pytest.mark.parametrize("n,d,chunks", [(20000, 2, ("count", 8)), (9000, 2, ("count", 8)), (9000, 3, ("count", 4)),
+                                        (6000, 6, ("count", 2)), (9000, 2, ("sm", 1))])
+def test_chunked_long_runs_are_cut(n, d, chunks):
+    """Few large chunks run more than max_seg_tiles(D) tiles (32 at D <= 2,
+    16 beyond) in a row block: the pass cuts their row sums into segments of
+    at most 64 terms a lane (its second kernel variant) and still matches
+    the oracle at the stated tolerances; the grouped case at N = 9000 (chunks
+    of about 22 tiles) keeps the uncut loop."""
+    wl = W.custom(n, d, sigma=0.3, seed=700 + n + d, mixture=(6, 0.3))
+    with chunked(wl, chunks, reorder=True) as m:
+        info = compare(m, wl, "fp32c")
+    print(n, d, chunks, info)
