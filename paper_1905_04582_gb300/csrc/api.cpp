@@ -936,8 +936,11 @@ void tune_load() {
         if (fld.size() != 8) continue;
         TuneKey k{fld[0], atoll(fld[1].c_str()), atoi(fld[2].c_str()), fld[3] == "fp64", fld[4] == "locality"};
         TuneVal v{atoi(fld[5].c_str()), atoi(fld[6].c_str()), atof(fld[7].c_str())};
+        // chunked: param chunks per slot (1..8), or for kPassChunks minus an
+        // exact chunk count
         if ((v.kind == kPassStrips && v.param >= 1 && v.param <= kMaxStrip) ||
-            ((v.kind == kPassChunks || v.kind == kPassChunksSM) && v.param >= 1 && v.param <= 8))
+            ((v.kind == kPassChunks || v.kind == kPassChunksSM) && v.param >= 1 && v.param <= 8) ||
+            (v.kind == kPassChunks && v.param < 0 && v.param >= -(1 << 26)))
             g_tune_cache[k] = v;
     }
     fclose(f);
@@ -1041,6 +1044,12 @@ int autotune(mds_ctx *c) {
         // max_seg_tiles at large N, where the uncut loop is the faster build
         for (int m : {1, 2, 3, 4, 6})
             if (static_cast<int64_t>(c->sm_count) * per_sm * m <= c->tiles || m == 1) cands.emplace_back(kPassChunks, m);
+        // where even 6 chunks per slot run longer than the segment cut in a row
+        // block: enough chunks (0.8 of the cut on average) for the uncut loop
+        const int64_t cut = max_seg_tiles(c->d);
+        const int64_t uncut = (c->tiles * 5 + 4 * cut - 1) / (4 * cut);
+        if (uncut > static_cast<int64_t>(c->sm_count) * per_sm * 6 && uncut <= (1 << 26))
+            cands.emplace_back(kPassChunks, -static_cast<int>(uncut));
         // the grouped form (not beside a tree prior's traversal, which it
         // leaves no room for)
         const int per_sm_g = pair_chunk_blocks_per_sm(c->d, true);
