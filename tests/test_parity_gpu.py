@@ -168,6 +168,35 @@ def test_large_and_tiny_separations(prec):
         compare(m, wl, prec)
 
 
+def test_set_locations_range_error_keeps_state():
+    """Locations beyond the FP32C split range are refused on the device before
+    anything is written (the set-up kernel derives the split quantum from
+    max |x|): INVALID_ARG naming the range, and the previous locations and
+    their likelihood unchanged; a NaN entry is INVALID_ARG as well."""
+    from paper_1905_04582_gb300.mds import MDS
+    wl = W.custom(120, 2, seed=12)
+    with MDS(wl.n, wl.d, "fp32c") as m:
+        m.set_data(wl.y_packed)
+        m.set_sigma(wl.sigma)
+        m.set_locations(wl.x_eval)
+        ll0, _ = m.log_likelihood()
+        far = wl.x_eval.copy()
+        far[7, 0] = 1e36
+        with pytest.raises(MDSError) as e:
+            m.set_locations(far)
+        assert e.value.status == MDS_ERR_INVALID_ARG and "FP32C range" in str(e.value)
+        np.testing.assert_array_equal(m.get_locations(dtype=np.float32), wl.x_eval)
+        ll1, _ = m.log_likelihood()
+        assert ll1 == ll0
+        m.set_locations(wl.x_eval)
+        assert m.log_likelihood()[0] == ll0
+        nanx = wl.x_eval.copy()
+        nanx[2, 1] = np.nan
+        with pytest.raises(MDSError) as e:
+            m.set_locations(nanx)
+        assert e.value.status == MDS_ERR_INVALID_ARG
+
+
 def test_invalid_inputs_are_rejected():
     from paper_1905_04582_gb300.mds import MDS
     wl = W.custom(100, 2, seed=10)
